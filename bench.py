@@ -1,0 +1,341 @@
+"""Benchmark: forward + backward propagations per second on the polarised 4f workload.
+
+Workload (one step): 16 objects x 3 field components (Ex, Ey, Ez) x 8 wavelengths in
+450-700 nm = 384 fields of 1024 x 1024, spacing 5 um, 2x zero padding (2048^2 FFTs),
+angular-spectrum method; a 4f system with two thin lenses (f = 0.2 m) and a circular
+pupil (R = 1 mm) carrying a trainable phase; detector intensity summed over each
+object's components and wavelengths; MSE loss against seeded targets; gradient with
+respect to the pupil phase. Per field: 4 forward and 2 backward propagations. The
+metric counts fwd+bwd propagation pairs: (forward + backward propagations) / 2 per
+second, whole job over all ranks (weak scaling, one replica of the workload per GPU).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import glob
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synthetic as S  # noqa: E402
+
+METRIC = "fwd+bwd propagations/s at 1024² c64, % of HBM roofline, rel-L2 vs FP64"
+UNIT = "fwd+bwd propagations/s"
+FALLBACK_HBM = 6800.0
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except Exception:
+        return {"hbm_gbs": FALLBACK_HBM}, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2411_18591_gb300", "csrc", "*"))):
+        with open(p, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kind: str):
+    """DRAM bytes per field of a kernel from the committed ncu summary, if it matches the current sources."""
+    path = os.path.join(ROOT, "profiles", f"{kind}_summary.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m = re.search(r"dram_bytes_per_field:\s*([0-9.eE+]+)", text)
+    s = re.search(r"source_hash:\s*([0-9a-f]+)", text)
+    if not m or not s or s.group(1) != kernel_source_hash():
+        return None
+    return float(m.group(1))
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id: str | None):
+        self.bus_id = bus_id
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        cmd = ["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.bus_id:
+            cmd += ["-i", self.bus_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [v.strip() for v in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def bus_id_of(dev_index: int):
+    import torch
+    try:
+        p = torch.cuda.get_device_properties(dev_index)
+        return f"{p.pci_domain_id:08X}:{p.pci_bus_id:02X}:{p.pci_device_id:02X}.0"
+    except Exception:
+        return None
+
+
+# ----------------------------------------------------------------------------- CPU oracle sample
+
+def oracle_sample_step(obj_field, lam, fourf_cfg, phase, target):
+    """The oracle (FP64, host) on one field of the workload: 4 forward + 2 backward propagations."""
+    import oracle as O
+    c = fourf_cfg
+    t0 = time.perf_counter()
+    loss, g_phi, _ = O.fourf_loss_and_grad(obj_field[None], [lam], c["d"], c["f"], c["lens_radius"],
+                                           c["pupil_radius"], phase, 1, target[None], c["pad"])
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(steps: int, warmup: int, budget_s: float = 25.0):
+    n = S.CFG4["n"]
+    c = S.CFG4
+    obj = S.cfg4_objects(1, 1, n)[0, 0].astype(np.complex128)
+    phase = S.cfg4_pupil_phase(n)
+    target = S.cfg4_target(1, n)[0]
+    lam = float(S.cfg4_wavelengths(c["wavelengths"])[0])
+    cfg = dict(d=c["d"], f=c["f"], lens_radius=c["lens_radius"], pupil_radius=c["pupil_radius"], pad=c["pad"])
+    times = []
+    t_start = time.perf_counter()
+    for i in range(warmup + steps):
+        dt = oracle_sample_step(obj, lam, cfg, phase, target)
+        if i >= warmup:
+            times.append(dt)
+        if time.perf_counter() - t_start > budget_s and len(times) >= 1:
+            break
+    per = statistics.median(times)
+    units = (4 + 2) / 2.0
+    return {"value": units / per, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "1 of 384 fields (object 0, Ex, 450 nm): the full 4f chain in float64 numpy "
+                      "(4 forward + 2 backward propagations, 2048^2 FFTs), loss on that field's intensity; "
+                      f"{len(times)} timed of {warmup + len(times)} runs, median {per:.2f} s per field"}
+
+
+# ----------------------------------------------------------------------------- reference arm
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    cb = cpu_baseline(args.steps, args.warmup, budget_s=150.0)
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * 3.0 / cb["value"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(sample=True),
+            "cpu_baseline": cb, "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
+                                       "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(sample=False):
+    c = S.CFG4
+    return {"workload": "polarised 4f imaging, fwd+bwd w.r.t. pupil phase" + (" (oracle sample)" if sample else ""),
+            "objects": c["objects"], "components": c["comps"], "wavelengths": c["wavelengths"],
+            "fields": c["objects"] * c["comps"] * c["wavelengths"], "grid": [c["n"], c["n"]], "spacing_m": c["d"],
+            "pad": c["pad"], "fft": [2 * c["n"], 2 * c["n"]], "method": "angular spectrum", "focal_m": c["f"],
+            "props_per_field": {"fwd": 4, "bwd": 2}, "l2": "inputs and intermediates (3.2 GB per plane) exceed L2"}
+
+
+# ----------------------------------------------------------------------------- our arm
+
+def run_ours(args, rank, world):
+    import torch
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2411_18591_gb300 import binding as Bd
+    from paper_2411_18591_gb300.fourf import FourF
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    c = S.CFG4
+    sysm = FourF(n=c["n"], d=c["d"], f=c["f"], lens_radius=c["lens_radius"], pupil_radius=c["pupil_radius"],
+                 objects=c["objects"], comps=c["comps"], wavelengths=tuple(S.cfg4_wavelengths(c["wavelengths"])),
+                 pad=c["pad"])
+    obj_host = S.cfg4_objects(c["objects"], c["comps"], c["n"]).reshape(-1, c["n"], c["n"]).astype(np.complex64)
+    obj_pinned = torch.from_numpy(obj_host).pin_memory()
+    obj = obj_pinned.to(dev)
+    phase = torch.from_numpy(S.cfg4_pupil_phase(c["n"]).astype(np.float32)).to(dev)
+    target = torch.from_numpy(S.cfg4_target(c["objects"], c["n"]).astype(np.float32)).to(dev)
+    gphase = torch.empty_like(phase)
+    bufs = {}
+    dist = world > 1
+    if dist:
+        import torch.distributed as tdist
+
+    def step(x):
+        loss, _ = sysm.step(x, phase, target, gphase, bufs)
+        if dist:
+            tdist.all_reduce(gphase)
+        return loss
+
+    for _ in range(max(3, args.warmup)):
+        step(obj)
+    torch.cuda.synchronize()
+
+    stream = torch.cuda.current_stream(dev)
+    sampler = ClockSampler(bus_id_of(local))
+
+    def barrier():
+        if dist:
+            tdist.barrier()
+        torch.cuda.synchronize()
+
+    # device-resident timing, with the library's per-kernel event timing on the same stream
+    Bd.profile_enable(True, dev)
+    Bd.profile_read(dev)
+    barrier()
+    sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step(obj)
+    e1.record(stream)
+    barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    prof = Bd.profile_read(dev)
+    Bd.profile_enable(False, dev)
+    t = torch.tensor([ms], device=dev)
+    if dist:
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    ms = float(t.item())
+    units_per_step = sysm.batch * (FourF.FWD_PROPS + FourF.BWD_PROPS) / 2.0
+    value = units_per_step * world / (ms / 1000.0)
+
+    # end to end: inputs copied from pinned host memory every step, loss and gradient read back
+    h2d = obj_pinned.numel() * 8
+    host_g = torch.empty(phase.shape, dtype=torch.float32).pin_memory()
+    host_l = torch.empty(1, dtype=torch.float64).pin_memory()
+    xin = torch.empty_like(obj)
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        xin.copy_(obj_pinned, non_blocking=True)
+        loss = step(xin)
+        host_l.copy_(loss.reshape(1), non_blocking=True)
+        host_g.copy_(gphase, non_blocking=True)
+    e1.record(stream)
+    barrier()
+    ms_e2e = e0.elapsed_time(e1) / args.steps
+    t = torch.tensor([ms_e2e], device=dev)
+    if dist:
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    ms_e2e = float(t.item())
+    e2e = {"value": units_per_step * world / (ms_e2e / 1000.0), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+           "d2h_bytes_per_step": int(host_g.numel() * 4 + 8)}
+
+    # roofline of the dominant kernel (the column pass): algorithmic bytes = the workspace lines
+    # read and written once, 2 x Px x ny x 8 B per field per launch
+    peaks, peak_kind = measured_peaks()
+    kinds = {k: v for k, v in prof.items() if v[1] > 0}
+    dominant = max(kinds, key=lambda k: kinds[k][0])
+    cols_ms, cols_n = prof["cols"]
+    bytes_per_field = 2 * (2 * c["n"]) * c["n"] * 8
+    cols_bytes = sysm.batch * bytes_per_field
+    cols_avg_s = cols_ms / cols_n / 1000.0
+    achieved = cols_bytes / cols_avg_s / 1e9
+    traffic = profiled_traffic("cols")
+    roofline = {"kernel": "cols (column pass: y-FFT x H x inverse y-FFT)", "bound": "hbm", "achieved": achieved,
+                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+                "traffic": None if traffic is None else traffic * sysm.batch, "peak_source": peak_kind,
+                "algorithmic_bytes_per_launch": cols_bytes, "avg_launch_ms": cols_avg_s * 1000.0,
+                "dominant_by_time": dominant,
+                "kernel_ms_per_step": {k: v[0] / args.steps for k, v in kinds.items()}}
+    launches = int(sum(v[1] for v in prof.values()))
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c64/f32 (FP64 phase tables)", "data": "synthetic",
+            "config": workload_config(), "roofline": roofline, "clocks": clocks, "e2e": e2e,
+            "gpu_launches": launches}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(2, 0)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)  # host-only; ranks other than 0 exit without work
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        local = int(os.environ.get("LOCAL_RANK", "0"))
+        torch.cuda.set_device(local)
+        tdist.init_process_group("nccl")
+    try:
+        run_ours(args, rank, world)
+    finally:
+        if world > 1:
+            import torch.distributed as tdist
+            tdist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,232 @@
+/*
+ * top.h -- C ABI of a GB300 (sm_103a) library for differentiable free-space
+ * propagation of sampled scalar optical fields (TorchOptics, arXiv 2411.18591).
+ *
+ * The library implements, in its own CUDA kernels (no cuFFT):
+ *   - angular-spectrum (AS) propagation, Eq. 4 with the transfer function of
+ *     Eq. 5, and the Fresnel transfer-function variant named in §3;
+ *   - configurable zero padding and cropping (§3);
+ *   - element modulation, Eq. 1 (phase masks, amplitude masks, complex masks,
+ *     thin lenses and circular apertures, §2 and §5.4), fused into the
+ *     propagation passes;
+ *   - detector intensity |psi|^2 and the incoherent sum of Eq. 14, fused;
+ *   - the hand-written adjoint (backward) of all of the above (§4);
+ *   - mutual-coherence modulation and propagation, Eq. 12-13 (§5.2).
+ *
+ * Conventions shared by every call
+ *   - Fields are complex64 (interleaved float re, im), row-major
+ *     [batch][ny][nx], x fastest. Intensities and phases are float32.
+ *   - All field, mask and gradient buffers are DEVICE memory owned by the
+ *     caller and must be 16-byte aligned; the library never frees them.
+ *     Wavelength and distance arrays (lambda, z) are HOST arrays of doubles.
+ *   - Padded size per axis P = floor(pad * n + 0.5) (P >= n); the field sits at
+ *     offset floor((P - n) / 2) of the padded grid and is cropped from the same
+ *     window. Frequencies are f_k = k / (P d) with k in FFT order. The forward
+ *     DFT is unnormalised and the inverse carries 1 / (Py Px).
+ *   - AS transfer function H = exp(2 pi i z sqrt(1/lambda^2 - fx^2 - fy^2)), set
+ *     to 0 where the radicand is negative (evanescent cutoff). Fresnel transfer
+ *     function H = exp(2 pi i z / lambda) exp(-i pi lambda z (fx^2 + fy^2)).
+ *   - Gradients use the real-loss convention g = dL/dRe + i dL/dIm, so the
+ *     backward of a complex-linear map A is its adjoint A^H.
+ *   - Calls are asynchronous on the caller's CUDA stream (cudaStream_t passed as
+ *     void*, NULL = legacy default stream). Argument errors are detected on the
+ *     host before anything is launched. Nothing throws across the ABI; every
+ *     call returns a top_status and top_last_error() gives a message for the
+ *     calling thread.
+ *   - Transfer-function, lens and aperture tables are built on first use of a
+ *     parameter set and cached in the handle; the handle's workspace grows on
+ *     first use of a grid size. Make one warm-up call with each parameter set
+ *     before capturing a stream into a CUDA graph (table building and workspace
+ *     growth allocate and copy synchronously).
+ *   - Results are deterministic: batch reductions use a fixed order, no atomics.
+ *   - One handle must not be used from two host threads at the same time.
+ */
+#ifndef TOP_H_
+#define TOP_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TOP_ABI_VERSION 1
+
+typedef enum top_status {
+  TOP_OK = 0,
+  TOP_ERR_INVALID_ARG = 1, /* bad size, spacing, wavelength, pointer or alignment */
+  TOP_ERR_UNSUPPORTED = 2, /* valid request outside what the kernels implement */
+  TOP_ERR_OOM = 3,         /* device allocation failed (workspace or tables) */
+  TOP_ERR_CUDA = 4,        /* a CUDA runtime call failed */
+  TOP_ERR_TIMEOUT = 5,     /* a bounded device wait gave up */
+  TOP_ERR_INTERNAL = 6
+} top_status;
+
+/* Propagation method (§3): angular spectrum (Eq. 4-5) or Fresnel transfer function. */
+typedef enum top_method { TOP_AS = 0, TOP_FRESNEL_TF = 1 } top_method;
+
+typedef struct top_ctx* top_handle;
+
+/* Planar sampling grid shared by all fields of a call (§3: "a discrete grid that is
+ * uniformly sampled over the xy-plane"). */
+typedef struct top_grid {
+  int64_t batch;  /* number of fields (or coherence tensors), >= 1 */
+  int32_t ny, nx; /* samples per field, >= 1 */
+  double dy, dx;  /* sample spacing in metres, > 0 */
+  double pad;     /* zero-padding factor per axis, P = floor(pad*n + 0.5) >= n */
+  int32_t method; /* top_method */
+  int32_t input_repeat; /* forward calls only: input field b / input_repeat feeds output field b (0 or 1:
+                           one input per output). Broadcasts one object over consecutive wavelengths
+                           (Listing 5). Must divide batch; backward calls require 0 or 1. */
+} top_grid;
+
+/* Element modulation M(x, y) of Eq. 1, a product of the enabled factors:
+ *   TOP_MOD_COMPLEX    complex64 mask [ny][nx]
+ *   TOP_MOD_AMPLITUDE  float32 amplitude A [ny][nx]
+ *   TOP_MOD_PHASE      float32 phase phi [ny][nx], factor exp(i phi)
+ *   TOP_MOD_LENS       thin lens exp(-i pi (x^2 + y^2) / (lambda f)) (§2 Lens, §5.4)
+ *   TOP_MOD_CIRC       circular aperture: 1 where x^2 + y^2 <= R^2, else 0 (§5.4)
+ * Sample positions are x_i = (i - (nx-1)/2) dx, y_j = (j - (ny-1)/2) dy. */
+#define TOP_MOD_COMPLEX 0x1u
+#define TOP_MOD_AMPLITUDE 0x2u
+#define TOP_MOD_PHASE 0x4u
+#define TOP_MOD_LENS 0x8u
+#define TOP_MOD_CIRC 0x10u
+
+typedef struct top_mod {
+  uint32_t flags;         /* OR of TOP_MOD_* (0 = identity) */
+  int32_t reserved;
+  const void* mask;       /* TOP_MOD_COMPLEX: complex64, device */
+  const float* amplitude; /* TOP_MOD_AMPLITUDE: float32, device */
+  const float* phase;     /* TOP_MOD_PHASE: float32, device */
+  int64_t batch_stride;   /* elements between the masks of consecutive fields; 0 = one mask for all */
+  double focal_length;    /* TOP_MOD_LENS: f in metres (non-zero) */
+  double radius;          /* TOP_MOD_CIRC: R in metres (>= 0) */
+} top_mod;
+
+/* Gradients of a modulation's parameters (backward of Eq. 1), accumulated over the
+ * batch in a fixed order when the mask is shared (batch_stride == 0), per field
+ * otherwise. Any output pointer may be NULL. */
+typedef struct top_mod_grads {
+  const void* saved_in; /* complex64 [batch][ny][nx]: the field x that entered M in the forward pass */
+  float* grad_phase;    /* dL/dphi, float32 */
+  float* grad_amplitude;/* dL/dA, float32 */
+  void* grad_mask;      /* dL/dRe M + i dL/dIm M, complex64 */
+} top_mod_grads;
+
+/* ---------------------------------------------------------------- handle and errors */
+
+/* Create a handle bound to CUDA device `device`. Returns TOP_ERR_CUDA without a GPU. */
+top_status top_create(top_handle* out, int device);
+/* Synchronise the device, free the workspace and cached tables, destroy the handle. */
+top_status top_destroy(top_handle h);
+/* Message of the last failing call on this host thread ("" if none). Never NULL. */
+const char* top_last_error(void);
+/* Static name of a status code. */
+const char* top_status_string(top_status s);
+/* TOP_ABI_VERSION of the loaded library. */
+int top_version(void);
+/* Cap on the handle's workspace in bytes (default 8 GiB); larger batches run in chunks. */
+top_status top_set_workspace_limit(top_handle h, uint64_t bytes);
+
+/* Host-only plan query: padded sizes and per-field workspace bytes of a propagation.
+ * Validates `g` exactly like the propagation calls. */
+top_status top_plan_query(const top_grid* g, int64_t* py, int64_t* px, uint64_t* workspace_per_field);
+
+/* Eq. 6: z_critical = L dx / lambda. AS is the accurate method for z < z_critical. */
+double top_zcritical(double L, double dx, double lambda);
+
+/* ---------------------------------------------------------------- propagation (Eq. 4-5) */
+
+/* out = post * P_z(pre * in) for every field (Eq. 1 then Eq. 4, then Eq. 1).
+ * in, out: complex64 [batch][ny][nx] device (in == out allowed).
+ * lambda, z: host arrays of n_lz values, n_lz == 1 (shared) or == batch (per field).
+ * pre, post: modulations or NULL. */
+top_status top_propagate(top_handle h, const top_grid* g, const void* in, void* out,
+                         const double* lambda, const double* z, int64_t n_lz,
+                         const top_mod* pre, const top_mod* post, void* stream);
+
+/* Backward of top_propagate (§4): grad_in = conj(pre) * P_z^H(conj(post) * grad_out),
+ * P_z^H using conj(H). grad_in may be NULL when only `pre_grads` is wanted.
+ * pre_grads (may be NULL): gradients of pre's phase / amplitude / mask; needs
+ * pre_grads->saved_in = the `in` of the forward call. */
+top_status top_propagate_backward(top_handle h, const top_grid* g, const void* grad_out, void* grad_in,
+                                  const double* lambda, const double* z, int64_t n_lz,
+                                  const top_mod* pre, const top_mod* post,
+                                  const top_mod_grads* pre_grads, void* stream);
+
+/* Detector intensity fused into the propagation (Eq. 14):
+ * I[b / group] = sum over each consecutive group of `group` fields of w_b |post * P_z(pre * in_b)|^2.
+ * intensity: float32 [batch/group][ny][nx]; weights: device float32 [batch] or NULL (all 1);
+ * field_out: complex64 [batch][ny][nx] or NULL, receives post * P_z(pre * in) (needed by the backward). */
+top_status top_propagate_intensity(top_handle h, const top_grid* g, const void* in, void* field_out,
+                                   float* intensity, int64_t group, const float* weights,
+                                   const double* lambda, const double* z, int64_t n_lz,
+                                   const top_mod* pre, const top_mod* post, void* stream);
+
+/* Backward of top_propagate_intensity: with psi = the saved field_out,
+ * grad_in = conj(pre) * P_z^H(conj(post) * 2 w_b grad_I[b/group] psi_b); pre_grads as in
+ * top_propagate_backward. grad_intensity: float32 [batch/group][ny][nx]. */
+top_status top_propagate_intensity_backward(top_handle h, const top_grid* g, const void* field,
+                                            const float* grad_intensity, void* grad_in, int64_t group,
+                                            const float* weights, const double* lambda, const double* z,
+                                            int64_t n_lz, const top_mod* pre, const top_mod* post,
+                                            const top_mod_grads* pre_grads, void* stream);
+
+/* ---------------------------------------------------------------- modulation (Eq. 1) */
+
+/* out = M * in, point-wise (in == out allowed). lambda (host, n_lz values) is used by lenses only. */
+top_status top_modulate(top_handle h, const top_grid* g, const top_mod* mod, const void* in, void* out,
+                        const double* lambda, int64_t n_lz, void* stream);
+
+/* Backward of top_modulate: grad_in = conj(M) * grad_out (grad_in may be NULL) and the
+ * parameter gradients of `grads` (grads->saved_in = the forward `in`). */
+top_status top_modulate_backward(top_handle h, const top_grid* g, const top_mod* mod, const void* grad_out,
+                                 void* grad_in, const top_mod_grads* grads, const double* lambda,
+                                 int64_t n_lz, void* stream);
+
+/* ---------------------------------------------------------------- losses */
+
+/* L = mean((I - T)^2) over n elements and grad = 2 (I - T) / n (float32, device; grad may be
+ * NULL). loss: device double[1]. Deterministic two-stage reduction. */
+top_status top_mse_loss(top_handle h, int64_t n, const float* intensity, const float* target, double* loss,
+                        float* grad, void* stream);
+
+/* ---------------------------------------------------------------- mutual coherence (§5.2) */
+
+/* Gamma_out = P_z (M(r1) M*(r2) Gamma_in) P_z^H  (Eq. 12 then Eq. 13): h_z acts on
+ * (y1, x1) and h_z* on (y2, x2). gamma_in, gamma_out: complex64
+ * [batch][ny][nx][ny][nx] device (distinct buffers). mask: M or NULL. lambda, z: host,
+ * one value each (shared by the batch). Uses workspace of one Gamma tensor. */
+top_status top_propagate_coherence(top_handle h, const top_grid* g, const void* gamma_in, void* gamma_out,
+                                   const double* lambda, const double* z, const top_mod* mask, void* stream);
+
+/* Backward of top_propagate_coherence: grad_in = M*(r1) M(r2) (P_z^H G P_z) (grad_in may be
+ * NULL) and the gradients of the mask parameters (grads->saved_in = the forward gamma_in). */
+top_status top_propagate_coherence_backward(top_handle h, const top_grid* g, const void* grad_out,
+                                            void* grad_in, const double* lambda, const double* z,
+                                            const top_mod* mask, const top_mod_grads* grads, void* stream);
+
+/* Intensity Gamma(r, r) of each coherence tensor: float32 [batch][ny][nx]. */
+top_status top_coherence_intensity(top_handle h, const top_grid* g, const void* gamma, float* intensity,
+                                   void* stream);
+
+/* Backward of top_coherence_intensity: grad_gamma = diag(grad_I) (all other elements 0). */
+top_status top_coherence_intensity_backward(top_handle h, const top_grid* g, const float* grad_intensity,
+                                            void* grad_gamma, void* stream);
+
+/* ---------------------------------------------------------------- instrumentation */
+
+/* Enable (1) or disable (0) CUDA-event timing of every kernel launched by the handle. */
+top_status top_profile_enable(top_handle h, int enable);
+/* Drain the recorded events (synchronising on them) and return per-kind totals.
+ * kinds (up to `cap` entries) get static names, ms the summed milliseconds and count the
+ * launches since the last call; *n receives the number of kinds written. */
+top_status top_profile_read(top_handle h, int cap, const char** kinds, double* ms, int64_t* count, int* n);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TOP_H_ */

@@ -1,0 +1,354 @@
+"""Python binding of the C ABI with the same call names, for torch CUDA tensors.
+
+Argument marshalling only: every step of the computation runs in libtop.so's
+CUDA kernels. Tensors must live on a CUDA device; fields are complex64
+[batch, ny, nx] (a single [ny, nx] field is treated as batch 1), phases,
+amplitudes and intensities float32. Calls run on torch's current stream.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import threading
+from dataclasses import dataclass
+from typing import Optional, Sequence
+
+import torch
+
+from . import _lib
+from ._lib import TopGrid, TopMod, TopModGrads, check, doubles
+
+METHODS = {"as": _lib.TOP_AS, "angular_spectrum": _lib.TOP_AS, "fresnel": _lib.TOP_FRESNEL_TF,
+           "fresnel_tf": _lib.TOP_FRESNEL_TF, _lib.TOP_AS: _lib.TOP_AS, _lib.TOP_FRESNEL_TF: _lib.TOP_FRESNEL_TF}
+
+_handles: dict = {}
+_handle_lock = threading.Lock()
+
+
+def handle(device: Optional[torch.device] = None) -> C.c_void_p:
+    """The library handle of a CUDA device (created on first use, kept for the process)."""
+    lib = _lib.load()
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    idx = dev.index if dev.index is not None else torch.cuda.current_device()
+    with _handle_lock:
+        h = _handles.get(idx)
+        if h is None:
+            h = C.c_void_p()
+            check(lib.top_create(C.byref(h), idx))
+            _handles[idx] = h
+    return h
+
+
+def _stream(t: torch.Tensor) -> C.c_void_p:
+    return C.c_void_p(torch.cuda.current_stream(t.device).cuda_stream)
+
+
+def _ptr(t: Optional[torch.Tensor]) -> Optional[int]:
+    return None if t is None else t.data_ptr()
+
+
+def _field(t: torch.Tensor, name: str) -> torch.Tensor:
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != torch.complex64:
+        raise ValueError(f"{name} must be complex64")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t
+
+
+def _real(t: Optional[torch.Tensor], name: str) -> Optional[torch.Tensor]:
+    if t is None:
+        return None
+    if not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous float32 CUDA tensor")
+    return t
+
+
+def _shape3(t: torch.Tensor):
+    if t.dim() == 2:
+        return 1, t.shape[0], t.shape[1]
+    if t.dim() == 3:
+        return t.shape[0], t.shape[1], t.shape[2]
+    raise ValueError("fields must be [ny, nx] or [batch, ny, nx]")
+
+
+def make_grid(batch: int, ny: int, nx: int, dy: float, dx: float, pad: float = 2.0, method="as",
+              input_repeat: int = 1) -> TopGrid:
+    return TopGrid(int(batch), int(ny), int(nx), float(dy), float(dx), float(pad), METHODS[method],
+                   int(input_repeat))
+
+
+@dataclass
+class Modulation:
+    """Element modulation of Eq. 1: product of the factors that are set.
+
+    mask: complex64 [ny, nx] or [batch, ny, nx]; amplitude / phase: float32 of the same shapes;
+    focal_length: thin lens f (m); radius: circular aperture radius R (m).
+    """
+    mask: Optional[torch.Tensor] = None
+    amplitude: Optional[torch.Tensor] = None
+    phase: Optional[torch.Tensor] = None
+    focal_length: Optional[float] = None
+    radius: Optional[float] = None
+
+    def to_c(self) -> TopMod:
+        m = TopMod()
+        flags = 0
+        stride = 0
+        for t, flag, name in ((self.mask, _lib.TOP_MOD_COMPLEX, "mask"),
+                              (self.amplitude, _lib.TOP_MOD_AMPLITUDE, "amplitude"),
+                              (self.phase, _lib.TOP_MOD_PHASE, "phase")):
+            if t is None:
+                continue
+            if flag == _lib.TOP_MOD_COMPLEX:
+                _field(t, name)
+            else:
+                _real(t, name)
+            flags |= flag
+            s = t.shape[-1] * t.shape[-2] if t.dim() == 3 else 0
+            stride = max(stride, s)
+        m.mask = _ptr(self.mask)
+        m.amplitude = _ptr(self.amplitude)
+        m.phase = _ptr(self.phase)
+        if self.focal_length is not None:
+            flags |= _lib.TOP_MOD_LENS
+            m.focal_length = float(self.focal_length)
+        if self.radius is not None:
+            flags |= _lib.TOP_MOD_CIRC
+            m.radius = float(self.radius)
+        m.flags = flags
+        m.batch_stride = stride
+        return m
+
+
+def _mod(m: Optional[Modulation]):
+    return None if m is None else C.byref(m.to_c())
+
+
+def _lz(lam, z, batch):
+    lam = [lam] if isinstance(lam, (int, float)) else list(lam)
+    zs = [z] if isinstance(z, (int, float)) else list(z)
+    n = max(len(lam), len(zs))
+    if len(lam) == 1 and n > 1:
+        lam = lam * n
+    if len(zs) == 1 and n > 1:
+        zs = zs * n
+    return doubles(lam), doubles(zs), n
+
+
+def top_propagate(field: torch.Tensor, dy: float, dx: float, lam, z, pad: float = 2.0, method="as",
+                  pre: Optional[Modulation] = None, post: Optional[Modulation] = None,
+                  out: Optional[torch.Tensor] = None, input_repeat: int = 1) -> torch.Tensor:
+    """out = post * P_z(pre * field) (Eq. 1 and Eq. 4-5).
+
+    With input_repeat = k each input field feeds k consecutive output fields (batch_out = k batch_in).
+    """
+    _field(field, "field")
+    b, ny, nx = _shape3(field)
+    b *= input_repeat
+    if out is None:
+        out = torch.empty((b, ny, nx), dtype=field.dtype, device=field.device)
+    else:
+        _field(out, "out")
+    lams, zs, n = _lz(lam, z, b)
+    g = make_grid(b, ny, nx, dy, dx, pad, method, input_repeat)
+    check(_lib.load().top_propagate(handle(field.device), C.byref(g), field.data_ptr(), out.data_ptr(), lams, zs, n,
+                                    _mod(pre), _mod(post), _stream(field)))
+    return out
+
+
+def top_propagate_backward(grad_out: torch.Tensor, dy: float, dx: float, lam, z, pad: float = 2.0, method="as",
+                           pre: Optional[Modulation] = None, post: Optional[Modulation] = None,
+                           saved_in: Optional[torch.Tensor] = None, want_grad_in: bool = True,
+                           grad_phase: Optional[torch.Tensor] = None, grad_amplitude: Optional[torch.Tensor] = None,
+                           grad_mask: Optional[torch.Tensor] = None) -> Optional[torch.Tensor]:
+    """Adjoint of top_propagate; fills grad_phase / grad_amplitude / grad_mask of ``pre`` if given."""
+    _field(grad_out, "grad_out")
+    b, ny, nx = _shape3(grad_out)
+    grad_in = torch.empty_like(grad_out) if want_grad_in else None
+    lams, zs, n = _lz(lam, z, b)
+    g = make_grid(b, ny, nx, dy, dx, pad, method)
+    grads = None
+    if grad_phase is not None or grad_amplitude is not None or grad_mask is not None:
+        if saved_in is None:
+            raise ValueError("modulation gradients need saved_in (the forward input)")
+        _field(saved_in, "saved_in")
+        grads = C.byref(TopModGrads(saved_in.data_ptr(), _ptr(_real(grad_phase, "grad_phase")),
+                                    _ptr(_real(grad_amplitude, "grad_amplitude")), _ptr(grad_mask)))
+    check(_lib.load().top_propagate_backward(handle(grad_out.device), C.byref(g), grad_out.data_ptr(), _ptr(grad_in),
+                                             lams, zs, n, _mod(pre), _mod(post), grads, _stream(grad_out)))
+    return grad_in
+
+
+def top_propagate_intensity(field: torch.Tensor, dy: float, dx: float, lam, z, pad: float = 2.0, method="as",
+                            group: int = 1, weights: Optional[torch.Tensor] = None,
+                            pre: Optional[Modulation] = None, post: Optional[Modulation] = None,
+                            keep_field: bool = False, input_repeat: int = 1):
+    """I[b/group] = sum_group w_b |post * P_z(pre * field_b)|^2 (Eq. 14); returns (I, field or None)."""
+    _field(field, "field")
+    b, ny, nx = _shape3(field)
+    b *= input_repeat
+    inten = torch.empty((b // group, ny, nx), dtype=torch.float32, device=field.device)
+    fout = torch.empty((b, ny, nx), dtype=field.dtype, device=field.device) if keep_field else None
+    lams, zs, n = _lz(lam, z, b)
+    g = make_grid(b, ny, nx, dy, dx, pad, method, input_repeat)
+    check(_lib.load().top_propagate_intensity(handle(field.device), C.byref(g), field.data_ptr(), _ptr(fout),
+                                              inten.data_ptr(), group, _ptr(_real(weights, "weights")), lams, zs,
+                                              n, _mod(pre), _mod(post), _stream(field)))
+    return inten, fout
+
+
+def top_propagate_intensity_backward(field: torch.Tensor, grad_intensity: torch.Tensor, dy: float, dx: float, lam,
+                                     z, pad: float = 2.0, method="as", group: int = 1,
+                                     weights: Optional[torch.Tensor] = None, pre: Optional[Modulation] = None,
+                                     post: Optional[Modulation] = None, saved_in: Optional[torch.Tensor] = None,
+                                     want_grad_in: bool = True, grad_phase: Optional[torch.Tensor] = None,
+                                     grad_amplitude: Optional[torch.Tensor] = None,
+                                     grad_mask: Optional[torch.Tensor] = None) -> Optional[torch.Tensor]:
+    """Backward of top_propagate_intensity given the saved output field."""
+    _field(field, "field")
+    _real(grad_intensity, "grad_intensity")
+    b, ny, nx = _shape3(field)
+    grad_in = torch.empty_like(field) if want_grad_in else None
+    lams, zs, n = _lz(lam, z, b)
+    g = make_grid(b, ny, nx, dy, dx, pad, method)
+    grads = None
+    if grad_phase is not None or grad_amplitude is not None or grad_mask is not None:
+        _field(saved_in, "saved_in")
+        grads = C.byref(TopModGrads(saved_in.data_ptr(), _ptr(_real(grad_phase, "grad_phase")),
+                                    _ptr(_real(grad_amplitude, "grad_amplitude")), _ptr(grad_mask)))
+    check(_lib.load().top_propagate_intensity_backward(handle(field.device), C.byref(g), field.data_ptr(),
+                                                       grad_intensity.data_ptr(), _ptr(grad_in), group,
+                                                       _ptr(_real(weights, "weights")), lams, zs, n, _mod(pre),
+                                                       _mod(post), grads, _stream(field)))
+    return grad_in
+
+
+def top_modulate(field: torch.Tensor, mod: Modulation, dy: float, dx: float, lam=1.0,
+                 out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """out = M * field (Eq. 1)."""
+    _field(field, "field")
+    b, ny, nx = _shape3(field)
+    out = torch.empty_like(field) if out is None else _field(out, "out")
+    lams, _, n = _lz(lam, 0.0, b)
+    g = make_grid(b, ny, nx, dy, dx, 1.0, "as")
+    check(_lib.load().top_modulate(handle(field.device), C.byref(g), C.byref(mod.to_c()), field.data_ptr(),
+                                   out.data_ptr(), lams, n, _stream(field)))
+    return out
+
+
+def top_modulate_backward(grad_out: torch.Tensor, mod: Modulation, dy: float, dx: float, lam=1.0,
+                          saved_in: Optional[torch.Tensor] = None, want_grad_in: bool = True,
+                          grad_phase: Optional[torch.Tensor] = None, grad_amplitude: Optional[torch.Tensor] = None,
+                          grad_mask: Optional[torch.Tensor] = None) -> Optional[torch.Tensor]:
+    """Backward of top_modulate: conj(M) grad_out and the gradients of M's parameters."""
+    _field(grad_out, "grad_out")
+    b, ny, nx = _shape3(grad_out)
+    grad_in = torch.empty_like(grad_out) if want_grad_in else None
+    lams, _, n = _lz(lam, 0.0, b)
+    g = make_grid(b, ny, nx, dy, dx, 1.0, "as")
+    grads = None
+    if grad_phase is not None or grad_amplitude is not None or grad_mask is not None:
+        _field(saved_in, "saved_in")
+        grads = C.byref(TopModGrads(saved_in.data_ptr(), _ptr(_real(grad_phase, "grad_phase")),
+                                    _ptr(_real(grad_amplitude, "grad_amplitude")), _ptr(grad_mask)))
+    check(_lib.load().top_modulate_backward(handle(grad_out.device), C.byref(g), C.byref(mod.to_c()),
+                                            grad_out.data_ptr(), _ptr(grad_in), grads, lams, n, _stream(grad_out)))
+    return grad_in
+
+
+def top_mse_loss(intensity: torch.Tensor, target: torch.Tensor, want_grad: bool = True):
+    """(loss as a float64 device scalar, dL/dI or None) for L = mean((I - T)^2)."""
+    _real(intensity, "intensity")
+    _real(target, "target")
+    loss = torch.empty(2, dtype=torch.float64, device=intensity.device)  # 16-byte aligned scalar
+    grad = torch.empty_like(intensity) if want_grad else None
+    check(_lib.load().top_mse_loss(handle(intensity.device), intensity.numel(), intensity.data_ptr(),
+                                   target.data_ptr(), loss.data_ptr(), _ptr(grad), _stream(intensity)))
+    return loss[0], grad
+
+
+def _coh_grid(gamma: torch.Tensor, dy, dx, pad, method) -> TopGrid:
+    if gamma.dim() == 4:
+        b, ny, nx = 1, gamma.shape[0], gamma.shape[1]
+    elif gamma.dim() == 5:
+        b, ny, nx = gamma.shape[0], gamma.shape[1], gamma.shape[2]
+    else:
+        raise ValueError("coherence tensors are [ny, nx, ny, nx] or [batch, ny, nx, ny, nx]")
+    return make_grid(b, ny, nx, dy, dx, pad, method)
+
+
+def top_propagate_coherence(gamma: torch.Tensor, dy: float, dx: float, lam: float, z: float, pad: float = 2.0,
+                            method="as", mask: Optional[Modulation] = None) -> torch.Tensor:
+    """Gamma_z = P (M M* Gamma) P^H (Eq. 12-13)."""
+    _field(gamma, "gamma")
+    out = torch.empty_like(gamma)
+    g = _coh_grid(gamma, dy, dx, pad, method)
+    check(_lib.load().top_propagate_coherence(handle(gamma.device), C.byref(g), gamma.data_ptr(), out.data_ptr(),
+                                              doubles([lam]), doubles([z]), _mod(mask), _stream(gamma)))
+    return out
+
+
+def top_propagate_coherence_backward(grad_out: torch.Tensor, dy: float, dx: float, lam: float, z: float,
+                                     pad: float = 2.0, method="as", mask: Optional[Modulation] = None,
+                                     saved_in: Optional[torch.Tensor] = None, want_grad_in: bool = True,
+                                     grad_phase: Optional[torch.Tensor] = None,
+                                     grad_amplitude: Optional[torch.Tensor] = None,
+                                     grad_mask: Optional[torch.Tensor] = None) -> Optional[torch.Tensor]:
+    _field(grad_out, "grad_out")
+    grad_in = torch.empty_like(grad_out) if want_grad_in else None
+    g = _coh_grid(grad_out, dy, dx, pad, method)
+    grads = None
+    if grad_phase is not None or grad_amplitude is not None or grad_mask is not None:
+        _field(saved_in, "saved_in")
+        grads = C.byref(TopModGrads(saved_in.data_ptr(), _ptr(_real(grad_phase, "grad_phase")),
+                                    _ptr(_real(grad_amplitude, "grad_amplitude")), _ptr(grad_mask)))
+    check(_lib.load().top_propagate_coherence_backward(handle(grad_out.device), C.byref(g), grad_out.data_ptr(),
+                                                       _ptr(grad_in), doubles([lam]), doubles([z]), _mod(mask),
+                                                       grads, _stream(grad_out)))
+    return grad_in
+
+
+def top_coherence_intensity(gamma: torch.Tensor) -> torch.Tensor:
+    _field(gamma, "gamma")
+    g = _coh_grid(gamma, 1.0, 1.0, 1.0, "as")
+    out = torch.empty((g.batch, g.ny, g.nx), dtype=torch.float32, device=gamma.device)
+    check(_lib.load().top_coherence_intensity(handle(gamma.device), C.byref(g), gamma.data_ptr(), out.data_ptr(),
+                                              _stream(gamma)))
+    return out.reshape(gamma.shape[:-2]) if gamma.dim() == 4 else out
+
+
+def top_coherence_intensity_backward(grad_intensity: torch.Tensor, like: torch.Tensor) -> torch.Tensor:
+    _real(grad_intensity, "grad_intensity")
+    g = _coh_grid(like, 1.0, 1.0, 1.0, "as")
+    out = torch.empty_like(like)
+    check(_lib.load().top_coherence_intensity_backward(handle(like.device), C.byref(g), grad_intensity.data_ptr(),
+                                                       out.data_ptr(), _stream(like)))
+    return out
+
+
+def top_plan_query(batch: int, ny: int, nx: int, dy: float, dx: float, pad: float = 2.0, method="as"):
+    """(Py, Px, workspace bytes per field); host only, no GPU needed."""
+    g = make_grid(batch, ny, nx, dy, dx, pad, method)
+    py, px, ws = C.c_int64(), C.c_int64(), C.c_uint64()
+    check(_lib.load().top_plan_query(C.byref(g), C.byref(py), C.byref(px), C.byref(ws)))
+    return py.value, px.value, ws.value
+
+
+def top_zcritical(L: float, dx: float, lam: float) -> float:
+    return _lib.load().top_zcritical(L, dx, lam)
+
+
+def profile_enable(enable: bool = True, device=None) -> None:
+    check(_lib.load().top_profile_enable(handle(device), 1 if enable else 0))
+
+
+def profile_read(device=None) -> dict:
+    """{kernel kind: (milliseconds, launches)} accumulated since the last read (synchronises)."""
+    cap = 8
+    kinds = (C.c_char_p * cap)()
+    ms = (C.c_double * cap)()
+    cnt = (C.c_int64 * cap)()
+    n = C.c_int()
+    check(_lib.load().top_profile_read(handle(device), cap, kinds, ms, cnt, C.byref(n)))
+    return {kinds[i].decode(): (ms[i], cnt[i]) for i in range(n.value)}

@@ -1,0 +1,1207 @@
+// C ABI of the propagation library: handle, argument validation, float64 table
+// caches, workspace management and the launch sequence of each call.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <numeric>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "top_aux.h"
+#include "top_dispatch.h"
+#include "top_internal.h"
+
+using namespace top;
+
+// ============================================================================= errors
+
+namespace {
+
+thread_local std::string t_last_error;
+
+top_status fail(top_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  t_last_error = buf;
+  return s;
+}
+
+top_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(e == cudaErrorMemoryAllocation ? TOP_ERR_OOM : TOP_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define TOP_CUDA(call, what)                         \
+  do {                                               \
+    cudaError_t e_ = (call);                         \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+#define TOP_TRY(call)                    \
+  do {                                   \
+    top_status s_ = (call);              \
+    if (s_ != TOP_OK) return s_;         \
+  } while (0)
+
+uint64_t bits(double d) {
+  uint64_t u;
+  std::memcpy(&u, &d, sizeof u);
+  return u;
+}
+
+}  // namespace
+
+// ============================================================================= handle
+
+struct TransferEntry {
+  float4* hx = nullptr;
+  float4* hy = nullptr;
+  int* kcut = nullptr;
+  float2 cg;
+  float cr;
+};
+
+struct top_ctx {
+  int device = 0;
+  uint64_t ws_limit = 8ull << 30;
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  void* coh = nullptr;  // one coherence tensor of scratch for the transposes
+  size_t coh_bytes = 0;
+  std::vector<void*> allocs;  // cached tables, freed with the handle
+  std::map<int, float2*> eng_tw;
+  std::map<int, float2*> split_tw;
+  std::map<std::array<uint64_t, 7>, TransferEntry> transfer;
+  std::map<std::array<uint64_t, 4>, float2*> lens;
+  std::map<std::array<uint64_t, 5>, int2*> circ;
+  // instrumentation
+  bool prof = false;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
+  std::vector<cudaEvent_t> pool;
+  double prof_ms[KK_COUNT] = {};
+  long long prof_cnt[KK_COUNT] = {};
+};
+
+namespace {
+
+top_status bind(top_handle h) {
+  TOP_CUDA(cudaSetDevice(h->device), "cudaSetDevice");
+  return TOP_OK;
+}
+
+template <class T>
+top_status upload(top_handle h, const std::vector<T>& host, T** out) {
+  void* p = nullptr;
+  TOP_CUDA(cudaMalloc(&p, std::max<size_t>(sizeof(T), host.size() * sizeof(T))), "cudaMalloc(table)");
+  h->allocs.push_back(p);
+  if (!host.empty()) TOP_CUDA(cudaMemcpy(p, host.data(), host.size() * sizeof(T), cudaMemcpyHostToDevice), "cudaMemcpy(table)");
+  *out = static_cast<T*>(p);
+  return TOP_OK;
+}
+
+top_status ensure_workspace(top_handle h, size_t bytes) {
+  if (bytes <= h->ws_bytes) return TOP_OK;
+  if (h->ws) {
+    TOP_CUDA(cudaDeviceSynchronize(), "cudaDeviceSynchronize(workspace growth)");
+    cudaFree(h->ws);
+    h->ws = nullptr;
+    h->ws_bytes = 0;
+  }
+  const size_t rounded = (bytes + (1u << 20) - 1) & ~size_t((1u << 20) - 1);
+  cudaError_t e = cudaMalloc(&h->ws, rounded);
+  if (e != cudaSuccess) {
+    h->ws = nullptr;
+    return cuda_fail(e, "cudaMalloc(workspace)");
+  }
+  h->ws_bytes = rounded;
+  return TOP_OK;
+}
+
+cudaEvent_t take_event(top_handle h) {
+  if (!h->pool.empty()) {
+    cudaEvent_t e = h->pool.back();
+    h->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Launch with optional CUDA-event timing on the launching stream.
+template <class F>
+top_status timed(top_handle h, int kind, cudaStream_t st, const char* what, F&& launch) {
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (h->prof) {
+    a = take_event(h);
+    b = take_event(h);
+    cudaEventRecord(a, st);
+  }
+  cudaError_t e = launch();
+  if (h->prof) {
+    cudaEventRecord(b, st);
+    h->pending.push_back({kind, {a, b}});
+  }
+  if (e != cudaSuccess) return cuda_fail(e, what);
+  return TOP_OK;
+}
+
+// ============================================================================= engines and tables
+
+bool find_engine(int M, EngineInfo* info) {
+  return engine_info_small(M, info) || engine_info_mid(M, info) || engine_info_m1024(M, info) ||
+         engine_info_large(M, info) || engine_info_mixed(M, info);
+}
+
+cudaError_t launch_pass(int kind, int M, const PassParams& p, cudaStream_t s) {
+  bool found = false;
+  cudaError_t e = launch_pass_small(kind, M, p, s, &found);
+  if (found) return e;
+  e = launch_pass_mid(kind, M, p, s, &found);
+  if (found) return e;
+  e = launch_pass_m1024(kind, M, p, s, &found);
+  if (found) return e;
+  e = launch_pass_large(kind, M, p, s, &found);
+  if (found) return e;
+  e = launch_pass_mixed(kind, M, p, s, &found);
+  if (found) return e;
+  return cudaErrorInvalidValue;
+}
+
+// (cos, sin) of pi * x for a float64 x, with x reduced modulo 2 exactly (fmod is exact).
+void cis_pi(double x, double* c, double* s) {
+  double r = std::fmod(x, 2.0);
+  if (r > 1.0) r -= 2.0;
+  if (r < -1.0) r += 2.0;
+  *c = std::cos(M_PI * r);
+  *s = std::sin(M_PI * r);
+}
+
+// exp(-2 pi i m / n) for integers, m reduced modulo n first
+float2 unit_root(long long m, long long n) {
+  m %= n;
+  if (m < 0) m += n;
+  double c, s;
+  cis_pi(-2.0 * double(m) / double(n), &c, &s);
+  return make_float2(float(c), float(s));
+}
+
+// Stage twiddles w_{R SP}^{i j} of an engine plan, in the layout the device reads.
+top_status engine_twiddles(top_handle h, int M, const float2** out) {
+  auto it = h->eng_tw.find(M);
+  if (it != h->eng_tw.end()) {
+    *out = it->second;
+    return TOP_OK;
+  }
+  EngineInfo info;
+  if (!find_engine(M, &info)) return fail(TOP_ERR_UNSUPPORTED, "no FFT engine for line length %d", M);
+  std::vector<float2> tw(std::max(1, info.tw_size));
+  size_t off = 0;
+  for (int s = 0; s < info.NS; ++s) {
+    int sp = 1;
+    for (int i = s + 1; i < info.NS; ++i) sp *= info.R[i];
+    if (sp <= 1) continue;
+    const int r = info.R[s], L = r * sp;
+    for (int j = 1; j < r; ++j)
+      for (int i = 0; i < sp; ++i) tw[off + size_t(j - 1) * sp + i] = unit_root((long long)i * j, L);
+    off += size_t(r - 1) * sp;
+  }
+  if ((int)off > std::max(1, info.tw_size)) return fail(TOP_ERR_INTERNAL, "twiddle table size mismatch");
+  float2* d = nullptr;
+  TOP_TRY(upload(h, tw, &d));
+  h->eng_tw[M] = d;
+  *out = d;
+  return TOP_OK;
+}
+
+// exp(-2 pi i p / P) for p < P / 2: the twiddles that fold and unfold the two halves.
+top_status split_twiddles(top_handle h, int P, const float2** out) {
+  auto it = h->split_tw.find(P);
+  if (it != h->split_tw.end()) {
+    *out = it->second;
+    return TOP_OK;
+  }
+  std::vector<float2> w(P / 2);
+  for (int p = 0; p < P / 2; ++p) w[p] = unit_root(p, P);
+  float2* d = nullptr;
+  TOP_TRY(upload(h, w, &d));
+  h->split_tw[P] = d;
+  *out = d;
+  return TOP_OK;
+}
+
+long long signed_index(long long k, long long P) { return k < (P + 1) / 2 ? k : k - P; }
+double freq(long long k, long long P, double d) { return double(signed_index(k, P)) / (double(P) * d); }
+
+// Separable transfer-function tables for one (lambda, z) (Eq. 5 and the Fresnel form), float64.
+top_status transfer_tables(top_handle h, int Py, int Px, double dy, double dx, double lam, double z, int method,
+                           TransferEntry* out) {
+  const std::array<uint64_t, 7> key = {uint64_t(Py), uint64_t(Px), bits(dy), bits(dx), bits(lam), bits(z),
+                                       uint64_t(method)};
+  auto it = h->transfer.find(key);
+  if (it != h->transfer.end()) {
+    *out = it->second;
+    return TOP_OK;
+  }
+  TransferEntry te;
+  auto axis = [&](int P, double d, std::vector<float4>& t) {
+    t.resize(P);
+    for (int k = 0; k < P; ++k) {
+      const double f = freq(k, P, d);
+      double c, s;
+      cis_pi(-lam * z * f * f, &c, &s);  // exp(-i pi lambda z f^2)
+      t[k] = make_float4(float(c), float(s), float(lam * lam * f * f), 0.f);
+    }
+  };
+  std::vector<float4> hx, hy;
+  axis(Px, dx, hx);
+  axis(Py, dy, hy);
+  TOP_TRY(upload(h, hx, &te.hx));
+  TOP_TRY(upload(h, hy, &te.hy));
+  double c, s;
+  cis_pi(2.0 * z / lam, &c, &s);  // exp(2 pi i z / lambda)
+  const double norm = 1.0 / (double(Py) * double(Px));
+  te.cg = make_float2(float(c * norm), float(s * norm));
+  te.cr = float(2.0 * M_PI * z / lam);
+  if (method == TOP_AS) {
+    // evanescent cutoff: the radicand ((1/lambda^2) - fx^2) - fy^2 must be >= 0; it falls
+    // monotonically in |fy|, so each column keeps |signed ky| <= kcut[kx].
+    const double inv_l2 = 1.0 / (lam * lam);
+    const double fxm = freq(Px / 2, Px, dx), fym = freq(Py / 2, Py, dy);
+    const bool any_evanescent = ((inv_l2 - fxm * fxm) - fym * fym) < 0.0;
+    if (any_evanescent) {
+      std::vector<int> kc(Px);
+      for (int k = 0; k < Px; ++k) {
+        const double fx = freq(k, Px, dx);
+        const double a = inv_l2 - fx * fx;
+        int best = -1;
+        for (long long sy = 0; sy <= Py / 2; ++sy) {
+          const double fy = double(sy) / (double(Py) * dy);
+          if (a - fy * fy >= 0.0) best = int(sy); else break;
+        }
+        kc[k] = best;
+      }
+      TOP_TRY(upload(h, kc, &te.kcut));
+    }
+  }
+  h->transfer[key] = te;
+  *out = te;
+  return TOP_OK;
+}
+
+// Thin-lens factor table exp(-i pi s^2 / (lambda f)) along one axis (s = (i - (n-1)/2) d).
+top_status lens_table(top_handle h, int n, double d, double lam, double f, const float2** out) {
+  const std::array<uint64_t, 4> key = {uint64_t(n), bits(d), bits(lam), bits(f)};
+  auto it = h->lens.find(key);
+  if (it != h->lens.end()) {
+    *out = it->second;
+    return TOP_OK;
+  }
+  std::vector<float2> t(n);
+  for (int i = 0; i < n; ++i) {
+    const double s = (double(i) - double(n - 1) / 2.0) * d;
+    double c, sn;
+    cis_pi(-(s * s) / (lam * f), &c, &sn);
+    t[i] = make_float2(float(c), float(sn));
+  }
+  float2* dp = nullptr;
+  TOP_TRY(upload(h, t, &dp));
+  h->lens[key] = dp;
+  *out = dp;
+  return TOP_OK;
+}
+
+// Circular aperture: per row the inclusive x range with x^2 + y^2 <= R^2 (float64, pixel centres).
+top_status circ_table(top_handle h, int ny, int nx, double dy, double dx, double R, const int2** out) {
+  const std::array<uint64_t, 5> key = {uint64_t(ny), uint64_t(nx), bits(dy), bits(dx), bits(R)};
+  auto it = h->circ.find(key);
+  if (it != h->circ.end()) {
+    *out = it->second;
+    return TOP_OK;
+  }
+  std::vector<int2> t(ny);
+  const double r2 = R * R;
+  for (int j = 0; j < ny; ++j) {
+    const double yv = (double(j) - double(ny - 1) / 2.0) * dy;
+    const double y2 = yv * yv;
+    int lo = nx, hi = -1;
+    for (int i = 0; i < nx; ++i) {
+      const double xv = (double(i) - double(nx - 1) / 2.0) * dx;
+      if (xv * xv + y2 <= r2) {
+        lo = std::min(lo, i);
+        hi = std::max(hi, i);
+      }
+    }
+    t[j] = make_int2(lo, hi);
+  }
+  int2* dp = nullptr;
+  TOP_TRY(upload(h, t, &dp));
+  h->circ[key] = dp;
+  *out = dp;
+  return TOP_OK;
+}
+
+// ============================================================================= validation
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+struct Geometry {
+  int ny, nx, Py, Px, oy, ox;
+};
+
+top_status padded(int n, double pad, int* P) {
+  const double v = std::floor(pad * double(n) + 0.5);
+  if (!(v >= double(n)) || v > 1048576.0) return fail(TOP_ERR_INVALID_ARG, "padded size %.0f invalid for n = %d", v, n);
+  *P = int(v);
+  return TOP_OK;
+}
+
+top_status check_grid(const top_grid* g, Geometry* geo) {
+  if (!g) return fail(TOP_ERR_INVALID_ARG, "grid is NULL");
+  if (g->batch < 1) return fail(TOP_ERR_INVALID_ARG, "batch must be >= 1 (got %lld)", (long long)g->batch);
+  if (g->ny < 1 || g->nx < 1) return fail(TOP_ERR_INVALID_ARG, "ny, nx must be >= 1 (got %d, %d)", g->ny, g->nx);
+  if (!(std::isfinite(g->dy) && g->dy > 0) || !(std::isfinite(g->dx) && g->dx > 0))
+    return fail(TOP_ERR_INVALID_ARG, "spacing must be finite and > 0");
+  if (!(std::isfinite(g->pad) && g->pad >= 1.0)) return fail(TOP_ERR_INVALID_ARG, "pad must be finite and >= 1");
+  if (g->method != TOP_AS && g->method != TOP_FRESNEL_TF) return fail(TOP_ERR_INVALID_ARG, "unknown method %d", g->method);
+  if (g->input_repeat < 0 || (g->input_repeat > 1 && g->batch % g->input_repeat != 0))
+    return fail(TOP_ERR_INVALID_ARG, "input_repeat (%d) must be 0, 1 or a divisor of batch", g->input_repeat);
+  geo->ny = g->ny;
+  geo->nx = g->nx;
+  TOP_TRY(padded(g->ny, g->pad, &geo->Py));
+  TOP_TRY(padded(g->nx, g->pad, &geo->Px));
+  geo->oy = (geo->Py - g->ny) / 2;
+  geo->ox = (geo->Px - g->nx) / 2;
+  return TOP_OK;
+}
+
+top_status check_engines(const Geometry& geo) {
+  EngineInfo info;
+  for (int P : {geo.Py, geo.Px}) {
+    if (P % 2 != 0 || !find_engine(P / 2, &info))
+      return fail(TOP_ERR_UNSUPPORTED, "padded size %d has no FFT engine (supported: 2 x {16 .. 4096 powers of two, 250, 500, 768, 1000})", P);
+  }
+  return TOP_OK;
+}
+
+top_status check_lz(const top_grid* g, const double* lam, const double* z, int64_t n_lz, bool need_z) {
+  if (!lam || (need_z && !z)) return fail(TOP_ERR_INVALID_ARG, "lambda / z arrays are NULL");
+  if (n_lz != 1 && n_lz != g->batch)
+    return fail(TOP_ERR_INVALID_ARG, "n_lz must be 1 or batch (%lld), got %lld", (long long)g->batch, (long long)n_lz);
+  for (int64_t i = 0; i < n_lz; ++i) {
+    if (!(std::isfinite(lam[i]) && lam[i] > 0)) return fail(TOP_ERR_INVALID_ARG, "lambda[%lld] must be finite and > 0", (long long)i);
+    if (need_z && !std::isfinite(z[i])) return fail(TOP_ERR_INVALID_ARG, "z[%lld] must be finite", (long long)i);
+  }
+  return TOP_OK;
+}
+
+top_status check_ptr(const void* p, const char* name) {
+  if (!p) return fail(TOP_ERR_INVALID_ARG, "%s is NULL", name);
+  if (!aligned16(p)) return fail(TOP_ERR_INVALID_ARG, "%s is not 16-byte aligned", name);
+  return TOP_OK;
+}
+
+top_status check_mod(const top_mod* m, const char* name) {
+  if (!m || m->flags == 0) return TOP_OK;
+  const uint32_t all = TOP_MOD_COMPLEX | TOP_MOD_AMPLITUDE | TOP_MOD_PHASE | TOP_MOD_LENS | TOP_MOD_CIRC;
+  if (m->flags & ~all) return fail(TOP_ERR_INVALID_ARG, "%s: unknown modulation flags 0x%x", name, m->flags);
+  if ((m->flags & TOP_MOD_COMPLEX)) TOP_TRY(check_ptr(m->mask, "modulation mask"));
+  if ((m->flags & TOP_MOD_AMPLITUDE)) TOP_TRY(check_ptr(m->amplitude, "modulation amplitude"));
+  if ((m->flags & TOP_MOD_PHASE)) TOP_TRY(check_ptr(m->phase, "modulation phase"));
+  if ((m->flags & TOP_MOD_LENS) && !(std::isfinite(m->focal_length) && m->focal_length != 0.0))
+    return fail(TOP_ERR_INVALID_ARG, "%s: focal length must be finite and non-zero", name);
+  if ((m->flags & TOP_MOD_CIRC) && !(std::isfinite(m->radius) && m->radius >= 0.0))
+    return fail(TOP_ERR_INVALID_ARG, "%s: aperture radius must be finite and >= 0", name);
+  if (m->batch_stride < 0) return fail(TOP_ERR_INVALID_ARG, "%s: batch_stride must be >= 0", name);
+  return TOP_OK;
+}
+
+top_status check_as_remainder(const Geometry& geo, const top_grid* g, const double* lam, const double* z,
+                              int64_t n_lz) {
+  if (g->method != TOP_AS) return TOP_OK;
+  // largest non-separable phase cr * |g(u)| over propagating samples; float32 keeps it to ~1e-5 rad below 128 rad
+  const double fx = freq(geo.Px / 2, geo.Px, g->dx), fy = freq(geo.Py / 2, geo.Py, g->dy);
+  for (int64_t i = 0; i < n_lz; ++i) {
+    double u = lam[i] * lam[i] * (fx * fx + fy * fy);
+    if (u > 1.0) u = 1.0;
+    const double gu = (std::sqrt(1.0 - u) - 1.0 + 0.5 * u);
+    const double rmax = std::fabs(2.0 * M_PI * z[i] / lam[i] * gu);
+    if (rmax > 128.0)
+      return fail(TOP_ERR_UNSUPPORTED,
+                  "AS phase beyond the Fresnel terms reaches %.3g rad (> 128) for field %lld; use the Fresnel "
+                  "method, a smaller z or a larger spacing",
+                  rmax, (long long)i);
+  }
+  return TOP_OK;
+}
+
+ModDev mod_dev(const top_mod* m, int conj, const int2* circ) {
+  ModDev d{};
+  if (!m) return d;
+  d.flags = m->flags;
+  d.conj = conj;
+  d.cmask = static_cast<const float2*>(m->mask);
+  d.amp = m->amplitude;
+  d.phase = m->phase;
+  d.stride = m->batch_stride;
+  d.circ = circ;
+  return d;
+}
+
+// Per-field masks (batch_stride != 0) are addressed relative to the first field of a launch.
+ModDev offset_mod(ModDev d, long long pos) {
+  if (d.stride) {
+    if (d.cmask) d.cmask += pos * d.stride;
+    if (d.amp) d.amp += pos * d.stride;
+    if (d.phase) d.phase += pos * d.stride;
+  }
+  return d;
+}
+
+// ============================================================================= propagation driver
+
+struct Request {
+  const top_grid* g;
+  const double* lam;
+  const double* z;
+  int64_t n_lz;
+  int adjoint;
+  int src_kind;
+  const void* in;
+  const void* psi_src;  // SRC_INTENSITY saved field
+  const float* gI;
+  const float* weights;
+  int64_t group;  // intensity group (SRC_INTENSITY / EPI_INTENSITY)
+  const top_mod* msrc;
+  int msrc_conj;
+  int epi_kind;
+  void* out;
+  float* outf;
+  const top_mod* mepi;
+  int mepi_conj;
+  const top_mod_grads* grads;  // EPI_MODGRAD
+};
+
+top_status run_propagation(top_handle h, const Request& q, cudaStream_t st) {
+  const top_grid* g = q.g;
+  Geometry geo;
+  TOP_TRY(check_grid(g, &geo));
+  TOP_TRY(check_engines(geo));
+  TOP_TRY(check_lz(g, q.lam, q.z, q.n_lz, true));
+  TOP_TRY(check_mod(q.msrc, "source modulation"));
+  TOP_TRY(check_mod(q.mepi, "epilogue modulation"));
+  TOP_TRY(check_as_remainder(geo, g, q.lam, q.z, q.n_lz));
+  const int64_t B = g->batch;
+  if (q.adjoint && g->input_repeat > 1) return fail(TOP_ERR_INVALID_ARG, "input_repeat applies to forward calls only");
+  if (g->input_repeat > 1 && q.in && q.in == q.out)
+    return fail(TOP_ERR_INVALID_ARG, "input_repeat > 1 needs distinct input and output buffers");
+  if (q.src_kind == SRC_FIELD) TOP_TRY(check_ptr(q.in, "input field"));
+  if (q.src_kind == SRC_INTENSITY) {
+    TOP_TRY(check_ptr(q.psi_src, "saved field"));
+    TOP_TRY(check_ptr(q.gI, "intensity gradient"));
+  }
+  if (q.group < 1 || B % q.group != 0)
+    return fail(TOP_ERR_INVALID_ARG, "group (%lld) must be >= 1 and divide batch (%lld)", (long long)q.group, (long long)B);
+  if (q.group > kMaxFields) return fail(TOP_ERR_UNSUPPORTED, "group larger than %d fields", kMaxFields);
+  if (q.weights && !aligned16(q.weights)) return fail(TOP_ERR_INVALID_ARG, "weights not 16-byte aligned");
+  if (q.epi_kind == EPI_FIELD) TOP_TRY(check_ptr(q.out, "output field"));
+  if (q.epi_kind == EPI_INTENSITY) {
+    TOP_TRY(check_ptr(q.outf, "intensity"));
+    if (q.out) TOP_TRY(check_ptr(q.out, "field output"));
+  }
+  const top_mod_grads* gr = q.grads;
+  const bool want_pgrads = q.epi_kind == EPI_MODGRAD && gr && (gr->grad_phase || gr->grad_amplitude || gr->grad_mask);
+  if (q.epi_kind == EPI_MODGRAD) {
+    if (q.out) TOP_TRY(check_ptr(q.out, "grad_in"));
+    if (want_pgrads) {
+      TOP_TRY(check_ptr(gr->saved_in, "pre_grads->saved_in"));
+      if (!q.mepi || q.mepi->flags == 0) return fail(TOP_ERR_INVALID_ARG, "modulation gradients need a modulation");
+      if (gr->grad_phase && !(q.mepi->flags & TOP_MOD_PHASE)) return fail(TOP_ERR_INVALID_ARG, "grad_phase needs TOP_MOD_PHASE");
+      if (gr->grad_amplitude && !(q.mepi->flags & TOP_MOD_AMPLITUDE)) return fail(TOP_ERR_INVALID_ARG, "grad_amplitude needs TOP_MOD_AMPLITUDE");
+      if (gr->grad_mask && !(q.mepi->flags & TOP_MOD_COMPLEX)) return fail(TOP_ERR_INVALID_ARG, "grad_mask needs TOP_MOD_COMPLEX");
+      for (const void* p : {(const void*)gr->grad_phase, (const void*)gr->grad_amplitude, (const void*)gr->grad_mask})
+        if (p && !aligned16(p)) return fail(TOP_ERR_INVALID_ARG, "gradient output not 16-byte aligned");
+    }
+  }
+  TOP_TRY(bind(h));
+
+  // engine and split twiddles
+  const float2 *twx, *twy, *wpx, *wpy;
+  TOP_TRY(engine_twiddles(h, geo.Px / 2, &twx));
+  TOP_TRY(engine_twiddles(h, geo.Py / 2, &twy));
+  TOP_TRY(split_twiddles(h, geo.Px, &wpx));
+  TOP_TRY(split_twiddles(h, geo.Py, &wpy));
+  const int2* circ_src = nullptr;
+  const int2* circ_epi = nullptr;
+  if (q.msrc && (q.msrc->flags & TOP_MOD_CIRC)) TOP_TRY(circ_table(h, geo.ny, geo.nx, g->dy, g->dx, q.msrc->radius, &circ_src));
+  if (q.mepi && (q.mepi->flags & TOP_MOD_CIRC)) TOP_TRY(circ_table(h, geo.ny, geo.nx, g->dy, g->dx, q.mepi->radius, &circ_epi));
+
+  // per-field parameter sets
+  std::vector<FieldSet> field_sets(B);
+  for (int64_t b = 0; b < B; ++b) {
+    const int64_t i = q.n_lz == 1 ? 0 : b;
+    TransferEntry te;
+    TOP_TRY(transfer_tables(h, geo.Py, geo.Px, g->dy, g->dx, q.lam[i], q.z[i], g->method, &te));
+    FieldSet fs{};
+    fs.hx = te.hx;
+    fs.hy = te.hy;
+    fs.kcut = te.kcut;
+    fs.cg = te.cg;
+    fs.cr = te.cr;
+    if (q.msrc && (q.msrc->flags & TOP_MOD_LENS)) {
+      TOP_TRY(lens_table(h, geo.nx, g->dx, q.lam[i], q.msrc->focal_length, &fs.src_lx));
+      TOP_TRY(lens_table(h, geo.ny, g->dy, q.lam[i], q.msrc->focal_length, &fs.src_ly));
+    }
+    if (q.mepi && (q.mepi->flags & TOP_MOD_LENS)) {
+      TOP_TRY(lens_table(h, geo.nx, g->dx, q.lam[i], q.mepi->focal_length, &fs.epi_lx));
+      TOP_TRY(lens_table(h, geo.ny, g->dy, q.lam[i], q.mepi->focal_length, &fs.epi_ly));
+    }
+    field_sets[b] = fs;
+  }
+  auto same = [](const FieldSet& a, const FieldSet& b) { return std::memcmp(&a, &b, sizeof(FieldSet)) == 0; };
+
+  // epilogue grouping and workspace
+  const long long plane = (long long)geo.ny * geo.nx;
+  const bool shared_mask = q.mepi && q.mepi->batch_stride == 0;
+  int64_t group = 1;
+  if (q.epi_kind == EPI_INTENSITY) group = q.group;
+  const bool partials = want_pgrads && shared_mask;
+  const int rows_per_cta_guess = 8;
+  if (partials) {
+    const int64_t tiles = (geo.ny + rows_per_cta_guess - 1) / rows_per_cta_guess;
+    const int64_t want_groups = std::max<int64_t>(1, (4 * 152 + tiles - 1) / tiles);
+    group = std::max<int64_t>(1, (B + want_groups - 1) / want_groups);
+  }
+  const size_t ws_field = size_t(geo.Px) * size_t(geo.ny) * sizeof(float2);
+  size_t part_bytes_per_group = 0;
+  if (partials) {
+    if (gr->grad_phase) part_bytes_per_group += plane * sizeof(float);
+    if (gr->grad_amplitude) part_bytes_per_group += plane * sizeof(float);
+    if (gr->grad_mask) part_bytes_per_group += plane * sizeof(float2);
+  }
+  // chunk: a multiple of every grouping (intensity planes never straddle chunks), <= kMaxFields,
+  // workspace within the limit
+  const int64_t src_group = q.src_kind == SRC_INTENSITY ? q.group : 1;
+  const int64_t epi_align = q.epi_kind == EPI_INTENSITY ? group : 1;
+  const int64_t in_repeat = (q.src_kind == SRC_FIELD && g->input_repeat > 1) ? g->input_repeat : 1;
+  const int64_t align = std::lcm(std::lcm(src_group, epi_align), in_repeat);
+  if (align > kMaxFields) return fail(TOP_ERR_UNSUPPORTED, "intensity group larger than %d fields", kMaxFields);
+  int64_t chunk = std::min<int64_t>(B, kMaxFields);
+  chunk = std::max<int64_t>(align, chunk - chunk % align);
+  auto need = [&](int64_t c) {
+    const int64_t ng = (c + group - 1) / group;
+    return size_t(c) * ws_field + size_t(ng) * part_bytes_per_group + 256;
+  };
+  while (chunk > align && need(chunk) > h->ws_limit) chunk = std::max<int64_t>(align, (chunk / 2) - (chunk / 2) % align);
+  if (need(chunk) > h->ws_limit)
+    return fail(TOP_ERR_OOM, "one group of fields needs %zu bytes of workspace, above the limit %llu", need(chunk),
+                (unsigned long long)h->ws_limit);
+  TOP_TRY(ensure_workspace(h, need(chunk)));
+  float2* ws = static_cast<float2*>(h->ws);
+  char* part_base = reinterpret_cast<char*>(h->ws) + size_t(chunk) * ws_field;
+  part_base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(part_base) + 255) & ~uintptr_t(255));
+  const int64_t ngroups_chunk = (chunk + group - 1) / group;
+  float* part_phase = nullptr;
+  float* part_amp = nullptr;
+  float2* part_mask = nullptr;
+  if (partials) {
+    // chunks may hold different numbers of groups (the parameter-set limit can end a chunk early),
+    // so the partial planes start at zero and every chunk adds to them
+    char* pb = part_base;
+    if (gr->grad_phase) { part_phase = reinterpret_cast<float*>(pb); pb += ngroups_chunk * plane * sizeof(float); }
+    if (gr->grad_amplitude) { part_amp = reinterpret_cast<float*>(pb); pb += ngroups_chunk * plane * sizeof(float); }
+    if (gr->grad_mask) { part_mask = reinterpret_cast<float2*>(pb); pb += ngroups_chunk * plane * sizeof(float2); }
+    TOP_CUDA(cudaMemsetAsync(part_base, 0, size_t(pb - part_base), st), "cudaMemsetAsync(gradient partials)");
+  }
+
+  PassParams p{};
+  p.ny = geo.ny;
+  p.nx = geo.nx;
+  p.Py = geo.Py;
+  p.Px = geo.Px;
+  p.My = geo.Py / 2;
+  p.Mx = geo.Px / 2;
+  p.oy = geo.oy;
+  p.ox = geo.ox;
+  p.method = g->method;
+  p.adjoint = q.adjoint;
+  p.src_kind = q.src_kind;
+  p.epi_kind = q.epi_kind;
+  p.twx = twx;
+  p.twy = twy;
+  p.wpx = wpx;
+  p.wpy = wpy;
+  const ModDev msrc_base = mod_dev(q.msrc, q.msrc_conj, circ_src);
+  const ModDev mepi_base = mod_dev(q.mepi, q.mepi_conj, circ_epi);
+  p.ws = ws;
+  p.ws_stride = (long long)geo.Px * geo.ny;
+  p.in_stride = plane;
+  p.out_stride = plane;
+  p.psi_stride = plane;
+  p.gI_stride = plane;
+  p.outf_stride = plane;
+  p.part_stride = plane;
+
+  int64_t pos = 0;
+  while (pos < B) {
+    // grow the chunk field by field while the distinct parameter sets fit
+    int64_t n = 0;
+    p.nsets = 0;
+    while (pos + n < B && n < chunk) {
+      // a whole aligned group of fields at a time
+      int64_t gend = std::min<int64_t>(B, pos + n + align);
+      int added_sets = 0;
+      FieldSet tmp[kMaxSets];
+      int tmpn = p.nsets;
+      std::memcpy(tmp, p.sets, sizeof(FieldSet) * p.nsets);
+      unsigned char idx_tmp[kMaxFields];
+      bool ok = true;
+      for (int64_t b = pos + n; b < gend; ++b) {
+        int k = 0;
+        while (k < tmpn && !same(tmp[k], field_sets[b])) ++k;
+        if (k == tmpn) {
+          if (tmpn == kMaxSets) { ok = false; break; }
+          tmp[tmpn++] = field_sets[b];
+          ++added_sets;
+        }
+        idx_tmp[b - pos - n] = (unsigned char)k;
+      }
+      if (!ok) break;
+      std::memcpy(p.sets, tmp, sizeof(FieldSet) * tmpn);
+      p.nsets = tmpn;
+      std::memcpy(p.set_of + n, idx_tmp, size_t(gend - pos - n));
+      n = gend - pos;
+      (void)added_sets;
+    }
+    if (n == 0) return fail(TOP_ERR_UNSUPPORTED, "a group of fields uses more than %d (lambda, z) sets", kMaxSets);
+    p.nfields = int(n);
+    p.group = int(group);
+    p.src_group = int(src_group);
+    p.in_repeat = int(in_repeat);
+    p.msrc = offset_mod(msrc_base, pos);
+    p.mepi = offset_mod(mepi_base, pos);
+    p.in = q.src_kind == SRC_FIELD ? static_cast<const float2*>(q.in) + (pos / in_repeat) * plane : nullptr;
+    p.psi = nullptr;
+    if (q.src_kind == SRC_INTENSITY) {
+      p.psi = static_cast<const float2*>(q.psi_src) + pos * plane;
+      p.gI = q.gI + (pos / q.group) * plane;
+    }
+    p.weights = q.weights ? q.weights + pos : nullptr;
+    p.out = q.out ? static_cast<float2*>(q.out) + pos * plane : nullptr;
+    p.outf = q.outf ? q.outf + (pos / group) * plane : nullptr;
+    if (q.epi_kind == EPI_MODGRAD) {
+      p.psi = want_pgrads ? static_cast<const float2*>(gr->saved_in) + pos * plane : nullptr;
+      if (partials) {
+        p.part_phase = part_phase;
+        p.part_amp = part_amp;
+        p.part_mask = part_mask;
+        p.part_stride = plane;
+        p.part_accumulate = 1;
+      } else if (want_pgrads) {  // per-field masks: write straight into the outputs
+        p.part_phase = gr->grad_phase ? gr->grad_phase + pos * plane : nullptr;
+        p.part_amp = gr->grad_amplitude ? gr->grad_amplitude + pos * plane : nullptr;
+        p.part_mask = gr->grad_mask ? static_cast<float2*>(gr->grad_mask) + pos * plane : nullptr;
+        p.part_stride = plane;
+        p.part_accumulate = 0;
+      }
+      // partial planes are reused by every chunk (group g of each chunk adds to plane g);
+      // per-field gradients use groups of one field
+      p.group = partials ? int(group) : 1;
+    }
+    TOP_TRY(timed(h, KK_ROWS_FWD, st, "rows forward pass", [&] { return launch_pass(PASS_ROWS_FWD, p.Mx, p, st); }));
+    TOP_TRY(timed(h, KK_COLS, st, "column pass", [&] { return launch_pass(PASS_COLS, p.My, p, st); }));
+    TOP_TRY(timed(h, KK_ROWS_INV, st, "rows inverse pass", [&] { return launch_pass(PASS_ROWS_INV, p.Mx, p, st); }));
+    pos += n;
+  }
+  if (partials) {
+    TOP_TRY(timed(h, KK_AUX, st, "gradient reduction", [&] {
+      return launch_reduce_partials(part_phase, part_amp, part_mask, int(ngroups_chunk), plane, gr->grad_phase,
+                                    gr->grad_amplitude, static_cast<float2*>(gr->grad_mask), st);
+    }));
+  }
+  return TOP_OK;
+}
+
+}  // namespace
+
+// ============================================================================= C ABI
+
+extern "C" {
+
+const char* top_last_error(void) { return t_last_error.c_str(); }
+
+const char* top_status_string(top_status s) {
+  switch (s) {
+    case TOP_OK: return "TOP_OK";
+    case TOP_ERR_INVALID_ARG: return "TOP_ERR_INVALID_ARG";
+    case TOP_ERR_UNSUPPORTED: return "TOP_ERR_UNSUPPORTED";
+    case TOP_ERR_OOM: return "TOP_ERR_OOM";
+    case TOP_ERR_CUDA: return "TOP_ERR_CUDA";
+    case TOP_ERR_TIMEOUT: return "TOP_ERR_TIMEOUT";
+    case TOP_ERR_INTERNAL: return "TOP_ERR_INTERNAL";
+  }
+  return "TOP_ERR_UNKNOWN";
+}
+
+int top_version(void) { return TOP_ABI_VERSION; }
+
+double top_zcritical(double L, double dx, double lambda) { return L * dx / lambda; }
+
+top_status top_create(top_handle* out, int device) {
+  if (!out) return fail(TOP_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  int count = 0;
+  cudaError_t e = cudaGetDeviceCount(&count);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+  if (device < 0 || device >= count) return fail(TOP_ERR_INVALID_ARG, "device %d out of range (%d devices)", device, count);
+  TOP_CUDA(cudaSetDevice(device), "cudaSetDevice");
+  top_ctx* h = new top_ctx();
+  h->device = device;
+  *out = h;
+  return TOP_OK;
+}
+
+top_status top_destroy(top_handle h) {
+  if (!h) return fail(TOP_ERR_INVALID_ARG, "handle is NULL");
+  cudaSetDevice(h->device);
+  cudaDeviceSynchronize();
+  for (void* p : h->allocs) cudaFree(p);
+  if (h->ws) cudaFree(h->ws);
+  if (h->coh) cudaFree(h->coh);
+  for (auto& pe : h->pending) {
+    cudaEventDestroy(pe.second.first);
+    cudaEventDestroy(pe.second.second);
+  }
+  for (cudaEvent_t e : h->pool) cudaEventDestroy(e);
+  delete h;
+  return TOP_OK;
+}
+
+top_status top_set_workspace_limit(top_handle h, uint64_t bytes) {
+  if (!h) return fail(TOP_ERR_INVALID_ARG, "handle is NULL");
+  if (bytes < (1u << 20)) return fail(TOP_ERR_INVALID_ARG, "workspace limit below 1 MiB");
+  h->ws_limit = bytes;
+  return TOP_OK;
+}
+
+top_status top_plan_query(const top_grid* g, int64_t* py, int64_t* px, uint64_t* workspace_per_field) {
+  Geometry geo;
+  TOP_TRY(check_grid(g, &geo));
+  TOP_TRY(check_engines(geo));
+  if (py) *py = geo.Py;
+  if (px) *px = geo.Px;
+  if (workspace_per_field) *workspace_per_field = uint64_t(geo.Px) * uint64_t(geo.ny) * sizeof(float2);
+  return TOP_OK;
+}
+
+top_status top_propagate(top_handle h, const top_grid* g, const void* in, void* out, const double* lambda,
+                         const double* z, int64_t n_lz, const top_mod* pre, const top_mod* post, void* stream) {
+  if (!h) return fail(TOP_ERR_INVALID_ARG, "handle is NULL");
+  Request q{};
+  q.g = g; q.lam = lambda; q.z = z; q.n_lz = n_lz; q.adjoint = 0;
+  q.src_kind = SRC_FIELD; q.in = in; q.group = 1;
+  q.msrc = pre; q.msrc_conj = 0;
+  q.epi_kind = EPI_FIELD; q.out = out; q.mepi = post; q.mepi_conj = 0;
+  return run_propagation(h, q, static_cast<cudaStream_t>(stream));
+}
+
+top_status top_propagate_backward(top_handle h, const top_grid* g, const void* grad_out, void* grad_in,
+                                  const double* lambda, const double* z, int64_t n_lz, const top_mod* pre,
+                                  const top_mod* post, const top_mod_grads* pre_grads, void* stream) {
+  if (!h) return fail(TOP_ERR_INVALID_ARG, "handle is NULL");
+  Request q{};
+  q.g = g; q.lam = lambda; q.z = z; q.n_lz = n_lz; q.adjoint = 1;
+  q.src_kind = SRC_FIELD; q.in = grad_out; q.group = 1;
+  q.msrc = post; q.msrc_conj = 1;
+  const bool pg = pre_grads && (pre_grads->grad_phase || pre_grads->grad_amplitude || pre_grads->grad_mask);
+  if (pg) {
+    q.epi_kind = EPI_MODGRAD; q.out = grad_in; q.mepi = pre; q.mepi_conj = 0; q.grads = pre_grads;
+  } else {
+    if (!grad_in) return fail(TOP_ERR_INVALID_ARG, "grad_in is NULL and no modulation gradient requested");
+    q.epi_kind = EPI_FIELD; q.out = grad_in; q.mepi = pre; q.mepi_conj = 1;
+  }
+  return run_propagation(h, q, static_cast<cudaStream_t>(stream));
+}
+
+top_status top_propagate_intensity(top_handle h, const top_grid* g, const void* in, void* field_out,
+                                   float* intensity, int64_t group, const float* weights, const double* lambda,
+                                   const double* z, int64_t n_lz, const top_mod* pre, const top_mod* post,
+                                   void* stream) {
+  if (!h) return fail(TOP_ERR_INVALID_ARG, "handle is NULL");
+  Request q{};
+  q.g = g; q.lam = lambda; q.z = z; q.n_lz = n_lz; q.adjoint = 0;
+  q.src_kind = SRC_FIELD; q.in = in; q.group = group; q.weights = weights;
+  q.msrc = pre; q.msrc_conj = 0;
+  q.epi_kind = EPI_INTENSITY; q.out = field_out; q.outf = intensity; q.mepi = post; q.mepi_conj = 0;
+  return run_propagation(h, q, static_cast<cudaStream_t>(stream));
+}
+
+top_status top_propagate_intensity_backward(top_handle h, const top_grid* g, const void* field,
+                                            const float* grad_intensity, void* grad_in, int64_t group,
+                                            const float* weights, const double* lambda, const double* z,
+                                            int64_t n_lz, const top_mod* pre, const top_mod* post,
+                                            const top_mod_grads* pre_grads, void* stream) {
+  if (!h) return fail(TOP_ERR_INVALID_ARG, "handle is NULL");
+  Request q{};
+  q.g = g; q.lam = lambda; q.z = z; q.n_lz = n_lz; q.adjoint = 1;
+  q.src_kind = SRC_INTENSITY; q.psi_src = field; q.gI = grad_intensity; q.group = group; q.weights = weights;
+  q.msrc = post; q.msrc_conj = 1;
+  const bool pg = pre_grads && (pre_grads->grad_phase || pre_grads->grad_amplitude || pre_grads->grad_mask);
+  if (pg) {
+    q.epi_kind = EPI_MODGRAD; q.out = grad_in; q.mepi = pre; q.mepi_conj = 0; q.grads = pre_grads;
+  } else {
+    if (!grad_in) return fail(TOP_ERR_INVALID_ARG, "grad_in is NULL and no modulation gradient requested");
+    q.epi_kind = EPI_FIELD; q.out = grad_in; q.mepi = pre; q.mepi_conj = 1;
+  }
+  return run_propagation(h, q, static_cast<cudaStream_t>(stream));
+}
+
+// ----------------------------------------------------------------------------- modulation
+
+static top_status modulation_common(top_handle h, const top_grid* g, const top_mod* mod, const double* lambda,
+                                    int64_t n_lz, Geometry* geo, PassParams* p) {
+  TOP_TRY(check_grid(g, geo));
+  if (!mod) return fail(TOP_ERR_INVALID_ARG, "modulation is NULL");
+  TOP_TRY(check_mod(mod, "modulation"));
+  if (mod->flags & TOP_MOD_LENS) TOP_TRY(check_lz(g, lambda, nullptr, n_lz, false));
+  TOP_TRY(bind(h));
+  const int2* circ = nullptr;
+  if (mod->flags & TOP_MOD_CIRC) TOP_TRY(circ_table(h, geo->ny, geo->nx, g->dy, g->dx, mod->radius, &circ));
+  *p = PassParams{};
+  p->ny = geo->ny;
+  p->nx = geo->nx;
+  p->msrc = mod_dev(mod, 0, circ);
+  p->mepi = p->msrc;
+  return TOP_OK;
+}
+
+static top_status fill_lens_sets(top_handle h, const top_grid* g, const top_mod* mod, const double* lambda,
+                                 int64_t n_lz, int64_t pos, int64_t n, PassParams* p) {
+  p->nsets = 0;
+  for (int64_t b = pos; b < pos + n; ++b) {
+    FieldSet fs{};
+    if (mod->flags & TOP_MOD_LENS) {
+      const double lam = lambda[n_lz == 1 ? 0 : b];
+      TOP_TRY(lens_table(h, g->nx, g->dx, lam, mod->focal_length, &fs.src_lx));
+      TOP_TRY(lens_table(h, g->ny, g->dy, lam, mod->focal_length, &fs.src_ly));
+    }
+    fs.epi_lx = fs.src_lx;
+    fs.epi_ly = fs.src_ly;
+    int k = 0;
+    while (k < p->nsets && std::memcmp(&p->sets[k], &fs, sizeof fs) != 0) ++k;
+    if (k == p->nsets) {
+      if (p->nsets == kMaxSets) return fail(TOP_ERR_INTERNAL, "lens set overflow");
+      p->sets[p->nsets++] = fs;
+    }
+    p->set_of[b - pos] = (unsigned char)k;
+  }
+  return TOP_OK;
+}
+
+top_status top_modulate(top_handle h, const top_grid* g, const top_mod* mod, const void* in, void* out,
+                        const double* lambda, int64_t n_lz, void* stream) {
+  if (!h) return fail(TOP_ERR_INVALID_ARG, "handle is NULL");
+  Geometry geo;
+  PassParams p;
+  TOP_TRY(modulation_common(h, g, mod, lambda, n_lz, &geo, &p));
+  TOP_TRY(check_ptr(in, "input field"));
+  TOP_TRY(check_ptr(out, "output field"));
+  const ModDev base = p.msrc;
+  const long long plane = (long long)geo.ny * geo.nx;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  for (int64_t pos = 0; pos < g->batch; pos += kMaxSets) {
+    const int64_t n = std::min<int64_t>(kMaxSets, g->batch - pos);
+    TOP_TRY(fill_lens_sets(h, g, mod, lambda, n_lz, pos, n, &p));
+    p.nfields = int(n);
+    p.msrc = offset_mod(base, pos);
+    p.in = static_cast<const float2*>(in) + pos * plane;
+    p.out = static_cast<float2*>(out) + pos * plane;
+    TOP_TRY(timed(h, KK_AUX, st, "modulate", [&] { return launch_modulate(p, st); }));
+  }
+  return TOP_OK;
+}
+
+top_status top_modulate_backward(top_handle h, const top_grid* g, const top_mod* mod, const void* grad_out,
+                                 void* grad_in, const top_mod_grads* grads, const double* lambda, int64_t n_lz,
+                                 void* stream) {
+  if (!h) return fail(TOP_ERR_INVALID_ARG, "handle is NULL");
+  Geometry geo;
+  PassParams p;
+  TOP_TRY(modulation_common(h, g, mod, lambda, n_lz, &geo, &p));
+  TOP_TRY(check_ptr(grad_out, "grad_out"));
+  if (grad_in) TOP_TRY(check_ptr(grad_in, "grad_in"));
+  const bool pg = grads && (grads->grad_phase || grads->grad_amplitude || grads->grad_mask);
+  if (pg) {
+    TOP_TRY(check_ptr(grads->saved_in, "grads->saved_in"));
+    if (grads->grad_phase && !(mod->flags & TOP_MOD_PHASE)) return fail(TOP_ERR_INVALID_ARG, "grad_phase needs TOP_MOD_PHASE");
+    if (grads->grad_amplitude && !(mod->flags & TOP_MOD_AMPLITUDE)) return fail(TOP_ERR_INVALID_ARG, "grad_amplitude needs TOP_MOD_AMPLITUDE");
+    if (grads->grad_mask && !(mod->flags & TOP_MOD_COMPLEX)) return fail(TOP_ERR_INVALID_ARG, "grad_mask needs TOP_MOD_COMPLEX");
+  }
+  if (!grad_in && !pg) return fail(TOP_ERR_INVALID_ARG, "nothing to compute");
+  // the lens factor varies with the field's wavelength; all other factors are per pixel
+  const long long plane = (long long)geo.ny * geo.nx;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const bool shared = mod->batch_stride == 0;
+  const ModDev base = p.msrc;
+  // with a shared mask the first chunk writes the gradients and later chunks add to them
+  for (int64_t pos = 0; pos < g->batch; pos += kMaxSets) {
+    const int64_t n = std::min<int64_t>(kMaxSets, g->batch - pos);
+    TOP_TRY(fill_lens_sets(h, g, mod, lambda, n_lz, pos, n, &p));
+    p.nfields = int(n);
+    p.in = static_cast<const float2*>(grad_out) + pos * plane;
+    p.out = grad_in ? static_cast<float2*>(grad_in) + pos * plane : nullptr;
+    p.psi = pg ? static_cast<const float2*>(grads->saved_in) + pos * plane : nullptr;
+    p.msrc = offset_mod(base, pos);
+    const long long goff = shared ? 0 : pos * plane;
+    p.part_phase = pg && grads->grad_phase ? grads->grad_phase + goff : nullptr;
+    p.part_amp = pg && grads->grad_amplitude ? grads->grad_amplitude + goff : nullptr;
+    p.part_mask = pg && grads->grad_mask ? static_cast<float2*>(grads->grad_mask) + goff : nullptr;
+    p.part_accumulate = (shared && pos > 0) ? 1 : 0;
+    p.group = shared ? int(n) : 1;
+    TOP_TRY(timed(h, KK_AUX, st, "modulate backward", [&] { return launch_modulate_backward(p, st); }));
+  }
+  return TOP_OK;
+}
+
+// ----------------------------------------------------------------------------- loss
+
+top_status top_mse_loss(top_handle h, int64_t n, const float* intensity, const float* target, double* loss,
+                        float* grad, void* stream) {
+  if (!h) return fail(TOP_ERR_INVALID_ARG, "handle is NULL");
+  if (n < 1) return fail(TOP_ERR_INVALID_ARG, "n must be >= 1");
+  TOP_TRY(check_ptr(intensity, "intensity"));
+  TOP_TRY(check_ptr(target, "target"));
+  TOP_TRY(check_ptr(loss, "loss"));
+  if (grad) TOP_TRY(check_ptr(grad, "grad"));
+  TOP_TRY(bind(h));
+  // partial sums live in a small region at the end of the workspace
+  const size_t bytes = kMseBlocks * sizeof(double) + 256;
+  if (h->ws_bytes < bytes) TOP_TRY(ensure_workspace(h, bytes));
+  double* partial = reinterpret_cast<double*>(static_cast<char*>(h->ws) + h->ws_bytes - kMseBlocks * sizeof(double));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  return timed(h, KK_AUX, st, "mse loss", [&] { return launch_mse(n, intensity, target, grad, partial, loss, st); });
+}
+
+// ----------------------------------------------------------------------------- mutual coherence
+
+static top_status coh_scratch(top_handle h, size_t bytes, void** out) {
+  if (h->coh_bytes < bytes) {
+    if (h->coh) {
+      TOP_CUDA(cudaDeviceSynchronize(), "cudaDeviceSynchronize(coherence scratch growth)");
+      cudaFree(h->coh);
+      h->coh = nullptr;
+      h->coh_bytes = 0;
+    }
+    cudaError_t e = cudaMalloc(&h->coh, bytes);
+    if (e != cudaSuccess) {
+      h->coh = nullptr;
+      return cuda_fail(e, "cudaMalloc(coherence scratch)");
+    }
+    h->coh_bytes = bytes;
+  }
+  *out = h->coh;
+  return TOP_OK;
+}
+
+// Mask parameters of a coherence modulation M(r) (single wavelength).
+static top_status coh_mask_params(top_handle h, const top_grid* g, const top_mod* mask, double lam, PassParams* p) {
+  *p = PassParams{};
+  p->ny = g->ny;
+  p->nx = g->nx;
+  const int2* circ = nullptr;
+  if (mask->flags & TOP_MOD_CIRC) TOP_TRY(circ_table(h, g->ny, g->nx, g->dy, g->dx, mask->radius, &circ));
+  p->msrc = mod_dev(mask, 0, circ);
+  FieldSet fs{};
+  if (mask->flags & TOP_MOD_LENS) {
+    TOP_TRY(lens_table(h, g->nx, g->dx, lam, mask->focal_length, &fs.src_lx));
+    TOP_TRY(lens_table(h, g->ny, g->dy, lam, mask->focal_length, &fs.src_ly));
+  }
+  p->nsets = 1;
+  p->sets[0] = fs;
+  return TOP_OK;
+}
+
+static top_status coh_check(const top_grid* g, const double* lambda, const double* z, const top_mod* mask) {
+  Geometry geo;
+  TOP_TRY(check_grid(g, &geo));
+  TOP_TRY(check_engines(geo));
+  TOP_TRY(check_lz(g, lambda, z, 1, true));
+  TOP_TRY(check_mod(mask, "coherence mask"));
+  if (mask && mask->flags && mask->batch_stride != 0) return fail(TOP_ERR_INVALID_ARG, "coherence mask must be shared (batch_stride 0)");
+  const long long n = (long long)g->ny * g->nx;
+  if (n * n * g->batch > (1ll << 40)) return fail(TOP_ERR_INVALID_ARG, "coherence tensor too large");
+  return TOP_OK;
+}
+
+// P or P^H applied over r2 (each r1 slice), then over r1 via two batched transposes (Eq. 13).
+static top_status coh_two_sided(top_handle h, const top_grid* g, const void* src, void* dst, const double* lambda,
+                                const double* z, int adjoint_r2, cudaStream_t st) {
+  const int n = g->ny * g->nx;
+  top_grid fg = *g;
+  fg.batch = g->batch * n;
+  Request q{};
+  q.g = &fg; q.lam = lambda; q.z = z; q.n_lz = 1; q.adjoint = adjoint_r2;
+  q.src_kind = SRC_FIELD; q.in = src; q.group = 1;
+  q.epi_kind = EPI_FIELD; q.out = dst;
+  TOP_TRY(run_propagation(h, q, st));
+  void* tmp = nullptr;
+  TOP_TRY(coh_scratch(h, sizeof(float2) * size_t(g->batch) * n * n, &tmp));
+  TOP_TRY(timed(h, KK_AUX, st, "transpose", [&] {
+    return launch_transpose(static_cast<const float2*>(dst), static_cast<float2*>(tmp), g->batch, n, st);
+  }));
+  q.in = tmp; q.out = tmp; q.adjoint = 1 - adjoint_r2;
+  TOP_TRY(run_propagation(h, q, st));
+  return timed(h, KK_AUX, st, "transpose", [&] {
+    return launch_transpose(static_cast<const float2*>(tmp), static_cast<float2*>(dst), g->batch, n, st);
+  });
+}
+
+top_status top_propagate_coherence(top_handle h, const top_grid* g, const void* gamma_in, void* gamma_out,
+                                   const double* lambda, const double* z, const top_mod* mask, void* stream) {
+  if (!h) return fail(TOP_ERR_INVALID_ARG, "handle is NULL");
+  TOP_TRY(coh_check(g, lambda, z, mask));
+  TOP_TRY(check_ptr(gamma_in, "gamma_in"));
+  TOP_TRY(check_ptr(gamma_out, "gamma_out"));
+  if (gamma_in == gamma_out) return fail(TOP_ERR_INVALID_ARG, "gamma_in and gamma_out must be distinct");
+  TOP_TRY(bind(h));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const void* src = gamma_in;
+  if (mask && mask->flags) {
+    PassParams mp;
+    TOP_TRY(coh_mask_params(h, g, mask, lambda[0], &mp));
+    TOP_TRY(timed(h, KK_AUX, st, "coherence modulation", [&] {
+      return launch_coh_modulate(static_cast<const float2*>(gamma_in), static_cast<float2*>(gamma_out), mp, g->batch, 0, st);
+    }));
+    src = gamma_out;
+  }
+  // Gamma_z = P Gamma P^H: conj(H) over (y2, x2), H over (y1, x1)
+  return coh_two_sided(h, g, src, gamma_out, lambda, z, 1, st);
+}
+
+top_status top_propagate_coherence_backward(top_handle h, const top_grid* g, const void* grad_out, void* grad_in,
+                                            const double* lambda, const double* z, const top_mod* mask,
+                                            const top_mod_grads* grads, void* stream) {
+  if (!h) return fail(TOP_ERR_INVALID_ARG, "handle is NULL");
+  TOP_TRY(coh_check(g, lambda, z, mask));
+  TOP_TRY(check_ptr(grad_out, "grad_out"));
+  const bool pg = grads && (grads->grad_phase || grads->grad_amplitude || grads->grad_mask);
+  if (grad_in) TOP_TRY(check_ptr(grad_in, "grad_in"));
+  if (!grad_in && !pg) return fail(TOP_ERR_INVALID_ARG, "nothing to compute");
+  if (pg) {
+    if (!mask || !mask->flags) return fail(TOP_ERR_INVALID_ARG, "mask gradients need a mask");
+    TOP_TRY(check_ptr(grads->saved_in, "grads->saved_in"));
+    if (grads->grad_phase && !(mask->flags & TOP_MOD_PHASE)) return fail(TOP_ERR_INVALID_ARG, "grad_phase needs TOP_MOD_PHASE");
+    if (grads->grad_amplitude && !(mask->flags & TOP_MOD_AMPLITUDE)) return fail(TOP_ERR_INVALID_ARG, "grad_amplitude needs TOP_MOD_AMPLITUDE");
+    if (grads->grad_mask && !(mask->flags & TOP_MOD_COMPLEX)) return fail(TOP_ERR_INVALID_ARG, "grad_mask needs TOP_MOD_COMPLEX");
+  }
+  if (grad_in == grad_out) return fail(TOP_ERR_INVALID_ARG, "grad_in and grad_out must be distinct");
+  TOP_TRY(bind(h));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int n = g->ny * g->nx;
+  const size_t tensor = sizeof(float2) * size_t(g->batch) * n * n;
+  // G' = P^H G P lands in grad_in, or in a second scratch tensor placed in the workspace tail
+  void* dst = grad_in;
+  // the two-sided propagation uses the workspace and the transpose scratch, so an internal G' needs its own block
+  void* own = nullptr;
+  if (!dst) {
+    TOP_CUDA(cudaMalloc(&own, tensor), "cudaMalloc(coherence gradient)");
+    dst = own;
+  }
+  top_status s = coh_two_sided(h, g, grad_out, dst, lambda, z, 0, st);
+  if (s == TOP_OK && pg) {
+    PassParams mp;
+    s = coh_mask_params(h, g, mask, lambda[0], &mp);
+    if (s == TOP_OK && h->ws_bytes < size_t(n) * sizeof(float2) + 256) s = ensure_workspace(h, size_t(n) * sizeof(float2) + 256);
+    if (s == TOP_OK)
+      s = timed(h, KK_AUX, st, "coherence mask gradients", [&] {
+        return launch_coh_mask_grads(static_cast<const float2*>(dst), static_cast<const float2*>(grads->saved_in), mp,
+                                     g->batch, static_cast<float2*>(h->ws), grads->grad_phase, grads->grad_amplitude,
+                                     static_cast<float2*>(grads->grad_mask), st);
+      });
+  }
+  if (s == TOP_OK && grad_in && mask && mask->flags) {
+    PassParams mp;
+    s = coh_mask_params(h, g, mask, lambda[0], &mp);
+    if (s == TOP_OK)
+      s = timed(h, KK_AUX, st, "coherence modulation backward", [&] {
+        return launch_coh_modulate(static_cast<const float2*>(dst), static_cast<float2*>(dst), mp, g->batch, 1, st);
+      });
+  }
+  if (own) {
+    cudaStreamSynchronize(st);
+    cudaFree(own);
+  }
+  return s;
+}
+
+top_status top_coherence_intensity(top_handle h, const top_grid* g, const void* gamma, float* intensity, void* stream) {
+  if (!h) return fail(TOP_ERR_INVALID_ARG, "handle is NULL");
+  Geometry geo;
+  TOP_TRY(check_grid(g, &geo));
+  TOP_TRY(check_ptr(gamma, "gamma"));
+  TOP_TRY(check_ptr(intensity, "intensity"));
+  TOP_TRY(bind(h));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  return timed(h, KK_AUX, st, "coherence intensity", [&] {
+    return launch_coh_diag(static_cast<const float2*>(gamma), intensity, g->batch, g->ny * g->nx, st);
+  });
+}
+
+top_status top_coherence_intensity_backward(top_handle h, const top_grid* g, const float* grad_intensity,
+                                            void* grad_gamma, void* stream) {
+  if (!h) return fail(TOP_ERR_INVALID_ARG, "handle is NULL");
+  Geometry geo;
+  TOP_TRY(check_grid(g, &geo));
+  TOP_TRY(check_ptr(grad_intensity, "grad_intensity"));
+  TOP_TRY(check_ptr(grad_gamma, "grad_gamma"));
+  TOP_TRY(bind(h));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  return timed(h, KK_AUX, st, "coherence intensity backward", [&] {
+    return launch_coh_diag_backward(grad_intensity, static_cast<float2*>(grad_gamma), g->batch, g->ny * g->nx, st);
+  });
+}
+
+// ----------------------------------------------------------------------------- instrumentation
+
+top_status top_profile_enable(top_handle h, int enable) {
+  if (!h) return fail(TOP_ERR_INVALID_ARG, "handle is NULL");
+  h->prof = enable != 0;
+  return TOP_OK;
+}
+
+top_status top_profile_read(top_handle h, int cap, const char** kinds, double* ms, int64_t* count, int* n) {
+  if (!h) return fail(TOP_ERR_INVALID_ARG, "handle is NULL");
+  for (auto& pe : h->pending) {
+    float t = 0.f;
+    cudaEventSynchronize(pe.second.second);
+    if (cudaEventElapsedTime(&t, pe.second.first, pe.second.second) == cudaSuccess) {
+      h->prof_ms[pe.first] += t;
+      h->prof_cnt[pe.first] += 1;
+    }
+    h->pool.push_back(pe.second.first);
+    h->pool.push_back(pe.second.second);
+  }
+  h->pending.clear();
+  static const char* names[KK_COUNT] = {"rows_fwd", "cols", "rows_inv", "aux"};
+  int w = 0;
+  for (int k = 0; k < KK_COUNT && w < cap; ++k, ++w) {
+    if (kinds) kinds[w] = names[k];
+    if (ms) ms[w] = h->prof_ms[k];
+    if (count) count[w] = h->prof_cnt[k];
+    h->prof_ms[k] = 0;
+    h->prof_cnt[k] = 0;
+  }
+  if (n) *n = w;
+  return TOP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,283 @@
+#include "top_aux.h"
+#include "top_passes.cuh"
+
+namespace top {
+
+// out[f] = M_f * in[f] (Eq. 1)
+__global__ void __launch_bounds__(256) k_modulate(const __grid_constant__ PassParams p) {
+  const long long plane = (long long)p.ny * p.nx;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int f = blockIdx.y;
+  if (i >= plane) return;
+  const int y = int(i / p.nx), x = int(i - (long long)y * p.nx);
+  const FieldSet& fs = p.sets[p.set_of[f]];
+  const float2 m = mod_value(p.msrc, p.msrc.flags, 0, fs.src_lx, fs.src_ly, f, y, x, p.nx);
+  p.out[(long long)f * plane + i] = c_mul(ldg2(p.in + (long long)f * plane + i), m);
+}
+
+// Backward of y = M x: grad_in = conj(M) g; parameter gradients summed over the fields of a
+// group in field order (one thread per pixel, so the sum order is fixed).
+__global__ void __launch_bounds__(256) k_modulate_backward(const __grid_constant__ PassParams p) {
+  const long long plane = (long long)p.ny * p.nx;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= plane) return;
+  const int y = int(i / p.nx), x = int(i - (long long)y * p.nx);
+  const int f0 = blockIdx.y * p.group, f1 = min(f0 + p.group, p.nfields);
+  float gp = 0.f, ga = 0.f;
+  float2 gm = make_float2(0.f, 0.f);
+  const ModDev& m = p.msrc;
+  for (int f = f0; f < f1; ++f) {
+    const FieldSet& fs = p.sets[p.set_of[f]];
+    const float2 g = ldg2(p.in + (long long)f * plane + i);
+    const float2 mv = mod_value(m, m.flags, 0, fs.src_lx, fs.src_ly, f, y, x, p.nx);
+    if (p.out) p.out[(long long)f * plane + i] = c_mulc(g, mv);
+    if (p.psi) {
+      const float2 xs = ldg2(p.psi + (long long)f * plane + i);
+      if (p.part_phase) {
+        const float2 ys = c_mul(mv, xs);
+        gp += fmaf(g.y, ys.x, -g.x * ys.y);
+      }
+      if (p.part_amp) {
+        const float2 d = c_mul(mod_value(m, m.flags & ~TOP_MOD_AMPLITUDE, 0, fs.src_lx, fs.src_ly, f, y, x, p.nx), xs);
+        ga += fmaf(g.x, d.x, g.y * d.y);
+      }
+      if (p.part_mask) {
+        const float2 r = c_mul(mod_value(m, m.flags & ~TOP_MOD_COMPLEX, 0, fs.src_lx, fs.src_ly, f, y, x, p.nx), xs);
+        gm = c_add(gm, c_mulc(g, r));
+      }
+    }
+  }
+  if (p.psi) {
+    const long long o = (long long)blockIdx.y * plane + i;  // group plane (shared mask: one group)
+    if (p.part_phase) p.part_phase[o] = p.part_accumulate ? p.part_phase[o] + gp : gp;
+    if (p.part_amp) p.part_amp[o] = p.part_accumulate ? p.part_amp[o] + ga : ga;
+    if (p.part_mask) p.part_mask[o] = p.part_accumulate ? c_add(p.part_mask[o], gm) : gm;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_reduce_partials(const float* part_phase, const float* part_amp,
+                                                         const float2* part_mask, int ngroups, long long plane,
+                                                         float* phase, float* amp, float2* mask) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= plane) return;
+  if (phase) {
+    float s = 0.f;
+    for (int g = 0; g < ngroups; ++g) s += part_phase[(long long)g * plane + i];
+    phase[i] = s;
+  }
+  if (amp) {
+    float s = 0.f;
+    for (int g = 0; g < ngroups; ++g) s += part_amp[(long long)g * plane + i];
+    amp[i] = s;
+  }
+  if (mask) {
+    float2 s = make_float2(0.f, 0.f);
+    for (int g = 0; g < ngroups; ++g) s = c_add(s, part_mask[(long long)g * plane + i]);
+    mask[i] = s;
+  }
+}
+
+// MSE: each of kMseBlocks blocks sums a fixed strided subset in float64 (fixed tree order),
+// then one block sums the partials in a fixed order.
+__global__ void __launch_bounds__(256) k_mse_partial(long long n, const float* I, const float* T, float* grad,
+                                                     double* partial) {
+  __shared__ double red[256];
+  double acc = 0.0;
+  const float scale = float(2.0 / double(n));
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float r = I[i] - T[i];
+    acc += double(r) * double(r);
+    if (grad) grad[i] = scale * r;
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+__global__ void __launch_bounds__(256) k_mse_final(long long n, const double* partial, int np, double* loss) {
+  __shared__ double red[256];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) acc += partial[i];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *loss = red[0] / double(n);
+}
+
+cudaError_t launch_modulate(const PassParams& p, cudaStream_t s) {
+  const long long plane = (long long)p.ny * p.nx;
+  dim3 grid(unsigned((plane + 255) / 256), p.nfields);
+  TOP_LAUNCH(k_modulate, grid, 256, 0, s, p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_modulate_backward(const PassParams& p, cudaStream_t s) {
+  const long long plane = (long long)p.ny * p.nx;
+  dim3 grid(unsigned((plane + 255) / 256), (p.nfields + p.group - 1) / p.group);
+  TOP_LAUNCH(k_modulate_backward, grid, 256, 0, s, p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_partials(const float* part_phase, const float* part_amp, const float2* part_mask,
+                                   int ngroups, long long plane, float* phase, float* amp, float2* mask,
+                                   cudaStream_t s) {
+  TOP_LAUNCH(k_reduce_partials, unsigned((plane + 255) / 256), 256, 0, s, part_phase, part_amp, part_mask, ngroups,
+             plane, phase, amp, mask);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mse(long long n, const float* I, const float* T, float* grad, double* partial, double* loss,
+                       cudaStream_t s) {
+  TOP_LAUNCH(k_mse_partial, kMseBlocks, 256, 0, s, n, I, T, grad, partial);
+  TOP_LAUNCH(k_mse_final, 1, 256, 0, s, n, partial, kMseBlocks, loss);
+  return cudaGetLastError();
+}
+
+}  // namespace top
+
+namespace top {
+
+// ----------------------------------------------------------------------------- coherence
+
+__device__ __forceinline__ float2 coh_mask(const PassParams& p, int r) {
+  const int y = r / p.nx, x = r - (r / p.nx) * p.nx;
+  const FieldSet& fs = p.sets[0];
+  return mod_value(p.msrc, p.msrc.flags, 0, fs.src_lx, fs.src_ly, 0, y, x, p.nx);
+}
+
+// out(r1, r2) = M(r1) conj(M(r2)) in(r1, r2)  (Eq. 12), or its conjugate factor for the backward
+__global__ void __launch_bounds__(256) k_coh_modulate(const float2* in, float2* out, const __grid_constant__ PassParams p,
+                                                      int n, int conj_mask) {
+  const int r2 = blockIdx.x * blockDim.x + threadIdx.x;
+  const int r1 = blockIdx.y;
+  const long long b = blockIdx.z;
+  if (r2 >= n) return;
+  float2 d = c_mulc(coh_mask(p, r1), coh_mask(p, r2));
+  if (conj_mask) d = c_conj(d);
+  const long long i = (b * n + r1) * n + r2;
+  out[i] = c_mul(in[i], d);
+}
+
+// batched square transpose through a 32 x 33 shared tile
+__global__ void __launch_bounds__(256) k_transpose(const float2* in, float2* out, int n) {
+  __shared__ float2 tile[32][33];
+  const long long base = (long long)blockIdx.z * n * n;
+  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+  for (int j = threadIdx.y; j < 32; j += 8) {
+    const int r = by + j, c = bx + threadIdx.x;
+    if (r < n && c < n) tile[j][threadIdx.x] = in[base + (long long)r * n + c];
+  }
+  __syncthreads();
+  for (int j = threadIdx.y; j < 32; j += 8) {
+    const int r = bx + j, c = by + threadIdx.x;
+    if (r < n && c < n) out[base + (long long)r * n + c] = tile[threadIdx.x][j];
+  }
+}
+
+__global__ void __launch_bounds__(256) k_coh_diag(const float2* gamma, float* inten, int n) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  const long long b = blockIdx.y;
+  if (r < n) inten[b * n + r] = gamma[(b * n + r) * n + r].x;
+}
+
+__global__ void __launch_bounds__(256) k_coh_diag_backward(const float* gI, float2* grad, int n) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  const long long b = blockIdx.y;
+  if (r < n) grad[(b * n + r) * n + r] = make_float2(gI[b * n + r], 0.f);
+}
+
+// row term: one block per r, fixed tree order over s; batch summed in order
+__global__ void __launch_bounds__(256) k_coh_grad_rows(const float2* G, const float2* Gm, const __grid_constant__ PassParams p,
+                                                       int n, long long batch, float2* gm) {
+  __shared__ float2 red[256];
+  const int r = blockIdx.x;
+  float2 acc = make_float2(0.f, 0.f);
+  for (long long b = 0; b < batch; ++b) {
+    const long long row = (b * n + r) * n;
+    for (int s = threadIdx.x; s < n; s += blockDim.x)
+      acc = c_add(acc, c_mul(c_mulc(G[row + s], Gm[row + s]), coh_mask(p, s)));
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int k = 128; k > 0; k >>= 1) {
+    if (threadIdx.x < k) red[threadIdx.x] = c_add(red[threadIdx.x], red[threadIdx.x + k]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) gm[r] = red[0];
+}
+
+// column term: one thread per r, loop over s in order; then the parameter gradients
+__global__ void __launch_bounds__(256) k_coh_grad_cols(const float2* G, const float2* Gm, const __grid_constant__ PassParams p,
+                                                       int n, long long batch, const float2* gm_rows, float* gphase,
+                                                       float* gamp, float2* gmask) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  float2 acc = gm_rows[r];
+  for (long long b = 0; b < batch; ++b)
+    for (int s = 0; s < n; ++s) {
+      const long long i = (b * n + s) * n + r;
+      acc = c_add(acc, c_mul(c_mulc(Gm[i], G[i]), coh_mask(p, s)));
+    }
+  // acc = g_M(r) for the complex mask value M(r)
+  const int y = r / p.nx, x = r - (r / p.nx) * p.nx;
+  const FieldSet& fs = p.sets[0];
+  const ModDev& m = p.msrc;
+  const float2 mv = mod_value(m, m.flags, 0, fs.src_lx, fs.src_ly, 0, y, x, p.nx);
+  if (gphase) gphase[r] = fmaf(mv.x, acc.y, -mv.y * acc.x);  // Im(conj(M) g_M)
+  if (gamp) {
+    const float2 ra = mod_value(m, m.flags & ~TOP_MOD_AMPLITUDE, 0, fs.src_lx, fs.src_ly, 0, y, x, p.nx);
+    gamp[r] = fmaf(acc.x, ra.x, acc.y * ra.y);  // Re(conj(g_M) R_A)
+  }
+  if (gmask) {
+    const float2 rc = mod_value(m, m.flags & ~TOP_MOD_COMPLEX, 0, fs.src_lx, fs.src_ly, 0, y, x, p.nx);
+    gmask[r] = c_mulc(acc, rc);  // g_M conj(R_C)
+  }
+}
+
+cudaError_t launch_coh_modulate(const float2* in, float2* out, const PassParams& p, long long batch, int conj_mask,
+                                cudaStream_t s) {
+  const int n = p.ny * p.nx;
+  dim3 grid((n + 255) / 256, n, unsigned(batch));
+  TOP_LAUNCH(k_coh_modulate, grid, 256, 0, s, in, out, p, n, conj_mask);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_transpose(const float2* in, float2* out, long long batch, int n, cudaStream_t s) {
+  dim3 grid((n + 31) / 32, (n + 31) / 32, unsigned(batch));
+  TOP_LAUNCH(k_transpose, grid, dim3(32, 8), 0, s, in, out, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coh_diag(const float2* gamma, float* inten, long long batch, int n, cudaStream_t s) {
+  dim3 grid((n + 255) / 256, unsigned(batch));
+  TOP_LAUNCH(k_coh_diag, grid, 256, 0, s, gamma, inten, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coh_diag_backward(const float* gI, float2* grad, long long batch, int n, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(grad, 0, sizeof(float2) * size_t(batch) * n * n, s);
+  if (e != cudaSuccess) return e;
+  dim3 grid((n + 255) / 256, unsigned(batch));
+  TOP_LAUNCH(k_coh_diag_backward, grid, 256, 0, s, gI, grad, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coh_mask_grads(const float2* G, const float2* gamma_in, const PassParams& p, long long batch,
+                                  float2* gm_work, float* grad_phase, float* grad_amp, float2* grad_mask,
+                                  cudaStream_t s) {
+  const int n = p.ny * p.nx;
+  TOP_LAUNCH(k_coh_grad_rows, n, 256, 0, s, G, gamma_in, p, n, batch, gm_work);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  TOP_LAUNCH(k_coh_grad_cols, (n + 255) / 256, 256, 0, s, G, gamma_in, p, n, batch, gm_work, grad_phase, grad_amp, grad_mask);
+  return cudaGetLastError();
+}
+
+}  // namespace top

@@ -1,0 +1,37 @@
+// Auxiliary kernels: standalone modulation (Eq. 1) and its backward, deterministic
+// reductions of modulation-gradient partials, the MSE detector loss.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "top_internal.h"
+
+namespace top {
+
+constexpr int kMseBlocks = 1024;
+
+cudaError_t launch_modulate(const PassParams& p, cudaStream_t s);
+cudaError_t launch_modulate_backward(const PassParams& p, cudaStream_t s);
+cudaError_t launch_reduce_partials(const float* part_phase, const float* part_amp, const float2* part_mask,
+                                   int ngroups, long long plane, float* phase, float* amp, float2* mask,
+                                   cudaStream_t s);
+cudaError_t launch_mse(long long n, const float* I, const float* T, float* grad, double* partial, double* loss,
+                       cudaStream_t s);
+
+}  // namespace top
+
+namespace top {
+
+// Mutual coherence (Eq. 12-13), tensors [batch][n][n] with n = ny * nx.
+cudaError_t launch_coh_modulate(const float2* in, float2* out, const PassParams& p, long long batch, int conj_mask,
+                                cudaStream_t s);
+cudaError_t launch_transpose(const float2* in, float2* out, long long batch, int n, cudaStream_t s);
+cudaError_t launch_coh_diag(const float2* gamma, float* inten, long long batch, int n, cudaStream_t s);
+cudaError_t launch_coh_diag_backward(const float* gI, float2* grad, long long batch, int n, cudaStream_t s);
+// g_M(r) = sum_s G(r,s) conj(Gm(r,s)) M(s) + sum_s conj(G(s,r)) Gm(s,r) M(s), summed over the batch,
+// then turned into phase / amplitude / complex-mask gradients.
+cudaError_t launch_coh_mask_grads(const float2* G, const float2* gamma_in, const PassParams& p, long long batch,
+                                  float2* gm_work, float* grad_phase, float* grad_amp, float2* grad_mask,
+                                  cudaStream_t s);
+
+}  // namespace top

@@ -1,0 +1,33 @@
+// Registry of the instantiated FFT engines (one translation unit per group so the
+// build compiles them in parallel).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "top_internal.h"
+
+namespace top {
+
+struct EngineInfo {
+  int M;      // line length handled (half of an even padded size)
+  int G;      // threads per line
+  int NS;     // number of radix stages
+  int R[4];   // radices
+  int tw_size;
+};
+
+enum PassKind : int { PASS_ROWS_FWD = 0, PASS_COLS = 1, PASS_ROWS_INV = 2 };
+
+#define TOP_DECLARE_UNIT(name)                                                                        \
+  bool engine_info_##name(int M, EngineInfo* info);                                                   \
+  cudaError_t launch_pass_##name(int kind, int M, const PassParams& p, cudaStream_t s, bool* found);
+
+TOP_DECLARE_UNIT(small)
+TOP_DECLARE_UNIT(mid)
+TOP_DECLARE_UNIT(m1024)
+TOP_DECLARE_UNIT(large)
+TOP_DECLARE_UNIT(mixed)
+
+#undef TOP_DECLARE_UNIT
+
+}  // namespace top

@@ -1,0 +1,102 @@
+// Host/device shared structures of the propagation library.
+//
+// Every launch receives its parameters by value (a PassParams of a few KB in the
+// kernel parameter space), so a call needs no host-to-device copies and stays
+// capturable in a CUDA graph once its tables exist.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/top.h"
+
+namespace top {
+
+constexpr int kMaxSets = 24;      // distinct (lambda, z) parameter sets per launch
+constexpr int kMaxFields = 2048;  // fields per launch (larger batches run in chunks)
+
+// One (lambda, z) parameter set: separable factors of the transfer function and of
+// the lenses, precomputed in float64 on the host and rounded to float32.
+//   H(kx, ky) = cg * hx[kx].ex * hy[ky].ey * exp(i cr g(ux + uy)) (AS), cg * ex * ey (Fresnel)
+// with u = lambda^2 (fx^2 + fy^2), g(u) = sqrt(1 - u) - 1 + u/2 = -(u^2/4) / (sqrt(1-u) + 1 - u/2),
+// ex = exp(-i pi lambda z fx^2), cg = exp(2 pi i z / lambda) / (Py Px), cr = 2 pi z / lambda.
+struct FieldSet {
+  const float4* hx;      // [Px] by frequency index kx: {ex.re, ex.im, ux, 0}
+  const float4* hy;      // [Py] by frequency index ky
+  const int* kcut;       // [Px] or null: largest |signed ky| that propagates in column kx (-1: none)
+  const float2* src_lx;  // lens factor tables of the source-side modulation: [nx], [ny]
+  const float2* src_ly;
+  const float2* epi_lx;  // lens factor tables of the epilogue-side modulation
+  const float2* epi_ly;
+  float2 cg;
+  float cr;
+  float w;               // unused padding
+};
+
+// Element modulation (Eq. 1) applied in a prologue or epilogue.
+struct ModDev {
+  uint32_t flags;          // TOP_MOD_*
+  int conj;                // apply conj(M)
+  const float2* cmask;     // complex mask
+  const float* amp;        // amplitude
+  const float* phase;      // phase
+  long long stride;        // elements between consecutive fields' masks (0 = shared)
+  const int2* circ;        // [ny] inclusive x range inside the aperture per row (x > y: empty)
+};
+
+enum SrcKind : int {
+  SRC_FIELD = 0,      // v = modsrc * in[f]
+  SRC_INTENSITY = 1,  // v = modsrc * 2 w_f gI[f / group] psi[f]
+};
+
+enum EpiKind : int {
+  EPI_FIELD = 0,      // out[f] = modepi * v
+  EPI_INTENSITY = 1,  // I[g] += w_f |modepi * v|^2 over the group; optional out[f] = modepi * v
+  EPI_MODGRAD = 2,    // gradient of a modulation y = M x: grad_in = conj(M) v, grads of M (partials)
+};
+
+struct PassParams {
+  // geometry of the padded problem
+  int ny, nx;      // field samples
+  int Py, Px;      // padded sizes (even; each handled as two interleaved halves)
+  int My, Mx;      // Py / 2, Px / 2
+  int oy, ox;      // offset of the field in the padded grid
+  int nfields;     // fields in this launch
+  int group;       // fields per epilogue group (R2 grid.y = ceil(nfields / group))
+  int src_group;   // fields sharing one intensity-gradient plane (SRC_INTENSITY)
+  int in_repeat;   // SRC_FIELD: output field f reads input field f / in_repeat
+  int method;      // top_method
+  int adjoint;     // use conj(H)
+  int src_kind;
+  int epi_kind;
+  int fp64_r;      // reserved
+
+  // buffers (element strides per field)
+  const float2* in;   long long in_stride;
+  float2* ws;         long long ws_stride;   // pass workspace [field][Px][ny]
+  float2* out;        long long out_stride;
+  float* outf;        long long outf_stride; // intensity output per group / partial sums per group
+  const float2* psi;  long long psi_stride;  // saved field (SRC_INTENSITY) or saved input x (EPI_MODGRAD)
+  const float* gI;    long long gI_stride;   // intensity gradient per group (SRC_INTENSITY)
+  const float* weights;                      // per field or null
+  float* part_phase;  float* part_amp;  float2* part_mask;  long long part_stride;  // EPI_MODGRAD partials per group
+  int part_accumulate;                       // add to the partials instead of overwriting (later chunks)
+
+  // engine tables
+  const float2* twx;  // stage twiddles of the x engine
+  const float2* twy;
+  const float2* wpx;  // exp(-2 pi i p / Px), p < Mx
+  const float2* wpy;
+
+  ModDev msrc;  // modulation applied to the R1 source
+  ModDev mepi;  // modulation applied in the R2 epilogue
+
+  int nsets;
+  FieldSet sets[kMaxSets];
+  unsigned char set_of[kMaxFields];
+};
+
+// Kernel launch timing kinds (instrumentation)
+enum KernelKind : int { KK_ROWS_FWD = 0, KK_COLS, KK_ROWS_INV, KK_AUX, KK_COUNT };
+
+}  // namespace top

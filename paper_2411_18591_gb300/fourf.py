@@ -1,0 +1,110 @@
+"""Polarised, polychromatic 4f imaging system with a trainable pupil phase (Fig. 1, Listing 5).
+
+A sequence of library calls, no arithmetic of its own:
+
+  F1  psi1 = lens1 * P_f(obj)               (object broadcast over the wavelengths, input_repeat)
+  F2  psi2 = P_f(psi1)                       (in place)
+  F3  psi3 = lens2 * P_f(pupil * psi2)       (pupil = circ(R) exp(i phi))
+  F4  psi4 = P_f(psi3), I = sum over each object's component and wavelength fields of |psi4|^2 (Eq. 14)
+  L   = mean((I - T)^2), dL/dI
+  B4  g3 = P_f^H(2 dL/dI psi4)               (intensity backward)
+  B3  dL/dphi = sum_b Im(g_y conj(pupil psi2)),  g_y = P_f^H(conj(lens2) g3)
+
+Fields are ordered (object, component, wavelength), so each object's fields are
+consecutive (one intensity group) and each (object, component) input feeds its
+consecutive wavelength fields. Four forward and two backward propagations per
+field per step.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import torch
+
+from . import binding as B
+
+
+@dataclass
+class FourF:
+    n: int = 1024
+    d: float = 5e-6
+    f: float = 0.2
+    lens_radius: float = 2.56e-3
+    pupil_radius: float = 1.0e-3
+    objects: int = 16
+    comps: int = 3
+    wavelengths: tuple = ()
+    pad: float = 2.0
+    method: str = "as"
+
+    @property
+    def repeat(self) -> int:
+        return len(self.wavelengths)
+
+    @property
+    def batch(self) -> int:
+        return self.objects * self.comps * self.repeat
+
+    @property
+    def group(self) -> int:
+        return self.comps * self.repeat
+
+    def field_lambdas(self):
+        return list(self.wavelengths) * (self.objects * self.comps)
+
+    FWD_PROPS = 4
+    BWD_PROPS = 2
+
+    def lens(self) -> B.Modulation:
+        return B.Modulation(focal_length=self.f, radius=self.lens_radius)
+
+    def pupil(self, phase: torch.Tensor) -> B.Modulation:
+        return B.Modulation(phase=phase, radius=self.pupil_radius)
+
+    def step(self, obj: torch.Tensor, phase: torch.Tensor, target: torch.Tensor, grad_phase: torch.Tensor,
+             buffers: dict | None = None):
+        """One forward + backward pass; returns (loss device scalar, intensity). grad_phase is overwritten."""
+        lam = self.field_lambdas()
+        d, f, pad, m = self.d, self.f, self.pad, self.method
+        bufs = buffers if buffers is not None else {}
+        shape = (self.batch, self.n, self.n)
+        if "a" not in bufs:
+            bufs["a"] = torch.empty(shape, dtype=torch.complex64, device=obj.device)
+            bufs["b"] = torch.empty(shape, dtype=torch.complex64, device=obj.device)
+        a, b = bufs["a"], bufs["b"]
+        lens = self.lens()
+        pupil = self.pupil(phase)
+        B.top_propagate(obj, d, d, lam, f, pad, m, post=lens, out=a, input_repeat=self.repeat)       # F1
+        B.top_propagate(a, d, d, lam, f, pad, m, out=a)                                               # F2 (psi2 in a)
+        B.top_propagate(a, d, d, lam, f, pad, m, pre=pupil, post=lens, out=b)                         # F3
+        inten, _ = _intensity_into(b, b, self, lam)                                                   # F4 (psi4 in b)
+        loss, g_i = B.top_mse_loss(inten, target)
+        _intensity_backward_into(b, g_i, b, self, lam)                                                # B4 (g3 in b)
+        B.top_propagate_backward(b, d, d, lam, f, pad, m, pre=pupil, post=lens, saved_in=a,
+                                 want_grad_in=False, grad_phase=grad_phase)                           # B3
+        return loss, inten
+
+
+def _intensity_into(field, out_field, sysm: FourF, lam):
+    import ctypes as C
+    from . import _lib
+    b, ny, nx = field.shape
+    inten = torch.empty((b // sysm.group, ny, nx), dtype=torch.float32, device=field.device)
+    lams, zs, n = B._lz(lam, sysm.f, b)
+    g = B.make_grid(b, ny, nx, sysm.d, sysm.d, sysm.pad, sysm.method)
+    _lib.check(_lib.load().top_propagate_intensity(B.handle(field.device), C.byref(g), field.data_ptr(),
+                                                   out_field.data_ptr(), inten.data_ptr(), sysm.group, None, lams,
+                                                   zs, n, None, None, B._stream(field)))
+    return inten, out_field
+
+
+def _intensity_backward_into(psi, g_i, grad_in, sysm: FourF, lam):
+    import ctypes as C
+    from . import _lib
+    b, ny, nx = psi.shape
+    lams, zs, n = B._lz(lam, sysm.f, b)
+    g = B.make_grid(b, ny, nx, sysm.d, sysm.d, sysm.pad, sysm.method)
+    _lib.check(_lib.load().top_propagate_intensity_backward(B.handle(psi.device), C.byref(g), psi.data_ptr(),
+                                                            g_i.data_ptr(), grad_in.data_ptr(), sysm.group, None,
+                                                            lams, zs, n, None, None, None, B._stream(psi)))
+    return grad_in
