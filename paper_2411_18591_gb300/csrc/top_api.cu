@@ -647,6 +647,7 @@ top_status run_propagation(top_handle h, const Request& q, cudaStream_t st) {
   p.in_stride = plane;
   p.out_stride = plane;
   p.psi_stride = plane;
+  p.xs_stride = plane;
   p.gI_stride = plane;
   p.outf_stride = plane;
   p.part_stride = plane;
@@ -699,7 +700,7 @@ top_status run_propagation(top_handle h, const Request& q, cudaStream_t st) {
     p.out = q.out ? static_cast<float2*>(q.out) + pos * plane : nullptr;
     p.outf = q.outf ? q.outf + (pos / group) * plane : nullptr;
     if (q.epi_kind == EPI_MODGRAD) {
-      p.psi = want_pgrads ? static_cast<const float2*>(gr->saved_in) + pos * plane : nullptr;
+      p.xs = want_pgrads ? static_cast<const float2*>(gr->saved_in) + pos * plane : nullptr;
       if (partials) {
         p.part_phase = part_phase;
         p.part_amp = part_amp;
@@ -959,7 +960,7 @@ top_status top_modulate_backward(top_handle h, const top_grid* g, const top_mod*
     p.nfields = int(n);
     p.in = static_cast<const float2*>(grad_out) + pos * plane;
     p.out = grad_in ? static_cast<float2*>(grad_in) + pos * plane : nullptr;
-    p.psi = pg ? static_cast<const float2*>(grads->saved_in) + pos * plane : nullptr;
+    p.xs = pg ? static_cast<const float2*>(grads->saved_in) + pos * plane : nullptr;
     p.msrc = offset_mod(base, pos);
     const long long goff = shared ? 0 : pos * plane;
     p.part_phase = pg && grads->grad_phase ? grads->grad_phase + goff : nullptr;

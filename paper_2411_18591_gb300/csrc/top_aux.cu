@@ -31,8 +31,8 @@ __global__ void __launch_bounds__(256) k_modulate_backward(const __grid_constant
     const float2 g = ldg2(p.in + (long long)f * plane + i);
     const float2 mv = mod_value(m, m.flags, 0, fs.src_lx, fs.src_ly, f, y, x, p.nx);
     if (p.out) p.out[(long long)f * plane + i] = c_mulc(g, mv);
-    if (p.psi) {
-      const float2 xs = ldg2(p.psi + (long long)f * plane + i);
+    if (p.xs) {
+      const float2 xs = ldg2(p.xs + (long long)f * plane + i);
       if (p.part_phase) {
         const float2 ys = c_mul(mv, xs);
         gp += fmaf(g.y, ys.x, -g.x * ys.y);
@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(256) k_modulate_backward(const __grid_constant
       }
     }
   }
-  if (p.psi) {
+  if (p.xs) {
     const long long o = (long long)blockIdx.y * plane + i;  // group plane (shared mask: one group)
     if (p.part_phase) p.part_phase[o] = p.part_accumulate ? p.part_phase[o] + gp : gp;
     if (p.part_amp) p.part_amp[o] = p.part_accumulate ? p.part_amp[o] + ga : ga;

@@ -76,7 +76,8 @@ struct PassParams {
   float2* ws;         long long ws_stride;   // pass workspace [field][Px][ny]
   float2* out;        long long out_stride;
   float* outf;        long long outf_stride; // intensity output per group / partial sums per group
-  const float2* psi;  long long psi_stride;  // saved field (SRC_INTENSITY) or saved input x (EPI_MODGRAD)
+  const float2* psi;  long long psi_stride;  // saved output field (SRC_INTENSITY)
+  const float2* xs;   long long xs_stride;   // saved input x of the modulation (EPI_MODGRAD, modulate backward)
   const float* gI;    long long gI_stride;   // intensity gradient per group (SRC_INTENSITY)
   const float* weights;                      // per field or null
   float* part_phase;  float* part_amp;  float2* part_mask;  long long part_stride;  // EPI_MODGRAD partials per group

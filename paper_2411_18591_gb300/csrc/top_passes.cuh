@@ -235,7 +235,7 @@ __device__ __forceinline__ void epilogue(const PassParams& p, const FieldSet& fs
     const float2 mv = mod_value(m, m.flags, 0, fs.epi_lx, fs.epi_ly, f, y, x, p.nx);
     if (p.out) p.out[(long long)f * p.out_stride + idx] = c_mulc(val, mv);  // conj(M) dL/dy
     if (p.part_phase || p.part_amp || p.part_mask) {
-      const float2 xs = ldg2(p.psi + (long long)f * p.psi_stride + idx);
+      const float2 xs = ldg2(p.xs + (long long)f * p.xs_stride + idx);
       const long long pidx = (long long)g * p.part_stride + idx;
       const bool fresh = first && !p.part_accumulate;
       if (p.part_phase) {
