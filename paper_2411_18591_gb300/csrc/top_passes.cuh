@@ -8,16 +8,20 @@
 //                incoherent sums of Eq. 14, or modulation gradients)
 //
 // Each padded line of even length P = 2M is handled as its two interleaved
-// halves (even and odd frequencies). With a field of n <= P samples at offset
-// o, the even half is the M-point DFT of the folded sequence
-// v[q] = sum_{p = q mod M} x[p - o] and the odd half that of
-// sum_{p = q mod M} x[p - o] exp(-2 pi i p / P). Zero samples of the padding are
-// never loaded or transformed, and the inverse only produces the cropped
-// window: x[p] = E[p mod M] + exp(2 pi i p / P) O[p mod M].
+// halves (even and odd frequencies), transformed by two thread groups side by
+// side. With a field of n <= P samples at offset o, the even half is the M-point
+// DFT of the folded sequence v[q] = sum_{p = q mod M} x[p - o] and the odd half
+// that of sum_{p = q mod M} x[p - o] exp(-2 pi i p / P). Zero samples of the
+// padding are never loaded or transformed, and the inverse only produces the
+// cropped window: x[p] = E[p mod M] + exp(2 pi i p / P) O[p mod M].
+//
+// Global memory is only touched by block-cooperative loops (contiguous rows,
+// contiguous columns, or ROWS-sample chunks of the transposed workspace), so
+// loads are coalesced and many are in flight per thread; the FFT groups work on
+// shared-memory copies.
 //
 // Layout of the workspace between passes: for each field, Px lines of ny
-// samples, line kpos = r Mx + k holding frequency kx = 2 k + r. The column pass
-// therefore reads and writes contiguous lines; R1 and R2 move ROWS-sample chunks.
+// samples, line kpos = r Mx + k holding frequency kx = 2 k + r.
 #pragma once
 
 #include <climits>
@@ -28,24 +32,52 @@
 
 namespace top {
 
+// Rows per block of the row passes; two thread groups (the two halves) per row.
 template <class EN>
 struct RowShape {
-  static constexpr int ROWS = (256 / EN::G) >= 2 ? (256 / EN::G) : 2;
-  static constexpr int THREADS = ROWS * EN::G;
+  static constexpr int ROWS = (256 / EN::G) >= 1 ? (256 / EN::G) : 1;
+  static constexpr int GROUPS = 2 * ROWS;
+  static constexpr int THREADS = GROUPS * EN::G;
   static constexpr int LD = ROWS + 1;  // odd tile stride: conflict-free column writes
-  static constexpr int TILE = EN::M * LD;
-  static constexpr int XCH = ROWS * EN::BUF;
-  static constexpr size_t SMEM = sizeof(float2) * (TILE > XCH ? TILE : XCH);
+  static constexpr int TILE = 2 * EN::M * LD;
+  static constexpr int XCH = GROUPS * EN::BUF;
+  static constexpr int ROWBUF = ROWS * 2 * EN::M;  // input rows (n <= P = 2M) or E/O halves of the inverse
+  static constexpr int MAX2 = TILE > XCH ? TILE : XCH;
+  static constexpr size_t SMEM = sizeof(float2) * (MAX2 > ROWBUF ? MAX2 : ROWBUF);
+  static_assert(THREADS <= 1024, "row block too large");
 };
 
+// Columns per block of the column pass; two thread groups (the two halves) per column.
 template <class EN>
 struct ColShape {
-  static constexpr int COLS = (128 / EN::G) >= 1 ? (128 / EN::G) : 1;
-  static constexpr int THREADS = COLS * EN::G;
-  static constexpr size_t SMEM = sizeof(float2) * COLS * EN::BUF;
+  static constexpr int COLS = (64 / EN::G) >= 1 ? (64 / EN::G) : 1;
+  static constexpr int GROUPS = 2 * COLS;
+  static constexpr int THREADS = GROUPS * EN::G;
+  // shared memory: per column a line of max(ny, M) samples, then one exchange buffer per group
+  static size_t smem(int ny) {
+    const int line = ny > EN::M ? ny : EN::M;
+    return sizeof(float2) * (size_t(COLS) * line + size_t(GROUPS) * EN::BUF);
+  }
+  static constexpr size_t SMEM_MAX = sizeof(float2) * (COLS * 2 * EN::M + GROUPS * EN::BUF);
 };
 
 __device__ __forceinline__ float2 ldg2(const float2* p) { return __ldg(p); }
+
+// exp(i a) for a float32 phase: two-constant Cody-Waite reduction of a to [-pi, pi]
+// (2 pi = 6.28125 + 1.9353071795864769e-3, the first part exact in a few bits) and the
+// fast sin/cos there; large arguments take the library path.
+__device__ __forceinline__ float2 cis(float a) {
+  float s, c;
+  if (fabsf(a) < 1.0e5f) {
+    const float n = rintf(a * 0.15915494309189535f);
+    float r = fmaf(-n, 6.28125f, a);
+    r = fmaf(-n, 1.9353071795864769e-3f, r);
+    __sincosf(r, &s, &c);
+  } else {
+    sincosf(a, &s, &c);
+  }
+  return make_float2(c, s);
+}
 
 // M(x, y) of Eq. 1 for field f at sample (y, x)
 __device__ __forceinline__ float2 mod_value(const ModDev& m, uint32_t flags, int conj, const float2* lx,
@@ -58,11 +90,7 @@ __device__ __forceinline__ float2 mod_value(const ModDev& m, uint32_t flags, int
   const long long idx = (long long)f * m.stride + (long long)y * nx + x;
   if (flags & TOP_MOD_COMPLEX) r = ldg2(m.cmask + idx);
   if (flags & TOP_MOD_AMPLITUDE) r = c_scale(r, __ldg(m.amp + idx));
-  if (flags & TOP_MOD_PHASE) {
-    float s, c;
-    sincosf(__ldg(m.phase + idx), &s, &c);
-    r = c_mul(r, make_float2(c, s));
-  }
+  if (flags & TOP_MOD_PHASE) r = c_mul(r, cis(__ldg(m.phase + idx)));
   if (flags & TOP_MOD_LENS) r = c_mul(r, c_mul(ldg2(lx + x), ldg2(ly + y)));
   return conj ? c_conj(r) : r;
 }
@@ -81,52 +109,55 @@ __device__ __forceinline__ float2 load_src(const PassParams& p, const FieldSet& 
   return s;
 }
 
+// Slots of half r folded from a line of n samples at offset o (the odd half carries exp(-2 pi i p / 2M);
+// the copy at p + M picks up the opposite sign).
+template <class EN>
+__device__ __forceinline__ void fold(float2 (&v)[EN::E], const float2* line, int n, int o, int r,
+                                     const float2* __restrict__ wp, int t) {
+#pragma unroll
+  for (int e = 0; e < EN::E; ++e) {
+    const int pos = EN::in_pos(t, e);
+    const int x0 = pos - o, x1 = pos + EN::M - o;
+    const float2 a0 = (x0 >= 0 && x0 < n) ? line[x0] : make_float2(0.f, 0.f);
+    const float2 a1 = (x1 >= 0 && x1 < n) ? line[x1] : make_float2(0.f, 0.f);
+    v[e] = r ? c_mul(c_sub(a0, a1), ldg2(wp + pos)) : c_add(a0, a1);
+  }
+}
+
 // ----------------------------------------------------------------------------- R1
 
 template <class EX>
 __global__ void __launch_bounds__(RowShape<EX>::THREADS) k_rows_fwd(const __grid_constant__ PassParams p) {
-  constexpr int G = EX::G, E = EX::E, M = EX::M;
-  constexpr int ROWS = RowShape<EX>::ROWS, LD = RowShape<EX>::LD;
+  using SH = RowShape<EX>;
+  constexpr int G = EX::G, E = EX::E, M = EX::M, ROWS = SH::ROWS, LD = SH::LD;
   TOP_DYN_SMEM(float2, smem);
   const int grp = threadIdx.x / G, t = threadIdx.x - grp * G;
-  const int y0 = blockIdx.x * ROWS, y = y0 + grp;
+  const int row = grp >> 1, r = grp & 1;  // two groups per row: the even and odd halves
+  const int y0 = blockIdx.x * ROWS;
+  const int nrows = min(ROWS, p.ny - y0);
   const int f = blockIdx.y;
-  const bool valid = y < p.ny;
   const FieldSet& fs = p.sets[p.set_of[f]];
-  float2* buf = smem + grp * EX::BUF;
+  const int nx = p.nx;
 
-#pragma unroll 1
-  for (int r = 0; r < 2; ++r) {
-    float2 v[E];
+  // (A) modulated input rows -> shared [ROWS][nx]
+  for (int i = threadIdx.x; i < ROWS * nx; i += SH::THREADS) {
+    const int rr = i / nx, x = i - rr * nx;
+    smem[i] = rr < nrows ? load_src(p, fs, f, y0 + rr, x) : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  float2 v[E];
+  fold<EX>(v, smem + row * nx, nx, p.ox, r, p.wpx, t);
+  __syncthreads();  // the rows alias the exchange buffers
+  EX::fwd(v, smem + grp * EX::BUF, t, p.twx);
+  __syncthreads();  // the exchange buffers alias the tile
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
-      const int pos = EX::in_pos(t, e);
-      float2 acc = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        const int x = pos + c * M - p.ox;
-        if (valid && x >= 0 && x < p.nx) {
-          float2 s = load_src(p, fs, f, y, x);
-          if (r) {
-            const float2 w = ldg2(p.wpx + pos);
-            s = c_mul(s, c ? c_neg(w) : w);
-          }
-          acc = c_add(acc, s);
-        }
-      }
-      v[e] = acc;
-    }
-    EX::fwd(v, buf, t, p.twx);
-    __syncthreads();  // line buffers alias the tile
-#pragma unroll
-    for (int e = 0; e < E; ++e) smem[EX::bin(t, e) * LD + grp] = v[e];
-    __syncthreads();
-    float2* dst = p.ws + (long long)f * p.ws_stride + (long long)(r * M) * p.ny;
-    for (int idx = threadIdx.x; idx < M * ROWS; idx += blockDim.x) {
-      const int k = idx / ROWS, row = idx - (idx / ROWS) * ROWS;
-      if (y0 + row < p.ny) dst[(long long)k * p.ny + y0 + row] = smem[k * LD + row];
-    }
-    __syncthreads();
+  for (int e = 0; e < E; ++e) smem[(r * M + EX::bin(t, e)) * LD + row] = v[e];
+  __syncthreads();
+  // (B) transposed store: ROWS-sample chunks of the 2M lines
+  float2* dst = p.ws + (long long)f * p.ws_stride + y0;
+  for (int i = threadIdx.x; i < 2 * M * ROWS; i += SH::THREADS) {
+    const int k = i / ROWS, rr = i - k * ROWS;
+    if (rr < nrows) dst[(long long)k * p.ny + rr] = smem[k * LD + rr];
   }
 }
 
@@ -144,72 +175,67 @@ __device__ __forceinline__ float2 transfer_value(const PassParams& p, const Fiel
     // AS remainder beyond the separable Fresnel phase: cr * g(u), g(u) = -(u^2/4)/(sqrt(1-u) + 1 - u/2)
     const float u = ux + hy.z;
     const float sq = sqrtf(fmaxf(1.f - u, 0.f));
-    const float rr = fs.cr * (-0.25f * u * u) / (sq + 1.f - 0.5f * u);
-    float s, c;
-    sincosf(rr, &s, &c);
-    h = c_mul(h, make_float2(c, s));
+    const float rr = __fdividef(fs.cr * (-0.25f * u * u), sq + 1.f - 0.5f * u);
+    h = c_mul(h, cis(rr));
   }
   return p.adjoint ? c_conj(h) : h;
 }
 
 template <class EY>
 __global__ void __launch_bounds__(ColShape<EY>::THREADS) k_cols(const __grid_constant__ PassParams p) {
-  constexpr int G = EY::G, E = EY::E, M = EY::M, COLS = ColShape<EY>::COLS;
+  using SH = ColShape<EY>;
+  constexpr int G = EY::G, E = EY::E, M = EY::M, COLS = SH::COLS;
   TOP_DYN_SMEM(float2, smem);
   const int grp = threadIdx.x / G, t = threadIdx.x - grp * G;
-  const int col = blockIdx.x * COLS + grp;
+  const int cl = grp >> 1, r = grp & 1;
+  const int ny = p.ny;
+  const int line_len = ny > M ? ny : M;
+  const int col0 = blockIdx.x * COLS;
+  const int ncols = min(COLS, p.Px - col0);
   const int f = blockIdx.y;
-  const bool valid = col < p.Px;
-  const int cc = valid ? col : 0;
   const FieldSet& fs = p.sets[p.set_of[f]];
-  float2* buf = smem + grp * EY::BUF;
-  float2* line = p.ws + (long long)f * p.ws_stride + (long long)cc * p.ny;
+  float2* lines = smem;                                   // [COLS][line_len]
+  float2* xbuf = smem + COLS * line_len + grp * EY::BUF;  // this group's exchange buffer
+  float2* gcols = p.ws + (long long)f * p.ws_stride + (long long)col0 * ny;
 
-  const int rx = cc >= p.Mx ? 1 : 0;
-  const int kx = 2 * (cc - rx * p.Mx) + rx;
+  // (A) the block's columns (contiguous in the workspace) -> shared
+  for (int i = threadIdx.x; i < COLS * ny; i += SH::THREADS) {
+    const int c = i / ny, yy = i - c * ny;
+    lines[c * line_len + yy] = c < ncols ? gcols[i] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  const int col = min(col0 + cl, p.Px - 1);
+  const int rx = col >= p.Mx ? 1 : 0;
+  const int kx = 2 * (col - rx * p.Mx) + rx;
   const float4 hx = __ldg(fs.hx + kx);
   const float2 cxh = c_mul(fs.cg, make_float2(hx.x, hx.y));
   const int kc = fs.kcut ? __ldg(fs.kcut + kx) : INT_MAX;
+  float2* line = lines + cl * line_len;
 
-  float2 acc[E];
   float2 v[E];
-#pragma unroll 1
-  for (int r = 0; r < 2; ++r) {
+  fold<EY>(v, line, ny, p.oy, r, p.wpy, t);
+  __syncthreads();  // both halves have read the column: its line now carries the odd half's output
+  EY::fwd(v, xbuf, t, p.twy);
+#pragma unroll
+  for (int e = 0; e < E; ++e) v[e] = c_mul(v[e], transfer_value(p, fs, cxh, hx.z, kc, 2 * EY::bin(t, e) + r));
+  EY::inv(v, xbuf, t, p.twy);
+  if (r) {
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int pos = EY::in_pos(t, e);
-      float2 a = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        const int yy = pos + c * M - p.oy;
-        if (valid && yy >= 0 && yy < p.ny) {
-          float2 s = line[yy];
-          if (r) {
-            const float2 w = ldg2(p.wpy + pos);
-            s = c_mul(s, c ? c_neg(w) : w);
-          }
-          a = c_add(a, s);
-        }
-      }
-      v[e] = a;
-    }
-    EY::fwd(v, buf, t, p.twy);
-#pragma unroll
-    for (int e = 0; e < E; ++e) v[e] = c_mul(v[e], transfer_value(p, fs, cxh, hx.z, kc, 2 * EY::bin(t, e) + r));
-    EY::inv(v, buf, t, p.twy);
-    if (r == 0) {
-#pragma unroll
-      for (int e = 0; e < E; ++e) acc[e] = v[e];
+      line[pos] = c_mulc(v[e], ldg2(p.wpy + pos));  // exp(2 pi i pos / P) O[pos]
     }
   }
+  __syncthreads();
+  if (!r && cl < ncols) {
+    float2* out = gcols + (long long)cl * ny;
 #pragma unroll
-  for (int e = 0; e < E; ++e) {
-    const int pos = EY::in_pos(t, e);
-    const float2 o = c_mulc(v[e], ldg2(p.wpy + pos));
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      const int yy = pos + c * M - p.oy;
-      if (valid && yy >= 0 && yy < p.ny) line[yy] = c ? c_sub(acc[e], o) : c_add(acc[e], o);
+    for (int e = 0; e < E; ++e) {
+      const int pos = EY::in_pos(t, e);
+      const float2 o = line[pos];
+      const int y0 = pos - p.oy, y1 = pos + M - p.oy;
+      if (y0 >= 0 && y0 < ny) out[y0] = c_add(v[e], o);
+      if (y1 >= 0 && y1 < ny) out[y1] = c_sub(v[e], o);
     }
   }
 }
@@ -261,52 +287,48 @@ __device__ __forceinline__ void epilogue(const PassParams& p, const FieldSet& fs
 
 template <class EX>
 __global__ void __launch_bounds__(RowShape<EX>::THREADS) k_rows_inv(const __grid_constant__ PassParams p) {
-  constexpr int G = EX::G, E = EX::E, M = EX::M;
-  constexpr int ROWS = RowShape<EX>::ROWS, LD = RowShape<EX>::LD;
+  using SH = RowShape<EX>;
+  constexpr int G = EX::G, E = EX::E, M = EX::M, ROWS = SH::ROWS, LD = SH::LD;
   TOP_DYN_SMEM(float2, smem);
   const int grp = threadIdx.x / G, t = threadIdx.x - grp * G;
-  const int y0 = blockIdx.x * ROWS, y = y0 + grp;
-  const bool valid = y < p.ny;
+  const int row = grp >> 1, r = grp & 1;
+  const int y0 = blockIdx.x * ROWS;
+  const int nrows = min(ROWS, p.ny - y0);
   const int g = blockIdx.y;
   const int f0 = g * p.group;
   const int f1 = min(f0 + p.group, p.nfields);
-  float2* buf = smem + grp * EX::BUF;
+  const int nx = p.nx;
 
 #pragma unroll 1
   for (int f = f0; f < f1; ++f) {
     const FieldSet& fs = p.sets[p.set_of[f]];
-    float2 acc[E];
+    // (A) ROWS-sample chunks of the 2M lines -> tile [2M][LD]
+    const float2* src = p.ws + (long long)f * p.ws_stride + y0;
+    for (int i = threadIdx.x; i < 2 * M * ROWS; i += SH::THREADS) {
+      const int k = i / ROWS, rr = i - k * ROWS;
+      smem[k * LD + rr] = rr < nrows ? src[(long long)k * p.ny + rr] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
     float2 v[E];
-#pragma unroll 1
-    for (int r = 0; r < 2; ++r) {
-      __syncthreads();
-      const float2* src = p.ws + (long long)f * p.ws_stride + (long long)(r * M) * p.ny;
-      for (int idx = threadIdx.x; idx < M * ROWS; idx += blockDim.x) {
-        const int k = idx / ROWS, row = idx - (idx / ROWS) * ROWS;
-        smem[k * LD + row] = (y0 + row < p.ny) ? src[(long long)k * p.ny + y0 + row] : make_float2(0.f, 0.f);
-      }
-      __syncthreads();
 #pragma unroll
-      for (int e = 0; e < E; ++e) v[e] = smem[EX::bin(t, e) * LD + grp];
-      __syncthreads();  // tile reads done before the aliased line buffers are written
-      EX::inv(v, buf, t, p.twx);
-      if (r == 0) {
+    for (int e = 0; e < E; ++e) v[e] = smem[(r * M + EX::bin(t, e)) * LD + row];
+    __syncthreads();  // the tile aliases the exchange buffers
+    EX::inv(v, smem + grp * EX::BUF, t, p.twx);
+    __syncthreads();  // the exchange buffers alias the half-row buffers
+    // (B) both halves in natural order -> shared [r][ROWS][M]
 #pragma unroll
-        for (int e = 0; e < E; ++e) acc[e] = v[e];
-      }
+    for (int e = 0; e < E; ++e) smem[(r * ROWS + row) * M + EX::in_pos(t, e)] = v[e];
+    __syncthreads();
+    // (C) combine the halves over the cropped window, epilogue, coalesced store
+    for (int i = threadIdx.x; i < nrows * nx; i += SH::THREADS) {
+      const int rr = i / nx, x = i - rr * nx;
+      const int pp = x + p.ox;
+      const int pos = pp >= M ? pp - M : pp;
+      const float2 o = c_mulc(smem[(ROWS + rr) * M + pos], ldg2(p.wpx + pos));
+      const float2 ev = smem[rr * M + pos];
+      epilogue(p, fs, f, g, f == f0, y0 + rr, x, pp >= M ? c_sub(ev, o) : c_add(ev, o));
     }
-    if (valid) {
-#pragma unroll
-      for (int e = 0; e < E; ++e) {
-        const int pos = EX::in_pos(t, e);
-        const float2 o = c_mulc(v[e], ldg2(p.wpx + pos));
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-          const int x = pos + c * M - p.ox;
-          if (x >= 0 && x < p.nx) epilogue(p, fs, f, g, f == f0, y, x, c ? c_sub(acc[e], o) : c_add(acc[e], o));
-        }
-      }
-    }
+    __syncthreads();
   }
 }
 
@@ -331,10 +353,10 @@ cudaError_t launch_rows_fwd(const PassParams& p, cudaStream_t s) {
 template <class EY>
 cudaError_t launch_cols(const PassParams& p, cudaStream_t s) {
   using SH = ColShape<EY>;
-  static const cudaError_t attr = set_smem(k_cols<EY>, SH::SMEM);
+  static const cudaError_t attr = set_smem(k_cols<EY>, SH::SMEM_MAX);
   if (attr != cudaSuccess) return attr;
   dim3 grid((p.Px + SH::COLS - 1) / SH::COLS, p.nfields);
-  TOP_LAUNCH(k_cols<EY>, grid, SH::THREADS, SH::SMEM, s, p);
+  TOP_LAUNCH(k_cols<EY>, grid, SH::THREADS, SH::smem(p.ny), s, p);
   return cudaGetLastError();
 }
 
