@@ -38,7 +38,9 @@ struct RowShape {
   static constexpr int ROWS = (256 / EN::G) >= 1 ? (256 / EN::G) : 1;
   static constexpr int GROUPS = 2 * ROWS;
   static constexpr int THREADS = GROUPS * EN::G;
-  static constexpr int LD = ROWS + 1;  // odd tile stride: conflict-free column writes
+  // tile stride: even (16-byte pairs of rows) with a 2-way bank pattern when ROWS >= 4, else odd
+  static constexpr bool VEC = ROWS % 2 == 0 && ROWS >= 4;
+  static constexpr int LD = VEC ? ROWS + 2 : ROWS + 1;
   static constexpr int TILE = 2 * EN::M * LD;
   static constexpr int XCH = GROUPS * EN::BUF;
   static constexpr int ROWBUF = ROWS * 2 * EN::M;  // input rows (n <= P = 2M) or E/O halves of the inverse
@@ -60,6 +62,18 @@ struct ColShape {
   }
   static constexpr size_t SMEM_MAX = sizeof(float2) * (COLS * 2 * EN::M + GROUPS * EN::BUF);
 };
+
+// Group index and lane of a thread (masks when G is a power of two, so lane ranges are known).
+template <int G>
+__device__ __forceinline__ void group_lane(int tid, int& grp, int& t) {
+  if constexpr ((G & (G - 1)) == 0) {
+    grp = tid / G;
+    t = tid & (G - 1);
+  } else {
+    grp = tid / G;
+    t = tid - grp * G;
+  }
+}
 
 __device__ __forceinline__ float2 ldg2(const float2* p) { return __ldg(p); }
 
@@ -110,28 +124,42 @@ __device__ __forceinline__ float2 load_src(const PassParams& p, const FieldSet& 
 }
 
 // Slots of half r folded from a line of n samples at offset o (the odd half carries exp(-2 pi i p / 2M);
-// the copy at p + M picks up the opposite sign).
-template <class EN>
+// the copy at p + M picks up the opposite sign). X2: n = M and o = M/2 (padding exactly 2), where
+// every slot has one source, (pos + M/2) mod M, lying in the upper copy when pos < M/2.
+template <class EN, bool X2>
 __device__ __forceinline__ void fold(float2 (&v)[EN::E], const float2* line, int n, int o, int r,
                                      const float2* __restrict__ wp, int t) {
+  constexpr int M = EN::M;
 #pragma unroll
   for (int e = 0; e < EN::E; ++e) {
     const int pos = EN::in_pos(t, e);
-    const int x0 = pos - o, x1 = pos + EN::M - o;
-    const float2 a0 = (x0 >= 0 && x0 < n) ? line[x0] : make_float2(0.f, 0.f);
-    const float2 a1 = (x1 >= 0 && x1 < n) ? line[x1] : make_float2(0.f, 0.f);
-    v[e] = r ? c_mul(c_sub(a0, a1), ldg2(wp + pos)) : c_add(a0, a1);
+    if constexpr (X2) {
+      const bool upper = pos < M / 2;
+      const float2 a = line[upper ? pos + M / 2 : pos - M / 2];
+      if (r) {
+        const float2 w = ldg2(wp + pos);
+        v[e] = c_mul(a, upper ? c_neg(w) : w);
+      } else {
+        v[e] = a;
+      }
+    } else {
+      const int x0 = pos - o, x1 = pos + M - o;
+      const float2 a0 = (x0 >= 0 && x0 < n) ? line[x0] : make_float2(0.f, 0.f);
+      const float2 a1 = (x1 >= 0 && x1 < n) ? line[x1] : make_float2(0.f, 0.f);
+      v[e] = r ? c_mul(c_sub(a0, a1), ldg2(wp + pos)) : c_add(a0, a1);
+    }
   }
 }
 
 // ----------------------------------------------------------------------------- R1
 
-template <class EX>
+template <class EX, bool X2>
 __global__ void __launch_bounds__(RowShape<EX>::THREADS) k_rows_fwd(const __grid_constant__ PassParams p) {
   using SH = RowShape<EX>;
-  constexpr int G = EX::G, E = EX::E, M = EX::M, ROWS = SH::ROWS, LD = SH::LD;
+  constexpr int G = EX::G, E = EX::E, M = EX::M, ROWS = SH::ROWS, LD = SH::LD, NT = SH::THREADS;
   TOP_DYN_SMEM(float2, smem);
-  const int grp = threadIdx.x / G, t = threadIdx.x - grp * G;
+  int grp, t;
+  group_lane<G>(threadIdx.x, grp, t);
   const int row = grp >> 1, r = grp & 1;  // two groups per row: the even and odd halves
   const int y0 = blockIdx.x * ROWS;
   const int nrows = min(ROWS, p.ny - y0);
@@ -140,24 +168,34 @@ __global__ void __launch_bounds__(RowShape<EX>::THREADS) k_rows_fwd(const __grid
   const int nx = p.nx;
 
   // (A) modulated input rows -> shared [ROWS][nx]
-  for (int i = threadIdx.x; i < ROWS * nx; i += SH::THREADS) {
-    const int rr = i / nx, x = i - rr * nx;
-    smem[i] = rr < nrows ? load_src(p, fs, f, y0 + rr, x) : make_float2(0.f, 0.f);
+#pragma unroll 2
+  for (int rr = 0; rr < ROWS; ++rr) {
+    for (int x = threadIdx.x; x < nx; x += NT)
+      smem[rr * nx + x] = rr < nrows ? load_src(p, fs, f, y0 + rr, x) : make_float2(0.f, 0.f);
   }
   __syncthreads();
   float2 v[E];
-  fold<EX>(v, smem + row * nx, nx, p.ox, r, p.wpx, t);
+  fold<EX, X2>(v, smem + row * nx, nx, p.ox, r, p.wpx, t);
   __syncthreads();  // the rows alias the exchange buffers
   EX::fwd(v, smem + grp * EX::BUF, t, p.twx);
   __syncthreads();  // the exchange buffers alias the tile
 #pragma unroll
   for (int e = 0; e < E; ++e) smem[(r * M + EX::bin(t, e)) * LD + row] = v[e];
   __syncthreads();
-  // (B) transposed store: ROWS-sample chunks of the 2M lines
+  // (B) transposed store: ROWS-sample chunks of the 2M lines (pairs of rows as 16-byte stores)
   float2* dst = p.ws + (long long)f * p.ws_stride + y0;
-  for (int i = threadIdx.x; i < 2 * M * ROWS; i += SH::THREADS) {
-    const int k = i / ROWS, rr = i - k * ROWS;
-    if (rr < nrows) dst[(long long)k * p.ny + rr] = smem[k * LD + rr];
+  if (SH::VEC && nrows == ROWS && (p.ny & 1) == 0) {
+    constexpr int RP = ROWS / 2;
+    for (int i = threadIdx.x; i < 2 * M * RP; i += NT) {
+      const int k = i / RP, rp = i - k * RP;
+      const float4 two = *reinterpret_cast<const float4*>(smem + k * LD + 2 * rp);
+      *reinterpret_cast<float4*>(dst + (long long)k * p.ny + 2 * rp) = two;
+    }
+  } else {
+    for (int i = threadIdx.x; i < 2 * M * ROWS; i += NT) {
+      const int k = i / ROWS, rr = i - k * ROWS;
+      if (rr < nrows) dst[(long long)k * p.ny + rr] = smem[k * LD + rr];
+    }
   }
 }
 
@@ -181,15 +219,16 @@ __device__ __forceinline__ float2 transfer_value(const PassParams& p, const Fiel
   return p.adjoint ? c_conj(h) : h;
 }
 
-template <class EY>
+template <class EY, bool X2>
 __global__ void __launch_bounds__(ColShape<EY>::THREADS) k_cols(const __grid_constant__ PassParams p) {
   using SH = ColShape<EY>;
-  constexpr int G = EY::G, E = EY::E, M = EY::M, COLS = SH::COLS;
+  constexpr int G = EY::G, E = EY::E, M = EY::M, COLS = SH::COLS, NT = SH::THREADS;
   TOP_DYN_SMEM(float2, smem);
-  const int grp = threadIdx.x / G, t = threadIdx.x - grp * G;
+  int grp, t;
+  group_lane<G>(threadIdx.x, grp, t);
   const int cl = grp >> 1, r = grp & 1;
   const int ny = p.ny;
-  const int line_len = ny > M ? ny : M;
+  const int line_len = X2 ? M : (ny > M ? ny : M);
   const int col0 = blockIdx.x * COLS;
   const int ncols = min(COLS, p.Px - col0);
   const int f = blockIdx.y;
@@ -199,9 +238,13 @@ __global__ void __launch_bounds__(ColShape<EY>::THREADS) k_cols(const __grid_con
   float2* gcols = p.ws + (long long)f * p.ws_stride + (long long)col0 * ny;
 
   // (A) the block's columns (contiguous in the workspace) -> shared
-  for (int i = threadIdx.x; i < COLS * ny; i += SH::THREADS) {
-    const int c = i / ny, yy = i - c * ny;
-    lines[c * line_len + yy] = c < ncols ? gcols[i] : make_float2(0.f, 0.f);
+  if (line_len == ny && (ny & 1) == 0) {
+    const int n4 = ncols * ny / 2;
+    for (int i = threadIdx.x; i < n4; i += NT)
+      reinterpret_cast<float4*>(lines)[i] = reinterpret_cast<const float4*>(gcols)[i];
+  } else {
+    for (int c = 0; c < ncols; ++c)
+      for (int yy = threadIdx.x; yy < ny; yy += NT) lines[c * line_len + yy] = gcols[(long long)c * ny + yy];
   }
   __syncthreads();
   const int col = min(col0 + cl, p.Px - 1);
@@ -213,7 +256,7 @@ __global__ void __launch_bounds__(ColShape<EY>::THREADS) k_cols(const __grid_con
   float2* line = lines + cl * line_len;
 
   float2 v[E];
-  fold<EY>(v, line, ny, p.oy, r, p.wpy, t);
+  fold<EY, X2>(v, line, ny, p.oy, r, p.wpy, t);
   __syncthreads();  // both halves have read the column: its line now carries the odd half's output
   EY::fwd(v, xbuf, t, p.twy);
 #pragma unroll
@@ -233,9 +276,14 @@ __global__ void __launch_bounds__(ColShape<EY>::THREADS) k_cols(const __grid_con
     for (int e = 0; e < E; ++e) {
       const int pos = EY::in_pos(t, e);
       const float2 o = line[pos];
-      const int y0 = pos - p.oy, y1 = pos + M - p.oy;
-      if (y0 >= 0 && y0 < ny) out[y0] = c_add(v[e], o);
-      if (y1 >= 0 && y1 < ny) out[y1] = c_sub(v[e], o);
+      if constexpr (X2) {
+        if (pos < M / 2) out[pos + M / 2] = c_sub(v[e], o);
+        else out[pos - M / 2] = c_add(v[e], o);
+      } else {
+        const int y0 = pos - p.oy, y1 = pos + M - p.oy;
+        if (y0 >= 0 && y0 < ny) out[y0] = c_add(v[e], o);
+        if (y1 >= 0 && y1 < ny) out[y1] = c_sub(v[e], o);
+      }
     }
   }
 }
@@ -285,12 +333,13 @@ __device__ __forceinline__ void epilogue(const PassParams& p, const FieldSet& fs
   }
 }
 
-template <class EX>
+template <class EX, bool X2>
 __global__ void __launch_bounds__(RowShape<EX>::THREADS) k_rows_inv(const __grid_constant__ PassParams p) {
   using SH = RowShape<EX>;
-  constexpr int G = EX::G, E = EX::E, M = EX::M, ROWS = SH::ROWS, LD = SH::LD;
+  constexpr int G = EX::G, E = EX::E, M = EX::M, ROWS = SH::ROWS, LD = SH::LD, NT = SH::THREADS;
   TOP_DYN_SMEM(float2, smem);
-  const int grp = threadIdx.x / G, t = threadIdx.x - grp * G;
+  int grp, t;
+  group_lane<G>(threadIdx.x, grp, t);
   const int row = grp >> 1, r = grp & 1;
   const int y0 = blockIdx.x * ROWS;
   const int nrows = min(ROWS, p.ny - y0);
@@ -298,15 +347,25 @@ __global__ void __launch_bounds__(RowShape<EX>::THREADS) k_rows_inv(const __grid
   const int f0 = g * p.group;
   const int f1 = min(f0 + p.group, p.nfields);
   const int nx = p.nx;
+  const bool vec = SH::VEC && nrows == ROWS && (p.ny & 1) == 0;
 
 #pragma unroll 1
   for (int f = f0; f < f1; ++f) {
     const FieldSet& fs = p.sets[p.set_of[f]];
-    // (A) ROWS-sample chunks of the 2M lines -> tile [2M][LD]
+    // (A) ROWS-sample chunks of the 2M lines -> tile [2M][LD] (pairs of rows as 16-byte loads)
     const float2* src = p.ws + (long long)f * p.ws_stride + y0;
-    for (int i = threadIdx.x; i < 2 * M * ROWS; i += SH::THREADS) {
-      const int k = i / ROWS, rr = i - k * ROWS;
-      smem[k * LD + rr] = rr < nrows ? src[(long long)k * p.ny + rr] : make_float2(0.f, 0.f);
+    if (vec) {
+      constexpr int RP = ROWS / 2;
+      for (int i = threadIdx.x; i < 2 * M * RP; i += NT) {
+        const int k = i / RP, rp = i - k * RP;
+        *reinterpret_cast<float4*>(smem + k * LD + 2 * rp) =
+            *reinterpret_cast<const float4*>(src + (long long)k * p.ny + 2 * rp);
+      }
+    } else {
+      for (int i = threadIdx.x; i < 2 * M * ROWS; i += NT) {
+        const int k = i / ROWS, rr = i - k * ROWS;
+        smem[k * LD + rr] = rr < nrows ? src[(long long)k * p.ny + rr] : make_float2(0.f, 0.f);
+      }
     }
     __syncthreads();
     float2 v[E];
@@ -320,13 +379,22 @@ __global__ void __launch_bounds__(RowShape<EX>::THREADS) k_rows_inv(const __grid
     for (int e = 0; e < E; ++e) smem[(r * ROWS + row) * M + EX::in_pos(t, e)] = v[e];
     __syncthreads();
     // (C) combine the halves over the cropped window, epilogue, coalesced store
-    for (int i = threadIdx.x; i < nrows * nx; i += SH::THREADS) {
-      const int rr = i / nx, x = i - rr * nx;
-      const int pp = x + p.ox;
-      const int pos = pp >= M ? pp - M : pp;
-      const float2 o = c_mulc(smem[(ROWS + rr) * M + pos], ldg2(p.wpx + pos));
-      const float2 ev = smem[rr * M + pos];
-      epilogue(p, fs, f, g, f == f0, y0 + rr, x, pp >= M ? c_sub(ev, o) : c_add(ev, o));
+    for (int rr = 0; rr < nrows; ++rr) {
+      for (int x = threadIdx.x; x < nx; x += NT) {
+        int pos;
+        bool upper;
+        if constexpr (X2) {
+          upper = x >= M / 2;
+          pos = upper ? x - M / 2 : x + M / 2;
+        } else {
+          const int pp = x + p.ox;
+          upper = pp >= M;
+          pos = upper ? pp - M : pp;
+        }
+        const float2 o = c_mulc(smem[(ROWS + rr) * M + pos], ldg2(p.wpx + pos));
+        const float2 ev = smem[rr * M + pos];
+        epilogue(p, fs, f, g, f == f0, y0 + rr, x, upper ? c_sub(ev, o) : c_add(ev, o));
+      }
     }
     __syncthreads();
   }
@@ -340,34 +408,52 @@ inline cudaError_t set_smem(K kernel, size_t bytes) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-template <class EX>
-cudaError_t launch_rows_fwd(const PassParams& p, cudaStream_t s) {
+template <class EX, bool X2>
+cudaError_t launch_rows_fwd_t(const PassParams& p, cudaStream_t s) {
   using SH = RowShape<EX>;
-  static const cudaError_t attr = set_smem(k_rows_fwd<EX>, SH::SMEM);
+  static const cudaError_t attr = set_smem(k_rows_fwd<EX, X2>, SH::SMEM);
   if (attr != cudaSuccess) return attr;
   dim3 grid((p.ny + SH::ROWS - 1) / SH::ROWS, p.nfields);
-  TOP_LAUNCH(k_rows_fwd<EX>, grid, SH::THREADS, SH::SMEM, s, p);
+  TOP_LAUNCH((k_rows_fwd<EX, X2>), grid, SH::THREADS, SH::SMEM, s, p);
   return cudaGetLastError();
+}
+
+template <class EY, bool X2>
+cudaError_t launch_cols_t(const PassParams& p, cudaStream_t s) {
+  using SH = ColShape<EY>;
+  static const cudaError_t attr = set_smem(k_cols<EY, X2>, SH::SMEM_MAX);
+  if (attr != cudaSuccess) return attr;
+  dim3 grid((p.Px + SH::COLS - 1) / SH::COLS, p.nfields);
+  TOP_LAUNCH((k_cols<EY, X2>), grid, SH::THREADS, SH::smem(p.ny), s, p);
+  return cudaGetLastError();
+}
+
+template <class EX, bool X2>
+cudaError_t launch_rows_inv_t(const PassParams& p, cudaStream_t s) {
+  using SH = RowShape<EX>;
+  static const cudaError_t attr = set_smem(k_rows_inv<EX, X2>, SH::SMEM);
+  if (attr != cudaSuccess) return attr;
+  dim3 grid((p.ny + SH::ROWS - 1) / SH::ROWS, (p.nfields + p.group - 1) / p.group);
+  TOP_LAUNCH((k_rows_inv<EX, X2>), grid, SH::THREADS, SH::SMEM, s, p);
+  return cudaGetLastError();
+}
+
+// padding exactly 2 along an axis: n = M and the field sits at M/2
+inline bool exact2(int n, int M, int o) { return n == M && o == M / 2; }
+
+template <class EX>
+cudaError_t launch_rows_fwd(const PassParams& p, cudaStream_t s) {
+  return exact2(p.nx, p.Mx, p.ox) ? launch_rows_fwd_t<EX, true>(p, s) : launch_rows_fwd_t<EX, false>(p, s);
 }
 
 template <class EY>
 cudaError_t launch_cols(const PassParams& p, cudaStream_t s) {
-  using SH = ColShape<EY>;
-  static const cudaError_t attr = set_smem(k_cols<EY>, SH::SMEM_MAX);
-  if (attr != cudaSuccess) return attr;
-  dim3 grid((p.Px + SH::COLS - 1) / SH::COLS, p.nfields);
-  TOP_LAUNCH(k_cols<EY>, grid, SH::THREADS, SH::smem(p.ny), s, p);
-  return cudaGetLastError();
+  return exact2(p.ny, p.My, p.oy) ? launch_cols_t<EY, true>(p, s) : launch_cols_t<EY, false>(p, s);
 }
 
 template <class EX>
 cudaError_t launch_rows_inv(const PassParams& p, cudaStream_t s) {
-  using SH = RowShape<EX>;
-  static const cudaError_t attr = set_smem(k_rows_inv<EX>, SH::SMEM);
-  if (attr != cudaSuccess) return attr;
-  dim3 grid((p.ny + SH::ROWS - 1) / SH::ROWS, (p.nfields + p.group - 1) / p.group);
-  TOP_LAUNCH(k_rows_inv<EX>, grid, SH::THREADS, SH::SMEM, s, p);
-  return cudaGetLastError();
+  return exact2(p.nx, p.Mx, p.ox) ? launch_rows_inv_t<EX, true>(p, s) : launch_rows_inv_t<EX, false>(p, s);
 }
 
 }  // namespace top
