@@ -64,10 +64,11 @@ uint64_t bits(double d) {
 
 struct TransferEntry {
   float4* hx = nullptr;
-  float4* hy = nullptr;
+  float2* eyh = nullptr;
   int* kcut = nullptr;
   float2 cg;
   float cr;
+  float ly2;
 };
 
 struct top_ctx {
@@ -265,8 +266,14 @@ top_status transfer_tables(top_handle h, int Py, int Px, double dy, double dx, d
   std::vector<float4> hx, hy;
   axis(Px, dx, hx);
   axis(Py, dy, hy);
+  // y factors grouped by half (even, odd frequencies) so a column's half reads them contiguously
+  std::vector<float2> eyh(Py);
+  for (int r = 0; r < 2; ++r)
+    for (int k = 0; k < Py / 2; ++k) eyh[r * (Py / 2) + k] = make_float2(hy[2 * k + r].x, hy[2 * k + r].y);
   TOP_TRY(upload(h, hx, &te.hx));
-  TOP_TRY(upload(h, hy, &te.hy));
+  TOP_TRY(upload(h, eyh, &te.eyh));
+  const double ly = lam / (double(Py) * dy);
+  te.ly2 = float(ly * ly);
   double c, s;
   cis_pi(2.0 * z / lam, &c, &s);  // exp(2 pi i z / lambda)
   const double norm = 1.0 / (double(Py) * double(Px));
@@ -553,7 +560,8 @@ top_status run_propagation(top_handle h, const Request& q, cudaStream_t st) {
     TOP_TRY(transfer_tables(h, geo.Py, geo.Px, g->dy, g->dx, q.lam[i], q.z[i], g->method, &te));
     FieldSet fs{};
     fs.hx = te.hx;
-    fs.hy = te.hy;
+    fs.eyh = te.eyh;
+    fs.ly2 = te.ly2;
     fs.kcut = te.kcut;
     fs.cg = te.cg;
     fs.cr = te.cr;

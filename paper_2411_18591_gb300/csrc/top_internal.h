@@ -17,12 +17,13 @@ constexpr int kMaxFields = 2048;  // fields per launch (larger batches run in ch
 
 // One (lambda, z) parameter set: separable factors of the transfer function and of
 // the lenses, precomputed in float64 on the host and rounded to float32.
-//   H(kx, ky) = cg * hx[kx].ex * hy[ky].ey * exp(i cr g(ux + uy)) (AS), cg * ex * ey (Fresnel)
+//   H(kx, ky) = cg * hx[kx].ex * ey[ky] * exp(i cr g(ux + uy)) (AS), cg * ex * ey (Fresnel)
 // with u = lambda^2 (fx^2 + fy^2), g(u) = sqrt(1 - u) - 1 + u/2 = -(u^2/4) / (sqrt(1-u) + 1 - u/2),
-// ex = exp(-i pi lambda z fx^2), cg = exp(2 pi i z / lambda) / (Py Px), cr = 2 pi z / lambda.
+// ex = exp(-i pi lambda z fx^2), cg = exp(2 pi i z / lambda) / (Py Px), cr = 2 pi z / lambda;
+// uy = ly2 * sky^2 with sky the signed index of ky and ly2 = (lambda / (Py dy))^2.
 struct FieldSet {
   const float4* hx;      // [Px] by frequency index kx: {ex.re, ex.im, ux, 0}
-  const float4* hy;      // [Py] by frequency index ky
+  const float2* eyh;     // [Py] ey by half: eyh[r My + k] = ey[2k + r]
   const int* kcut;       // [Px] or null: largest |signed ky| that propagates in column kx (-1: none)
   const float2* src_lx;  // lens factor tables of the source-side modulation: [nx], [ny]
   const float2* src_ly;
@@ -30,7 +31,7 @@ struct FieldSet {
   const float2* epi_ly;
   float2 cg;
   float cr;
-  float w;               // unused padding
+  float ly2;
 };
 
 // Element modulation (Eq. 1) applied in a prologue or epilogue.

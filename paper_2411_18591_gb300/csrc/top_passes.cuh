@@ -25,6 +25,8 @@
 #pragma once
 
 #include <climits>
+#include <type_traits>
+#include <utility>
 
 #include "top_engine.cuh"
 #include "top_internal.h"
@@ -33,9 +35,13 @@
 namespace top {
 
 // Rows per block of the row passes; two thread groups (the two halves) per row.
+#ifndef TOP_ROW_THREADS
+#define TOP_ROW_THREADS 256
+#endif
+
 template <class EN>
 struct RowShape {
-  static constexpr int ROWS = (256 / EN::G) >= 1 ? (256 / EN::G) : 1;
+  static constexpr int ROWS = (TOP_ROW_THREADS / EN::G) >= 1 ? (TOP_ROW_THREADS / EN::G) : 1;
   static constexpr int GROUPS = 2 * ROWS;
   static constexpr int THREADS = GROUPS * EN::G;
   // tile stride: even (16-byte pairs of rows) with a 2-way bank pattern when ROWS >= 4, else odd
@@ -76,6 +82,20 @@ __device__ __forceinline__ void group_lane(int tid, int& grp, int& t) {
 }
 
 __device__ __forceinline__ float2 ldg2(const float2* p) { return __ldg(p); }
+
+// Calls f(std::integral_constant<int, e>) for every register slot e, so slot positions are constants.
+template <class F, int... Es>
+__device__ __forceinline__ void for_slots(F&& f, std::integer_sequence<int, Es...>) {
+  (f(std::integral_constant<int, Es>{}), ...);
+}
+
+// exp(-2 pi i pos / 2M) for the stage-0 position pos = t + G q + SP0 j of slot e, as the lane's
+// exp(-2 pi i t / 2M) times a compile-time constant.
+template <class EN, int e>
+__device__ __forceinline__ float2 slot_split_twiddle(float2 wt) {
+  constexpr int R0 = EN::radix(0), SP0 = EN::span(0);
+  return tw_const<-1, long(EN::G * (e / R0) + SP0 * (e % R0)), long(2 * EN::M)>(wt);
+}
 
 // exp(i a) for a float32 phase: two-constant Cody-Waite reduction of a to [-pi, pi]
 // (2 pi = 6.28125 + 1.9353071795864769e-3, the first part exact in a few bits) and the
@@ -135,18 +155,24 @@ __device__ __forceinline__ void fold(float2 (&v)[EN::E], const float2* line, int
     const int pos = EN::in_pos(t, e);
     if constexpr (X2) {
       const bool upper = pos < M / 2;
-      const float2 a = line[upper ? pos + M / 2 : pos - M / 2];
-      if (r) {
-        const float2 w = ldg2(wp + pos);
-        v[e] = c_mul(a, upper ? c_neg(w) : w);
-      } else {
-        v[e] = a;
-      }
+      v[e] = line[upper ? pos + M / 2 : pos - M / 2];
     } else {
       const int x0 = pos - o, x1 = pos + M - o;
       const float2 a0 = (x0 >= 0 && x0 < n) ? line[x0] : make_float2(0.f, 0.f);
       const float2 a1 = (x1 >= 0 && x1 < n) ? line[x1] : make_float2(0.f, 0.f);
       v[e] = r ? c_mul(c_sub(a0, a1), ldg2(wp + pos)) : c_add(a0, a1);
+    }
+  }
+  if constexpr (X2) {
+    if (r) {
+      const float2 wt = ldg2(wp + t);
+      for_slots(
+          [&](auto ec) {
+            constexpr int e = decltype(ec)::value;
+            const float2 w = slot_split_twiddle<EN, e>(wt);
+            v[e] = c_mul(v[e], EN::in_pos(t, e) < M / 2 ? c_neg(w) : w);
+          },
+          std::make_integer_sequence<int, EN::E>{});
     }
   }
 }
@@ -168,10 +194,20 @@ __global__ void __launch_bounds__(RowShape<EX>::THREADS) k_rows_fwd(const __grid
   const int nx = p.nx;
 
   // (A) modulated input rows -> shared [ROWS][nx]
+  if (p.src_kind == SRC_FIELD && !p.msrc.flags && (nx & 1) == 0) {
+    // plain field rows: one contiguous block, copied as 16-byte pieces
+    const float4* src = reinterpret_cast<const float4*>(p.in + (long long)(f / p.in_repeat) * p.in_stride +
+                                                        (long long)y0 * nx);
+    float4* dst4 = reinterpret_cast<float4*>(smem);
+    const int n4 = nrows * nx / 2, all4 = ROWS * nx / 2;
+#pragma unroll 4
+    for (int i = threadIdx.x; i < all4; i += NT) dst4[i] = i < n4 ? __ldg(src + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+  } else {
 #pragma unroll 2
-  for (int rr = 0; rr < ROWS; ++rr) {
-    for (int x = threadIdx.x; x < nx; x += NT)
-      smem[rr * nx + x] = rr < nrows ? load_src(p, fs, f, y0 + rr, x) : make_float2(0.f, 0.f);
+    for (int rr = 0; rr < ROWS; ++rr) {
+      for (int x = threadIdx.x; x < nx; x += NT)
+        smem[rr * nx + x] = rr < nrows ? load_src(p, fs, f, y0 + rr, x) : make_float2(0.f, 0.f);
+    }
   }
   __syncthreads();
   float2 v[E];
@@ -201,17 +237,18 @@ __global__ void __launch_bounds__(RowShape<EX>::THREADS) k_rows_fwd(const __grid
 
 // ----------------------------------------------------------------------------- C
 
+// H(kx, ky) (conjugated for the adjoint) for bin k of half r of a column: ky = 2k + r.
 __device__ __forceinline__ float2 transfer_value(const PassParams& p, const FieldSet& fs, float2 cxh, float ux,
-                                                 int kc, int ky) {
-  const float4 hy = __ldg(fs.hy + ky);
-  float2 h = c_mul(cxh, make_float2(hy.x, hy.y));
+                                                 int kc, int r, int k) {
+  const float2 ey = ldg2(fs.eyh + r * p.My + k);
+  float2 h = c_mul(cxh, ey);
   if (p.method == TOP_AS) {
-    if (kc != INT_MAX) {
-      const int sy = ky < (p.Py + 1) / 2 ? ky : ky - p.Py;
-      if (abs(sy) > kc) return make_float2(0.f, 0.f);
-    }
+    const int ky = 2 * k + r;
+    const int sy = ky < (p.Py + 1) / 2 ? ky : ky - p.Py;
+    if (kc != INT_MAX && abs(sy) > kc) return make_float2(0.f, 0.f);
     // AS remainder beyond the separable Fresnel phase: cr * g(u), g(u) = -(u^2/4)/(sqrt(1-u) + 1 - u/2)
-    const float u = ux + hy.z;
+    const float fsy = float(sy);
+    const float u = fmaf(fs.ly2 * fsy, fsy, ux);
     const float sq = sqrtf(fmaxf(1.f - u, 0.f));
     const float rr = __fdividef(fs.cr * (-0.25f * u * u), sq + 1.f - 0.5f * u);
     h = c_mul(h, cis(rr));
@@ -240,6 +277,7 @@ __global__ void __launch_bounds__(ColShape<EY>::THREADS) k_cols(const __grid_con
   // (A) the block's columns (contiguous in the workspace) -> shared
   if (line_len == ny && (ny & 1) == 0) {
     const int n4 = ncols * ny / 2;
+#pragma unroll 4
     for (int i = threadIdx.x; i < n4; i += NT)
       reinterpret_cast<float4*>(lines)[i] = reinterpret_cast<const float4*>(gcols)[i];
   } else {
@@ -260,13 +298,23 @@ __global__ void __launch_bounds__(ColShape<EY>::THREADS) k_cols(const __grid_con
   __syncthreads();  // both halves have read the column: its line now carries the odd half's output
   EY::fwd(v, xbuf, t, p.twy);
 #pragma unroll
-  for (int e = 0; e < E; ++e) v[e] = c_mul(v[e], transfer_value(p, fs, cxh, hx.z, kc, 2 * EY::bin(t, e) + r));
+  for (int e = 0; e < E; ++e) v[e] = c_mul(v[e], transfer_value(p, fs, cxh, hx.z, kc, r, EY::bin(t, e)));
   EY::inv(v, xbuf, t, p.twy);
   if (r) {
+    if constexpr (X2) {
+      const float2 wt = ldg2(p.wpy + t);
+      for_slots(
+          [&](auto ec) {
+            constexpr int e = decltype(ec)::value;
+            line[EY::in_pos(t, e)] = c_mulc(v[e], slot_split_twiddle<EY, e>(wt));  // exp(2 pi i pos / P) O[pos]
+          },
+          std::make_integer_sequence<int, E>{});
+    } else {
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
-      const int pos = EY::in_pos(t, e);
-      line[pos] = c_mulc(v[e], ldg2(p.wpy + pos));  // exp(2 pi i pos / P) O[pos]
+      for (int e = 0; e < E; ++e) {
+        const int pos = EY::in_pos(t, e);
+        line[pos] = c_mulc(v[e], ldg2(p.wpy + pos));  // exp(2 pi i pos / P) O[pos]
+      }
     }
   }
   __syncthreads();
@@ -356,10 +404,11 @@ __global__ void __launch_bounds__(RowShape<EX>::THREADS) k_rows_inv(const __grid
     const float2* src = p.ws + (long long)f * p.ws_stride + y0;
     if (vec) {
       constexpr int RP = ROWS / 2;
+#pragma unroll 4
       for (int i = threadIdx.x; i < 2 * M * RP; i += NT) {
         const int k = i / RP, rp = i - k * RP;
         *reinterpret_cast<float4*>(smem + k * LD + 2 * rp) =
-            *reinterpret_cast<const float4*>(src + (long long)k * p.ny + 2 * rp);
+            __ldg(reinterpret_cast<const float4*>(src + (long long)k * p.ny + 2 * rp));
       }
     } else {
       for (int i = threadIdx.x; i < 2 * M * ROWS; i += NT) {
