@@ -69,6 +69,8 @@ struct TransferEntry {
   float2 cg;
   float cr;
   float ly2;
+  float ga[6];
+  int poly;
 };
 
 struct top_ctx {
@@ -279,6 +281,15 @@ top_status transfer_tables(top_handle h, int Py, int Px, double dy, double dx, d
   const double norm = 1.0 / (double(Py) * double(Px));
   te.cg = make_float2(float(c * norm), float(s * norm));
   te.cr = float(2.0 * M_PI * z / lam);
+  {
+    // series of g(u) = sqrt(1 - u) - 1 + u/2 = -(1/8) u^2 - (1/16) u^3 - (5/128) u^4 - (7/256) u^5
+    //                   - (21/1024) u^6 - (33/2048) u^7 - ..., used when all propagating u <= 0.05
+    static const double c[6] = {-1.0 / 8, -1.0 / 16, -5.0 / 128, -7.0 / 256, -21.0 / 1024, -33.0 / 2048};
+    const double cr = 2.0 * M_PI * z / lam;
+    for (int i = 0; i < 6; ++i) te.ga[i] = float(cr * c[i]);
+    const double fxm = freq(Px / 2, Px, dx), fym = freq(Py / 2, Py, dy);
+    te.poly = lam * lam * (fxm * fxm + fym * fym) <= 0.05 ? 1 : 0;
+  }
   if (method == TOP_AS) {
     // evanescent cutoff: the radicand ((1/lambda^2) - fx^2) - fy^2 must be >= 0; it falls
     // monotonically in |fy|, so each column keeps |signed ky| <= kcut[kx].
@@ -565,6 +576,8 @@ top_status run_propagation(top_handle h, const Request& q, cudaStream_t st) {
     fs.kcut = te.kcut;
     fs.cg = te.cg;
     fs.cr = te.cr;
+    for (int i = 0; i < 6; ++i) fs.ga[i] = te.ga[i];
+    fs.poly = te.poly;
     if (q.msrc && (q.msrc->flags & TOP_MOD_LENS)) {
       TOP_TRY(lens_table(h, geo.nx, g->dx, q.lam[i], q.msrc->focal_length, &fs.src_lx));
       TOP_TRY(lens_table(h, geo.ny, g->dy, q.lam[i], q.msrc->focal_length, &fs.src_ly));

@@ -32,6 +32,10 @@ struct FieldSet {
   float2 cg;
   float cr;
   float ly2;
+  // cr * g(u) as u^2 (a[0] + u (a[1] + ... + u a[5])) when every propagating u is <= 0.05 (poly = 1):
+  // the binomial series of sqrt(1 - u) - 1 + u/2 through u^7, truncation below 2e-9 relative there
+  float ga[6];
+  int poly;
 };
 
 // Element modulation (Eq. 1) applied in a prologue or epilogue.

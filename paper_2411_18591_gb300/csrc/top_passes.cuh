@@ -55,18 +55,24 @@ struct RowShape {
   static_assert(THREADS <= 1024, "row block too large");
 };
 
-// Columns per block of the column pass; two thread groups (the two halves) per column.
+// Columns per block of the column pass; two thread groups (the two halves) per column. Each
+// column owns two buffers: its input line, which becomes the even half's exchange buffer once
+// both halves have folded it, and the odd half's exchange buffer, which finally carries the odd
+// half's output to the even half.
 template <class EN>
 struct ColShape {
   static constexpr int COLS = (64 / EN::G) >= 1 ? (64 / EN::G) : 1;
   static constexpr int GROUPS = 2 * COLS;
   static constexpr int THREADS = GROUPS * EN::G;
-  // shared memory: per column a line of max(ny, M) samples, then one exchange buffer per group
-  static size_t smem(int ny) {
-    const int line = ny > EN::M ? ny : EN::M;
-    return sizeof(float2) * (size_t(COLS) * line + size_t(GROUPS) * EN::BUF);
+  // two-stage power-of-two plans fit five blocks per SM (96 registers) without real spills
+  static constexpr int MINB = (EN::NS == 2 && (EN::G & (EN::G - 1)) == 0 && THREADS <= 128) ? 5 : 1;
+  __host__ __device__ static int line_len(int ny) {  // even, so lines start on 16-byte boundaries
+    const int l = ny > EN::M ? ny : EN::M;
+    return ((l > EN::BUF ? l : EN::BUF) + 1) & ~1;
   }
-  static constexpr size_t SMEM_MAX = sizeof(float2) * (COLS * 2 * EN::M + GROUPS * EN::BUF);
+  static size_t smem(int ny) { return sizeof(float2) * size_t(COLS) * (line_len(ny) + EN::BUF); }
+  static constexpr size_t SMEM_MAX =
+      sizeof(float2) * COLS * ((2 * EN::M > EN::BUF ? 2 * EN::M : EN::BUF) + EN::BUF);
 };
 
 // Group index and lane of a thread (masks when G is a power of two, so lane ranges are known).
@@ -110,6 +116,17 @@ __device__ __forceinline__ float2 cis(float a) {
   } else {
     sincosf(a, &s, &c);
   }
+  return make_float2(c, s);
+}
+
+// exp(i a) for |a| below a few thousand rad (the transfer-function remainder is bounded by 128 rad
+// on the host): the same reduction without the library path.
+__device__ __forceinline__ float2 cis_small(float a) {
+  const float n = rintf(a * 0.15915494309189535f);
+  float r = fmaf(-n, 6.28125f, a);
+  r = fmaf(-n, 1.9353071795864769e-3f, r);
+  float s, c;
+  __sincosf(r, &s, &c);
   return make_float2(c, s);
 }
 
@@ -237,27 +254,38 @@ __global__ void __launch_bounds__(RowShape<EX>::THREADS) k_rows_fwd(const __grid
 
 // ----------------------------------------------------------------------------- C
 
-// H(kx, ky) (conjugated for the adjoint) for bin k of half r of a column: ky = 2k + r.
-__device__ __forceinline__ float2 transfer_value(const PassParams& p, const FieldSet& fs, float2 cxh, float ux,
-                                                 int kc, int r, int k) {
-  const float2 ey = ldg2(fs.eyh + r * p.My + k);
-  float2 h = c_mul(cxh, ey);
+// H(kx, ky) / (cg ex[kx]) (conjugated for the adjoint) for bin k of half r of a column, ky = 2k + r:
+// ey[ky] exp(i cr g(ux + uy)). The column factor cg ex[kx] is applied after the inverse transform.
+__device__ __forceinline__ float2 transfer_value(const PassParams& p, const FieldSet& fs, float ux, int kc, int r,
+                                                 int k) {
+  float2 h = ldg2(fs.eyh + r * p.My + k);
   if (p.method == TOP_AS) {
     const int ky = 2 * k + r;
     const int sy = ky < (p.Py + 1) / 2 ? ky : ky - p.Py;
     if (kc != INT_MAX && abs(sy) > kc) return make_float2(0.f, 0.f);
-    // AS remainder beyond the separable Fresnel phase: cr * g(u), g(u) = -(u^2/4)/(sqrt(1-u) + 1 - u/2)
     const float fsy = float(sy);
     const float u = fmaf(fs.ly2 * fsy, fsy, ux);
-    const float sq = sqrtf(fmaxf(1.f - u, 0.f));
-    const float rr = __fdividef(fs.cr * (-0.25f * u * u), sq + 1.f - 0.5f * u);
-    h = c_mul(h, cis(rr));
+    float rr;
+    if (fs.poly) {
+      // cr g(u) from its series (all propagating u <= 0.05 in this parameter set)
+      rr = fmaf(u, fs.ga[5], fs.ga[4]);
+      rr = fmaf(u, rr, fs.ga[3]);
+      rr = fmaf(u, rr, fs.ga[2]);
+      rr = fmaf(u, rr, fs.ga[1]);
+      rr = fmaf(u, rr, fs.ga[0]);
+      rr *= u * u;
+    } else {
+      // cr g(u) = cr (-(u^2/4)) / (sqrt(1-u) + 1 - u/2), free of cancellation
+      const float sq = sqrtf(fmaxf(1.f - u, 0.f));
+      rr = __fdividef(fs.cr * (-0.25f * u * u), sq + 1.f - 0.5f * u);
+    }
+    h = c_mul(h, cis_small(rr));
   }
   return p.adjoint ? c_conj(h) : h;
 }
 
 template <class EY, bool X2>
-__global__ void __launch_bounds__(ColShape<EY>::THREADS) k_cols(const __grid_constant__ PassParams p) {
+__global__ void __launch_bounds__(ColShape<EY>::THREADS, ColShape<EY>::MINB) k_cols(const __grid_constant__ PassParams p) {
   using SH = ColShape<EY>;
   constexpr int G = EY::G, E = EY::E, M = EY::M, COLS = SH::COLS, NT = SH::THREADS;
   TOP_DYN_SMEM(float2, smem);
@@ -265,72 +293,78 @@ __global__ void __launch_bounds__(ColShape<EY>::THREADS) k_cols(const __grid_con
   group_lane<G>(threadIdx.x, grp, t);
   const int cl = grp >> 1, r = grp & 1;
   const int ny = p.ny;
-  const int line_len = X2 ? M : (ny > M ? ny : M);
+  const int line_len = SH::line_len(ny);
   const int col0 = blockIdx.x * COLS;
   const int ncols = min(COLS, p.Px - col0);
   const int f = blockIdx.y;
   const FieldSet& fs = p.sets[p.set_of[f]];
-  float2* lines = smem;                                   // [COLS][line_len]
-  float2* xbuf = smem + COLS * line_len + grp * EY::BUF;  // this group's exchange buffer
+  float2* line = smem + cl * line_len;                     // input line, then the even half's exchange buffer
+  float2* obuf = smem + COLS * line_len + cl * EY::BUF;    // the odd half's exchange buffer and output
+  float2* xbuf = r ? obuf : line;
   float2* gcols = p.ws + (long long)f * p.ws_stride + (long long)col0 * ny;
 
-  // (A) the block's columns (contiguous in the workspace) -> shared
-  if (line_len == ny && (ny & 1) == 0) {
-    const int n4 = ncols * ny / 2;
+  // (A) the block's columns (contiguous in the workspace) -> shared lines
+  if ((ny & 1) == 0) {
+    const int n2 = ny / 2, h2 = line_len / 2;
+    for (int c = 0; c < ncols; ++c) {
+      const float4* src = reinterpret_cast<const float4*>(gcols + (long long)c * ny);
+      float4* dst = reinterpret_cast<float4*>(smem + c * line_len);
 #pragma unroll 4
-    for (int i = threadIdx.x; i < n4; i += NT)
-      reinterpret_cast<float4*>(lines)[i] = reinterpret_cast<const float4*>(gcols)[i];
+      for (int i = threadIdx.x; i < n2; i += NT) dst[i] = src[i];
+    }
   } else {
     for (int c = 0; c < ncols; ++c)
-      for (int yy = threadIdx.x; yy < ny; yy += NT) lines[c * line_len + yy] = gcols[(long long)c * ny + yy];
+      for (int yy = threadIdx.x; yy < ny; yy += NT) smem[c * line_len + yy] = gcols[(long long)c * ny + yy];
   }
   __syncthreads();
   const int col = min(col0 + cl, p.Px - 1);
   const int rx = col >= p.Mx ? 1 : 0;
   const int kx = 2 * (col - rx * p.Mx) + rx;
   const float4 hx = __ldg(fs.hx + kx);
-  const float2 cxh = c_mul(fs.cg, make_float2(hx.x, hx.y));
   const int kc = fs.kcut ? __ldg(fs.kcut + kx) : INT_MAX;
-  float2* line = lines + cl * line_len;
 
   float2 v[E];
   fold<EY, X2>(v, line, ny, p.oy, r, p.wpy, t);
-  __syncthreads();  // both halves have read the column: its line now carries the odd half's output
+  __syncthreads();  // both halves have read the line: it becomes the even half's exchange buffer
   EY::fwd(v, xbuf, t, p.twy);
 #pragma unroll
-  for (int e = 0; e < E; ++e) v[e] = c_mul(v[e], transfer_value(p, fs, cxh, hx.z, kc, r, EY::bin(t, e)));
+  for (int e = 0; e < E; ++e) v[e] = c_mul(v[e], transfer_value(p, fs, hx.z, kc, r, EY::bin(t, e)));
   EY::inv(v, xbuf, t, p.twy);
+  EY::sync_group();  // every lane is past the last reads of its exchange buffer
   if (r) {
     if constexpr (X2) {
       const float2 wt = ldg2(p.wpy + t);
       for_slots(
           [&](auto ec) {
             constexpr int e = decltype(ec)::value;
-            line[EY::in_pos(t, e)] = c_mulc(v[e], slot_split_twiddle<EY, e>(wt));  // exp(2 pi i pos / P) O[pos]
+            obuf[EY::in_pos(t, e)] = c_mulc(v[e], slot_split_twiddle<EY, e>(wt));  // exp(2 pi i pos / P) O[pos]
           },
           std::make_integer_sequence<int, E>{});
     } else {
 #pragma unroll
       for (int e = 0; e < E; ++e) {
         const int pos = EY::in_pos(t, e);
-        line[pos] = c_mulc(v[e], ldg2(p.wpy + pos));  // exp(2 pi i pos / P) O[pos]
+        obuf[pos] = c_mulc(v[e], ldg2(p.wpy + pos));  // exp(2 pi i pos / P) O[pos]
       }
     }
   }
   __syncthreads();
   if (!r && cl < ncols) {
+    // column factor of H (conjugated for the adjoint), applied once per output sample
+    float2 cx = c_mul(fs.cg, make_float2(hx.x, hx.y));
+    if (p.adjoint) cx = c_conj(cx);
     float2* out = gcols + (long long)cl * ny;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int pos = EY::in_pos(t, e);
-      const float2 o = line[pos];
+      const float2 o = obuf[pos];
       if constexpr (X2) {
-        if (pos < M / 2) out[pos + M / 2] = c_sub(v[e], o);
-        else out[pos - M / 2] = c_add(v[e], o);
+        if (pos < M / 2) out[pos + M / 2] = c_mul(c_sub(v[e], o), cx);
+        else out[pos - M / 2] = c_mul(c_add(v[e], o), cx);
       } else {
         const int y0 = pos - p.oy, y1 = pos + M - p.oy;
-        if (y0 >= 0 && y0 < ny) out[y0] = c_add(v[e], o);
-        if (y1 >= 0 && y1 < ny) out[y1] = c_sub(v[e], o);
+        if (y0 >= 0 && y0 < ny) out[y0] = c_mul(c_add(v[e], o), cx);
+        if (y1 >= 0 && y1 < ny) out[y1] = c_mul(c_sub(v[e], o), cx);
       }
     }
   }
