@@ -254,34 +254,47 @@ __global__ void __launch_bounds__(RowShape<EX>::THREADS) k_rows_fwd(const __grid
 
 // ----------------------------------------------------------------------------- C
 
-// H(kx, ky) / (cg ex[kx]) (conjugated for the adjoint) for bin k of half r of a column, ky = 2k + r:
-// ey[ky] exp(i cr g(ux + uy)). The column factor cg ex[kx] is applied after the inverse transform.
-__device__ __forceinline__ float2 transfer_value(const PassParams& p, const FieldSet& fs, float ux, int kc, int r,
-                                                 int k) {
-  float2 h = ldg2(fs.eyh + r * p.My + k);
-  if (p.method == TOP_AS) {
-    const int ky = 2 * k + r;
-    const int sy = ky < (p.Py + 1) / 2 ? ky : ky - p.Py;
-    if (kc != INT_MAX && abs(sy) > kc) return make_float2(0.f, 0.f);
-    const float fsy = float(sy);
-    const float u = fmaf(fs.ly2 * fsy, fsy, ux);
-    float rr;
-    if (fs.poly) {
-      // cr g(u) from its series (all propagating u <= 0.05 in this parameter set)
-      rr = fmaf(u, fs.ga[5], fs.ga[4]);
-      rr = fmaf(u, rr, fs.ga[3]);
-      rr = fmaf(u, rr, fs.ga[2]);
-      rr = fmaf(u, rr, fs.ga[1]);
-      rr = fmaf(u, rr, fs.ga[0]);
-      rr *= u * u;
-    } else {
-      // cr g(u) = cr (-(u^2/4)) / (sqrt(1-u) + 1 - u/2), free of cancellation
-      const float sq = sqrtf(fmaxf(1.f - u, 0.f));
-      rr = __fdividef(fs.cr * (-0.25f * u * u), sq + 1.f - 0.5f * u);
+// Multiply the bins of half r of a column by H(kx, ky) / (cg ex[kx]), conjugated for the adjoint:
+// ey[ky] exp(i cr g(ux + uy)) with ky = 2k + r. The column factor cg ex[kx] is applied after the
+// inverse transform. MODE 0: Fresnel (no remainder); 1: AS with the series of g; 2: AS, exact g.
+// The loop has no branches: the evanescent cutoff is a select (kc = INT_MAX: none) and the
+// adjoint a sign.
+template <class EY, int MODE>
+__device__ __forceinline__ void apply_transfer(float2 (&v)[EY::E], const PassParams& p, const FieldSet& fs, float ux,
+                                               int kc, int r, int t) {
+  const float sg = p.adjoint ? -1.f : 1.f;
+  const float2* ey = fs.eyh + r * p.My;
+  const int half_py = (p.Py + 1) / 2;
+#pragma unroll
+  for (int e = 0; e < EY::E; ++e) {
+    const int k = EY::bin(t, e);
+    float2 h = ldg2(ey + k);
+    if constexpr (MODE != 0) {
+      const int ky = 2 * k + r;
+      const int sy = ky < half_py ? ky : ky - p.Py;
+      const float fsy = float(sy);
+      const float u = fmaf(fs.ly2 * fsy, fsy, ux);
+      float rr;
+      if constexpr (MODE == 1) {
+        rr = fmaf(u, fs.ga[5], fs.ga[4]);
+        rr = fmaf(u, rr, fs.ga[3]);
+        rr = fmaf(u, rr, fs.ga[2]);
+        rr = fmaf(u, rr, fs.ga[1]);
+        rr = fmaf(u, rr, fs.ga[0]);
+        rr *= u * u;
+      } else {
+        // cr (-(u^2/4)) / (sqrt(1-u) + 1 - u/2), free of cancellation
+        const float sq = sqrtf(fmaxf(1.f - u, 0.f));
+        rr = __fdividef(fs.cr * (-0.25f * u * u), sq + 1.f - 0.5f * u);
+      }
+      h = c_mul(h, cis_small(rr));
+      const bool ev = abs(sy) > kc;
+      h.x = ev ? 0.f : h.x;
+      h.y = ev ? 0.f : h.y;
     }
-    h = c_mul(h, cis_small(rr));
+    h.y *= sg;
+    v[e] = c_mul(v[e], h);
   }
-  return p.adjoint ? c_conj(h) : h;
 }
 
 template <class EY, bool X2>
@@ -327,8 +340,13 @@ __global__ void __launch_bounds__(ColShape<EY>::THREADS, ColShape<EY>::MINB) k_c
   fold<EY, X2>(v, line, ny, p.oy, r, p.wpy, t);
   __syncthreads();  // both halves have read the line: it becomes the even half's exchange buffer
   EY::fwd(v, xbuf, t, p.twy);
-#pragma unroll
-  for (int e = 0; e < E; ++e) v[e] = c_mul(v[e], transfer_value(p, fs, hx.z, kc, r, EY::bin(t, e)));
+  if (p.method != TOP_AS) {
+    apply_transfer<EY, 0>(v, p, fs, hx.z, kc, r, t);
+  } else if (fs.poly) {
+    apply_transfer<EY, 1>(v, p, fs, hx.z, kc, r, t);
+  } else {
+    apply_transfer<EY, 2>(v, p, fs, hx.z, kc, r, t);
+  }
   EY::inv(v, xbuf, t, p.twy);
   EY::sync_group();  // every lane is past the last reads of its exchange buffer
   if (r) {
