@@ -1,4 +1,4 @@
-// Kernel launch and dynamic shared-memory spellings used by every unit.
+// Kernel launch, dynamic shared memory and asynchronous-copy spellings used by every unit.
 #pragma once
 
 #ifndef TOP_LAUNCH
@@ -7,4 +7,21 @@
 
 #ifndef TOP_DYN_SMEM
 #define TOP_DYN_SMEM(T, name) extern __shared__ T name[]
+#endif
+
+#ifndef TOP_ASYNC_COPY
+#define TOP_ASYNC_COPY
+// 16-byte global -> shared copy that completes asynchronously (cached in L2 only); both addresses
+// must be 16-byte aligned. top_cp_async_wait_all() waits for all of this thread's copies; a block
+// barrier afterwards makes them visible to the other threads.
+__device__ __forceinline__ void top_cp_async16(void* smem_dst, const void* gsrc) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+// 8-byte variant (cached in L1 and L2); both addresses 8-byte aligned.
+__device__ __forceinline__ void top_cp_async8(void* smem_dst, const void* gsrc) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void top_cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 #endif

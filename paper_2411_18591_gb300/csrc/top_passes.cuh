@@ -15,13 +15,12 @@
 // padding are never loaded or transformed, and the inverse only produces the
 // cropped window: x[p] = E[p mod M] + exp(2 pi i p / P) O[p mod M].
 //
-// Global memory is only touched by block-cooperative loops (contiguous rows,
-// contiguous columns, or ROWS-sample chunks of the transposed workspace), so
-// loads are coalesced and many are in flight per thread; the FFT groups work on
-// shared-memory copies.
-//
-// Layout of the workspace between passes: for each field, Px lines of ny
-// samples, line kpos = r Mx + k holding frequency kx = 2 k + r.
+// Layout of the workspace between passes: for each field, Px frequency lines of
+// ny samples, line kpos = r Mx + k holding frequency kx = 2 k + r, stored in
+// blocks of four lines: sample (kpos, y) at ((kpos / 4) ny + y) 4 + kpos % 4.
+// Four consecutive lanes of a two-stage FFT hold four consecutive lines, so the
+// row passes move whole 32-byte sectors straight between registers and memory,
+// and the column pass reads pairs of lines as one 16-byte stream.
 #pragma once
 
 #include <climits>
@@ -34,45 +33,64 @@
 
 namespace top {
 
-// Rows per block of the row passes; two thread groups (the two halves) per row.
+// Threads per block of the row passes (a block holds TOP_ROW_THREADS / G rows).
 #ifndef TOP_ROW_THREADS
-#define TOP_ROW_THREADS 256
+#define TOP_ROW_THREADS 64
 #endif
 
+// Workspace index of sample (kpos, y) in the four-line block layout.
+__device__ __forceinline__ long long ws_index(int kpos, int y, int ny) {
+  return ((long long)(kpos >> 2) * ny + y) * 4 + (kpos & 3);
+}
+
+// Rows per block of the row passes; two thread groups (the two halves) per row. Two-stage plans
+// move their bins directly between registers and the workspace (DIRECT); deeper plans stage them
+// through a shared tile [2M][LD].
 template <class EN>
 struct RowShape {
   static constexpr int ROWS = (TOP_ROW_THREADS / EN::G) >= 1 ? (TOP_ROW_THREADS / EN::G) : 1;
   static constexpr int GROUPS = 2 * ROWS;
   static constexpr int THREADS = GROUPS * EN::G;
-  // tile stride: even (16-byte pairs of rows) with a 2-way bank pattern when ROWS >= 4, else odd
-  static constexpr bool VEC = ROWS % 2 == 0 && ROWS >= 4;
-  static constexpr int LD = VEC ? ROWS + 2 : ROWS + 1;
-  static constexpr int TILE = 2 * EN::M * LD;
+  static constexpr bool DIRECT = EN::NS == 2;
+  static constexpr int LD = ROWS + 1;  // odd tile stride: conflict-free column writes
+  static constexpr int TILE = DIRECT ? 0 : 2 * EN::M * LD;
   static constexpr int XCH = GROUPS * EN::BUF;
   static constexpr int ROWBUF = ROWS * 2 * EN::M;  // input rows (n <= P = 2M) or E/O halves of the inverse
   static constexpr int MAX2 = TILE > XCH ? TILE : XCH;
   static constexpr size_t SMEM = sizeof(float2) * (MAX2 > ROWBUF ? MAX2 : ROWBUF);
   static_assert(THREADS <= 1024, "row block too large");
+  static_assert(EN::M % 2 == 0, "the four-line workspace blocks need P = 2M to be a multiple of 4");
 };
 
-// Columns per block of the column pass; two thread groups (the two halves) per column. Each
-// column owns two buffers: its input line, which becomes the even half's exchange buffer once
-// both halves have folded it, and the odd half's exchange buffer, which finally carries the odd
-// half's output to the even half.
+// Columns per block of the column pass (even; a multiple of four from four up); two thread groups
+// (the two halves) per column. The columns' samples are de-interleaved from the four-line blocks
+// into contiguous lines [COLS][LS] of shared memory (after the fold a line serves as its even
+// half's exchange buffer, then carries the column's output), followed by one exchange buffer per
+// odd half, which finally carries that half's output.
+#ifndef TOP_COL_MIN
+#define TOP_COL_MIN 4
+#endif
 template <class EN>
 struct ColShape {
-  static constexpr int COLS = (64 / EN::G) >= 1 ? (64 / EN::G) : 1;
+  static constexpr int C0 = (64 / EN::G) & ~1;
+  // whole four-line blocks where the block stays at 256 threads or below, else pairs
+  static constexpr int COLS = C0 >= 4 ? C0 : ((TOP_COL_MIN > 2 && EN::G <= 32) ? 4 : 2);
+  static constexpr int CB = COLS >= 4 ? 4 : 2;  // lines moved together: one block of four, or a pair
   static constexpr int GROUPS = 2 * COLS;
   static constexpr int THREADS = GROUPS * EN::G;
   // two-stage power-of-two plans fit five blocks per SM (96 registers) without real spills
-  static constexpr int MINB = (EN::NS == 2 && (EN::G & (EN::G - 1)) == 0 && THREADS <= 128) ? 5 : 1;
-  __host__ __device__ static int line_len(int ny) {  // even, so lines start on 16-byte boundaries
-    const int l = ny > EN::M ? ny : EN::M;
-    return ((l > EN::BUF ? l : EN::BUF) + 1) & ~1;
+  static constexpr int MINB = (EN::NS == 2 && (EN::G & (EN::G - 1)) == 0 && THREADS <= 128) ? 5
+                              : (EN::NS == 2 && THREADS == 256) ? 2 : 1;
+  // line stride: room for the column and an exchange buffer, and LS = 16 / CB (mod 16) so that the
+  // CB lines of a copy instruction fall on distinct banks
+  __host__ __device__ static int line_stride(int ny) {
+    const int l = ny > EN::BUF ? ny : EN::BUF;
+    return l + ((16 / CB - l) % 16 + 16) % 16;
   }
-  static size_t smem(int ny) { return sizeof(float2) * size_t(COLS) * (line_len(ny) + EN::BUF); }
-  static constexpr size_t SMEM_MAX =
-      sizeof(float2) * COLS * ((2 * EN::M > EN::BUF ? 2 * EN::M : EN::BUF) + EN::BUF);
+  static size_t smem(int ny) { return sizeof(float2) * size_t(COLS) * (line_stride(ny) + EN::BUF); }
+  static constexpr size_t SMEM_MAX = sizeof(float2) * COLS * ((2 * EN::M > EN::BUF ? 2 * EN::M : EN::BUF) + 16 + EN::BUF);
+  static_assert(COLS % CB == 0, "columns come in whole copy units");
+  static_assert(SMEM_MAX <= 227 * 1024, "column block above the shared-memory limit");
 };
 
 // Group index and lane of a thread (masks when G is a power of two, so lane ranges are known).
@@ -160,10 +178,11 @@ __device__ __forceinline__ float2 load_src(const PassParams& p, const FieldSet& 
   return s;
 }
 
-// Slots of half r folded from a line of n samples at offset o (the odd half carries exp(-2 pi i p / 2M);
-// the copy at p + M picks up the opposite sign). X2: n = M and o = M/2 (padding exactly 2), where
-// every slot has one source, (pos + M/2) mod M, lying in the upper copy when pos < M/2.
-template <class EN, bool X2>
+// Slots of half r folded from a line of n samples at offset o, sample x at line[x * LS] (the odd
+// half carries exp(-2 pi i p / 2M); the copy at p + M picks up the opposite sign). X2: n = M and
+// o = M/2 (padding exactly 2), where every slot has one source, (pos + M/2) mod M, lying in the
+// upper copy when pos < M/2.
+template <class EN, bool X2, int LS>
 __device__ __forceinline__ void fold(float2 (&v)[EN::E], const float2* line, int n, int o, int r,
                                      const float2* __restrict__ wp, int t) {
   constexpr int M = EN::M;
@@ -172,11 +191,11 @@ __device__ __forceinline__ void fold(float2 (&v)[EN::E], const float2* line, int
     const int pos = EN::in_pos(t, e);
     if constexpr (X2) {
       const bool upper = pos < M / 2;
-      v[e] = line[upper ? pos + M / 2 : pos - M / 2];
+      v[e] = line[(upper ? pos + M / 2 : pos - M / 2) * LS];
     } else {
       const int x0 = pos - o, x1 = pos + M - o;
-      const float2 a0 = (x0 >= 0 && x0 < n) ? line[x0] : make_float2(0.f, 0.f);
-      const float2 a1 = (x1 >= 0 && x1 < n) ? line[x1] : make_float2(0.f, 0.f);
+      const float2 a0 = (x0 >= 0 && x0 < n) ? line[x0 * LS] : make_float2(0.f, 0.f);
+      const float2 a1 = (x1 >= 0 && x1 < n) ? line[x1 * LS] : make_float2(0.f, 0.f);
       v[e] = r ? c_mul(c_sub(a0, a1), ldg2(wp + pos)) : c_add(a0, a1);
     }
   }
@@ -208,7 +227,7 @@ __global__ void __launch_bounds__(RowShape<EX>::THREADS) k_rows_fwd(const __grid
   const int nrows = min(ROWS, p.ny - y0);
   const int f = blockIdx.y;
   const FieldSet& fs = p.sets[p.set_of[f]];
-  const int nx = p.nx;
+  const int nx = p.nx, ny = p.ny;
 
   // (A) modulated input rows -> shared [ROWS][nx]
   if (p.src_kind == SRC_FIELD && !p.msrc.flags && (nx & 1) == 0) {
@@ -217,8 +236,11 @@ __global__ void __launch_bounds__(RowShape<EX>::THREADS) k_rows_fwd(const __grid
                                                         (long long)y0 * nx);
     float4* dst4 = reinterpret_cast<float4*>(smem);
     const int n4 = nrows * nx / 2, all4 = ROWS * nx / 2;
-#pragma unroll 4
-    for (int i = threadIdx.x; i < all4; i += NT) dst4[i] = i < n4 ? __ldg(src + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int i = threadIdx.x; i < all4; i += NT) {
+      if (i < n4) top_cp_async16(dst4 + i, src + i);
+      else dst4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    top_cp_async_wait_all();
   } else {
 #pragma unroll 2
     for (int rr = 0; rr < ROWS; ++rr) {
@@ -228,26 +250,26 @@ __global__ void __launch_bounds__(RowShape<EX>::THREADS) k_rows_fwd(const __grid
   }
   __syncthreads();
   float2 v[E];
-  fold<EX, X2>(v, smem + row * nx, nx, p.ox, r, p.wpx, t);
+  fold<EX, X2, 1>(v, smem + row * nx, nx, p.ox, r, p.wpx, t);
   __syncthreads();  // the rows alias the exchange buffers
   EX::fwd(v, smem + grp * EX::BUF, t, p.twx);
-  __syncthreads();  // the exchange buffers alias the tile
+  float2* ws = p.ws + (long long)f * p.ws_stride;
+  if constexpr (SH::DIRECT) {
+    // (B) bins straight to the workspace: four consecutive lanes fill one 32-byte sector
+    if (row < nrows) {
 #pragma unroll
-  for (int e = 0; e < E; ++e) smem[(r * M + EX::bin(t, e)) * LD + row] = v[e];
-  __syncthreads();
-  // (B) transposed store: ROWS-sample chunks of the 2M lines (pairs of rows as 16-byte stores)
-  float2* dst = p.ws + (long long)f * p.ws_stride + y0;
-  if (SH::VEC && nrows == ROWS && (p.ny & 1) == 0) {
-    constexpr int RP = ROWS / 2;
-    for (int i = threadIdx.x; i < 2 * M * RP; i += NT) {
-      const int k = i / RP, rp = i - k * RP;
-      const float4 two = *reinterpret_cast<const float4*>(smem + k * LD + 2 * rp);
-      *reinterpret_cast<float4*>(dst + (long long)k * p.ny + 2 * rp) = two;
+      for (int e = 0; e < E; ++e) ws[ws_index(r * M + EX::bin(t, e), y0 + row, ny)] = v[e];
     }
   } else {
+    __syncthreads();  // the exchange buffers alias the tile
+#pragma unroll
+    for (int e = 0; e < E; ++e) smem[(r * M + EX::bin(t, e)) * LD + row] = v[e];
+    __syncthreads();
+    // (B) the tile, ROWS rows x 4 lines per block, to the workspace in address order
     for (int i = threadIdx.x; i < 2 * M * ROWS; i += NT) {
-      const int k = i / ROWS, rr = i - k * ROWS;
-      if (rr < nrows) dst[(long long)k * p.ny + rr] = smem[k * LD + rr];
+      const int c = i & 3, q = i >> 2;
+      const int yo = q % ROWS, blk = q / ROWS;
+      if (yo < nrows) ws[((long long)blk * ny + y0 + yo) * 4 + c] = smem[(4 * blk + c) * LD + yo];
     }
   }
 }
@@ -297,48 +319,53 @@ __device__ __forceinline__ void apply_transfer(float2 (&v)[EY::E], const PassPar
   }
 }
 
+// Workspace index of copy j of the CB columns from kpos0 (sample j / CB of column kpos0 + j % CB):
+// a four-line block is one contiguous stretch; a pair covers half of each of its 32-byte rows.
+template <int CB>
+__device__ __forceinline__ long long col_src(int j, int kpos0, int ny) {
+  if constexpr (CB == 4) {
+    return (long long)kpos0 * ny + j;
+  } else {
+    return ws_index(kpos0 + (j & 1), j >> 1, ny);
+  }
+}
+
 template <class EY, bool X2>
 __global__ void __launch_bounds__(ColShape<EY>::THREADS, ColShape<EY>::MINB) k_cols(const __grid_constant__ PassParams p) {
   using SH = ColShape<EY>;
-  constexpr int G = EY::G, E = EY::E, M = EY::M, COLS = SH::COLS, NT = SH::THREADS;
+  constexpr int G = EY::G, E = EY::E, M = EY::M, COLS = SH::COLS, CB = SH::CB, NT = SH::THREADS;
   TOP_DYN_SMEM(float2, smem);
   int grp, t;
   group_lane<G>(threadIdx.x, grp, t);
   const int cl = grp >> 1, r = grp & 1;
   const int ny = p.ny;
-  const int line_len = SH::line_len(ny);
-  const int col0 = blockIdx.x * COLS;
-  const int ncols = min(COLS, p.Px - col0);
+  const int LS = SH::line_stride(ny);
+  const int kpos0 = blockIdx.x * COLS;
+  const int ncols = min(COLS, p.Px - kpos0);  // a multiple of CB
   const int f = blockIdx.y;
   const FieldSet& fs = p.sets[p.set_of[f]];
-  float2* line = smem + cl * line_len;                     // input line, then the even half's exchange buffer
-  float2* obuf = smem + COLS * line_len + cl * EY::BUF;    // the odd half's exchange buffer and output
+  float2* line = smem + cl * LS;                            // [COLS][LS]
+  float2* obuf = smem + COLS * LS + cl * EY::BUF;           // the odd half's exchange buffer and output
   float2* xbuf = r ? obuf : line;
-  float2* gcols = p.ws + (long long)f * p.ws_stride + (long long)col0 * ny;
+  float2* ws = p.ws + (long long)f * p.ws_stride;
 
-  // (A) the block's columns (contiguous in the workspace) -> shared lines
-  if ((ny & 1) == 0) {
-    const int n2 = ny / 2, h2 = line_len / 2;
-    for (int c = 0; c < ncols; ++c) {
-      const float4* src = reinterpret_cast<const float4*>(gcols + (long long)c * ny);
-      float4* dst = reinterpret_cast<float4*>(smem + c * line_len);
-#pragma unroll 4
-      for (int i = threadIdx.x; i < n2; i += NT) dst[i] = src[i];
-    }
-  } else {
-    for (int c = 0; c < ncols; ++c)
-      for (int yy = threadIdx.x; yy < ny; yy += NT) smem[c * line_len + yy] = gcols[(long long)c * ny + yy];
+  // (A) de-interleave each unit of CB columns into contiguous lines: copy j of a unit holds
+  // sample j / CB of its line j % CB
+  for (int u = 0; u < ncols; u += CB) {
+    for (int j = threadIdx.x; j < CB * ny; j += NT)
+      top_cp_async8(smem + (u + j % CB) * LS + j / CB, ws + col_src<CB>(j, kpos0 + u, ny));
   }
+  top_cp_async_wait_all();
   __syncthreads();
-  const int col = min(col0 + cl, p.Px - 1);
+  const int col = min(kpos0 + cl, p.Px - 1);
   const int rx = col >= p.Mx ? 1 : 0;
   const int kx = 2 * (col - rx * p.Mx) + rx;
   const float4 hx = __ldg(fs.hx + kx);
   const int kc = fs.kcut ? __ldg(fs.kcut + kx) : INT_MAX;
 
   float2 v[E];
-  fold<EY, X2>(v, line, ny, p.oy, r, p.wpy, t);
-  __syncthreads();  // both halves have read the line: it becomes the even half's exchange buffer
+  fold<EY, X2, 1>(v, line, ny, p.oy, r, p.wpy, t);
+  __syncthreads();  // the lines become the even halves' exchange buffers
   EY::fwd(v, xbuf, t, p.twy);
   if (p.method != TOP_AS) {
     apply_transfer<EY, 0>(v, p, fs, hx.z, kc, r, t);
@@ -367,37 +394,42 @@ __global__ void __launch_bounds__(ColShape<EY>::THREADS, ColShape<EY>::MINB) k_c
     }
   }
   __syncthreads();
-  if (!r && cl < ncols) {
-    // column factor of H (conjugated for the adjoint), applied once per output sample
+  if (!r) {
+    // combine with the column factor of H (conjugated for the adjoint) into the column's line
     float2 cx = c_mul(fs.cg, make_float2(hx.x, hx.y));
     if (p.adjoint) cx = c_conj(cx);
-    float2* out = gcols + (long long)cl * ny;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int pos = EY::in_pos(t, e);
       const float2 o = obuf[pos];
       if constexpr (X2) {
-        if (pos < M / 2) out[pos + M / 2] = c_mul(c_sub(v[e], o), cx);
-        else out[pos - M / 2] = c_mul(c_add(v[e], o), cx);
+        if (pos < M / 2) line[pos + M / 2] = c_mul(c_sub(v[e], o), cx);
+        else line[pos - M / 2] = c_mul(c_add(v[e], o), cx);
       } else {
         const int y0 = pos - p.oy, y1 = pos + M - p.oy;
-        if (y0 >= 0 && y0 < ny) out[y0] = c_mul(c_add(v[e], o), cx);
-        if (y1 >= 0 && y1 < ny) out[y1] = c_mul(c_sub(v[e], o), cx);
+        if (y0 >= 0 && y0 < ny) line[y0] = c_mul(c_add(v[e], o), cx);
+        if (y1 >= 0 && y1 < ny) line[y1] = c_mul(c_sub(v[e], o), cx);
       }
     }
+  }
+  __syncthreads();
+  // (B) interleave back in the copy order of (A)
+  for (int u = 0; u < ncols; u += CB) {
+    for (int j = threadIdx.x; j < CB * ny; j += NT) ws[col_src<CB>(j, kpos0 + u, ny)] = smem[(u + j % CB) * LS + j / CB];
   }
 }
 
 // ----------------------------------------------------------------------------- R2
 
 // Epilogue of one output sample val = psi(y, x) of field f in group g.
+template <int KIND>
 __device__ __forceinline__ void epilogue(const PassParams& p, const FieldSet& fs, int f, int g, bool first, int y,
                                          int x, float2 val) {
   const long long idx = (long long)y * p.nx + x;
-  if (p.epi_kind == EPI_FIELD) {
+  if constexpr (KIND == EPI_FIELD) {
     if (p.mepi.flags) val = c_mul(val, mod_value(p.mepi, p.mepi.flags, p.mepi.conj, fs.epi_lx, fs.epi_ly, f, y, x, p.nx));
     p.out[(long long)f * p.out_stride + idx] = val;
-  } else if (p.epi_kind == EPI_INTENSITY) {
+  } else if constexpr (KIND == EPI_INTENSITY) {
     if (p.mepi.flags) val = c_mul(val, mod_value(p.mepi, p.mepi.flags, p.mepi.conj, fs.epi_lx, fs.epi_ly, f, y, x, p.nx));
     if (p.out) p.out[(long long)f * p.out_stride + idx] = val;
     const float w = p.weights ? __ldg(p.weights + f) : 1.f;
@@ -433,6 +465,33 @@ __device__ __forceinline__ void epilogue(const PassParams& p, const FieldSet& fs
   }
 }
 
+// Combine the two inverse halves of each row in shared memory ([r][ROWS][M], natural order) over
+// the cropped window and hand every output sample to the epilogue (one cooperative loop).
+template <class EX, bool X2, int KIND>
+__device__ __forceinline__ void combine_rows(const PassParams& p, const FieldSet& fs, const float2* smem, int f, int g,
+                                             bool first, int y0, int nrows) {
+  using SH = RowShape<EX>;
+  constexpr int M = EX::M, ROWS = SH::ROWS, NT = SH::THREADS;
+  const int nx = p.nx;
+  for (int rr = 0; rr < nrows; ++rr) {
+    for (int x = threadIdx.x; x < nx; x += NT) {
+      int pos;
+      bool upper;
+      if constexpr (X2) {
+        upper = x >= M / 2;
+        pos = upper ? x - M / 2 : x + M / 2;
+      } else {
+        const int pp = x + p.ox;
+        upper = pp >= M;
+        pos = upper ? pp - M : pp;
+      }
+      const float2 o = c_mulc(smem[(ROWS + rr) * M + pos], ldg2(p.wpx + pos));
+      const float2 ev = smem[rr * M + pos];
+      epilogue<KIND>(p, fs, f, g, first, y0 + rr, x, upper ? c_sub(ev, o) : c_add(ev, o));
+    }
+  }
+}
+
 template <class EX, bool X2>
 __global__ void __launch_bounds__(RowShape<EX>::THREADS) k_rows_inv(const __grid_constant__ PassParams p) {
   using SH = RowShape<EX>;
@@ -446,56 +505,44 @@ __global__ void __launch_bounds__(RowShape<EX>::THREADS) k_rows_inv(const __grid
   const int g = blockIdx.y;
   const int f0 = g * p.group;
   const int f1 = min(f0 + p.group, p.nfields);
-  const int nx = p.nx;
-  const bool vec = SH::VEC && nrows == ROWS && (p.ny & 1) == 0;
+  const int ny = p.ny;
 
 #pragma unroll 1
   for (int f = f0; f < f1; ++f) {
     const FieldSet& fs = p.sets[p.set_of[f]];
-    // (A) ROWS-sample chunks of the 2M lines -> tile [2M][LD] (pairs of rows as 16-byte loads)
-    const float2* src = p.ws + (long long)f * p.ws_stride + y0;
-    if (vec) {
-      constexpr int RP = ROWS / 2;
-#pragma unroll 4
-      for (int i = threadIdx.x; i < 2 * M * RP; i += NT) {
-        const int k = i / RP, rp = i - k * RP;
-        *reinterpret_cast<float4*>(smem + k * LD + 2 * rp) =
-            __ldg(reinterpret_cast<const float4*>(src + (long long)k * p.ny + 2 * rp));
-      }
-    } else {
-      for (int i = threadIdx.x; i < 2 * M * ROWS; i += NT) {
-        const int k = i / ROWS, rr = i - k * ROWS;
-        smem[k * LD + rr] = rr < nrows ? src[(long long)k * p.ny + rr] : make_float2(0.f, 0.f);
-      }
-    }
-    __syncthreads();
+    const float2* ws = p.ws + (long long)f * p.ws_stride;
     float2 v[E];
+    if constexpr (SH::DIRECT) {
+      // bins straight from the workspace: four consecutive lanes read one 32-byte sector
+      const bool valid = row < nrows;
 #pragma unroll
-    for (int e = 0; e < E; ++e) v[e] = smem[(r * M + EX::bin(t, e)) * LD + row];
-    __syncthreads();  // the tile aliases the exchange buffers
+      for (int e = 0; e < E; ++e)
+        v[e] = valid ? ws[ws_index(r * M + EX::bin(t, e), y0 + row, ny)] : make_float2(0.f, 0.f);
+    } else {
+      // the tile [2M][LD] from the workspace in address order (ROWS rows x 4 lines per block)
+      for (int i = threadIdx.x; i < 2 * M * ROWS; i += NT) {
+        const int c = i & 3, q = i >> 2;
+        const int yo = q % ROWS, blk = q / ROWS;
+        smem[(4 * blk + c) * LD + yo] = yo < nrows ? ws[((long long)blk * ny + y0 + yo) * 4 + c] : make_float2(0.f, 0.f);
+      }
+      __syncthreads();
+#pragma unroll
+      for (int e = 0; e < E; ++e) v[e] = smem[(r * M + EX::bin(t, e)) * LD + row];
+      __syncthreads();  // the tile aliases the exchange buffers
+    }
     EX::inv(v, smem + grp * EX::BUF, t, p.twx);
     __syncthreads();  // the exchange buffers alias the half-row buffers
-    // (B) both halves in natural order -> shared [r][ROWS][M]
+    // both halves in natural order -> shared [r][ROWS][M]
 #pragma unroll
     for (int e = 0; e < E; ++e) smem[(r * ROWS + row) * M + EX::in_pos(t, e)] = v[e];
     __syncthreads();
-    // (C) combine the halves over the cropped window, epilogue, coalesced store
-    for (int rr = 0; rr < nrows; ++rr) {
-      for (int x = threadIdx.x; x < nx; x += NT) {
-        int pos;
-        bool upper;
-        if constexpr (X2) {
-          upper = x >= M / 2;
-          pos = upper ? x - M / 2 : x + M / 2;
-        } else {
-          const int pp = x + p.ox;
-          upper = pp >= M;
-          pos = upper ? pp - M : pp;
-        }
-        const float2 o = c_mulc(smem[(ROWS + rr) * M + pos], ldg2(p.wpx + pos));
-        const float2 ev = smem[rr * M + pos];
-        epilogue(p, fs, f, g, f == f0, y0 + rr, x, upper ? c_sub(ev, o) : c_add(ev, o));
-      }
+    // combine the halves over the cropped window, epilogue, coalesced store
+    if (p.epi_kind == EPI_FIELD) {
+      combine_rows<EX, X2, EPI_FIELD>(p, fs, smem, f, g, f == f0, y0, nrows);
+    } else if (p.epi_kind == EPI_INTENSITY) {
+      combine_rows<EX, X2, EPI_INTENSITY>(p, fs, smem, f, g, f == f0, y0, nrows);
+    } else {
+      combine_rows<EX, X2, EPI_MODGRAD>(p, fs, smem, f, g, f == f0, y0, nrows);
     }
     __syncthreads();
   }
