@@ -147,6 +147,33 @@ top_status top_propagate(top_handle h, const top_grid* g, const void* in, void* 
                          const double* lambda, const double* z, int64_t n_lz,
                          const top_mod* pre, const top_mod* post, void* stream);
 
+/* Bytes of the library's static device scratch used by top_propagate_noalloc. */
+#define TOP_NOALLOC_SCRATCH_BYTES (64u << 20)
+
+/* out = P_z(in) for every field (Eq. 4 with H of Eq. 5, or the Fresnel form) without a
+ * handle and without allocating device memory. The paper has no counterpart: this is an
+ * engineering variant of top_propagate (pre = post = NULL, input_repeat 0 or 1) for callers
+ * that cannot allocate -- a process whose device memory is held by another allocator (a
+ * cudaMalloc here would fail or force that allocator to release its cache), or a caller that
+ * must not stall other streams (a handle grows its workspace with a device-wide synchronise,
+ * cudaFree and cudaMalloc) -- and for callers that hold no handle.
+ *
+ * Scratch: the transfer-function and twiddle tables and the frequency-domain workspace of
+ * each chunk of fields live in one static device array of TOP_NOALLOC_SCRATCH_BYTES per
+ * device (the current device of the calling thread). The tables are rebuilt in float64 on
+ * the host and copied in on `stream` each call; nothing in the scratch needs to start at zero.
+ * Fields are processed in chunks that fit; one field needs Px * ny * 8 bytes of workspace plus
+ * the tables (1024^2 fields at 2x padding: 16 MiB each), and a grid whose single field does not
+ * fit is rejected with TOP_ERR_UNSUPPORTED before anything is launched.
+ * The first call on a device looks up the scratch address (cudaGetSymbolAddress, which loads
+ * the library's device code): make it before any stream capture. Calls share the scratch, so
+ * two calls in flight at once on one device (other streams, other threads) race; order them on
+ * one stream or synchronise between them.
+ * in, out: complex64 [batch][ny][nx] device, 16-byte aligned (in == out allowed); lambda, z:
+ * host arrays of n_lz values (1 or batch). Results equal top_propagate's bit for bit. */
+top_status top_propagate_noalloc(const top_grid* g, const void* in, void* out, const double* lambda,
+                                 const double* z, int64_t n_lz, void* stream);
+
 /* Backward of top_propagate (§4): grad_in = conj(pre) * P_z^H(conj(post) * grad_out),
  * P_z^H using conj(H). grad_in may be NULL when only `pre_grads` is wanted.
  * pre_grads (may be NULL): gradients of pre's phase / amplitude / mask; needs

@@ -58,6 +58,7 @@ SIGNATURES = {
     "top_plan_query": (C.c_int, [_GRID, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_uint64)]),
     "top_zcritical": (C.c_double, [C.c_double, C.c_double, C.c_double]),
     "top_propagate": (C.c_int, [_P, _GRID, _P, _P, _D, _D, _I64, _MOD, _MOD, _P]),
+    "top_propagate_noalloc": (C.c_int, [_GRID, _P, _P, _D, _D, _I64, _P]),
     "top_propagate_backward": (C.c_int, [_P, _GRID, _P, _P, _D, _D, _I64, _MOD, _MOD, _GRADS, _P]),
     "top_propagate_intensity": (C.c_int, [_P, _GRID, _P, _P, _P, _I64, _P, _D, _D, _I64, _MOD, _MOD, _P]),
     "top_propagate_intensity_backward": (C.c_int, [_P, _GRID, _P, _P, _P, _I64, _P, _D, _D, _I64, _MOD, _MOD,

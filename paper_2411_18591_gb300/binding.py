@@ -157,6 +157,25 @@ def top_propagate(field: torch.Tensor, dy: float, dx: float, lam, z, pad: float 
     return out
 
 
+def top_propagate_noalloc(field: torch.Tensor, dy: float, dx: float, lam, z, pad: float = 2.0, method="as", *,
+                          out: torch.Tensor) -> torch.Tensor:
+    """out = P_z(field) through the library's static device scratch: no handle, no device allocation.
+
+    ``out`` is required (complex64, the shape of ``field``; ``out is field`` allowed), so the call
+    allocates nothing. Calls on one device must not overlap (they share the scratch)."""
+    _field(field, "field")
+    _field(out, "out")
+    b, ny, nx = _shape3(field)
+    if _shape3(out) != (b, ny, nx):
+        raise ValueError("out must have the shape of field")
+    lams, zs, n = _lz(lam, z, b)
+    g = make_grid(b, ny, nx, dy, dx, pad, method)
+    with torch.cuda.device(field.device):
+        check(_lib.load().top_propagate_noalloc(C.byref(g), field.data_ptr(), out.data_ptr(), lams, zs, n,
+                                                _stream(field)))
+    return out
+
+
 def top_propagate_backward(grad_out: torch.Tensor, dy: float, dx: float, lam, z, pad: float = 2.0, method="as",
                            pre: Optional[Modulation] = None, post: Optional[Modulation] = None,
                            saved_in: Optional[torch.Tensor] = None, want_grad_in: bool = True,

@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <numeric>
 #include <string>
 #include <utility>
@@ -1227,3 +1228,241 @@ top_status top_profile_read(top_handle h, int cap, const char** kinds, double* m
 }
 
 }  // extern "C"
+
+// ============================================================================= static-scratch propagation
+
+// Tables and workspace of top_propagate_noalloc: one static array per device, no allocation.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[TOP_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kNoallocDevices = 64;
+std::mutex g_noalloc_mutex;
+void* g_noalloc_addr[kNoallocDevices] = {};
+
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+// Address of the scratch on the current device, looked up once per device.
+top_status noalloc_scratch(void** out) {
+  int dev = -1;
+  TOP_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+  if (dev < 0 || dev >= kNoallocDevices) return fail(TOP_ERR_UNSUPPORTED, "device %d beyond the %d supported", dev, kNoallocDevices);
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    TOP_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch), "cudaGetSymbolAddress(static scratch)");
+    if (!p) return fail(TOP_ERR_CUDA, "static scratch has no device address");
+    g_noalloc_addr[dev] = p;
+  }
+  *out = g_noalloc_addr[dev];
+  return TOP_OK;
+}
+
+// Host images of the tables (the same float64 arithmetic as the handle's cached tables).
+void noalloc_engine_twiddles(int M, std::vector<float2>& tw) {
+  EngineInfo info;
+  find_engine(M, &info);
+  tw.assign(std::max(1, info.tw_size), make_float2(0.f, 0.f));
+  size_t off = 0;
+  for (int s = 0; s < info.NS; ++s) {
+    int sp = 1;
+    for (int i = s + 1; i < info.NS; ++i) sp *= info.R[i];
+    if (sp <= 1) continue;
+    const int r = info.R[s], L = r * sp;
+    for (int j = 1; j < r; ++j)
+      for (int i = 0; i < sp; ++i) tw[off + size_t(j - 1) * sp + i] = unit_root((long long)i * j, L);
+    off += size_t(r - 1) * sp;
+  }
+}
+
+struct NoallocSet {
+  std::vector<float4> hx;
+  std::vector<float2> eyh;
+  std::vector<int> kcut;  // empty without evanescent samples
+  FieldSet fs;            // scalars; table pointers are set once the chunk is laid out
+};
+
+void noalloc_transfer(int Py, int Px, double dy, double dx, double lam, double z, int method, NoallocSet* o) {
+  auto axis = [&](int P, double d, std::vector<float4>& t) {
+    t.resize(P);
+    for (int k = 0; k < P; ++k) {
+      const double f = freq(k, P, d);
+      double c, s;
+      cis_pi(-lam * z * f * f, &c, &s);
+      t[k] = make_float4(float(c), float(s), float(lam * lam * f * f), 0.f);
+    }
+  };
+  std::vector<float4> hy;
+  axis(Px, dx, o->hx);
+  axis(Py, dy, hy);
+  o->eyh.resize(Py);
+  for (int r = 0; r < 2; ++r)
+    for (int k = 0; k < Py / 2; ++k) o->eyh[r * (Py / 2) + k] = make_float2(hy[2 * k + r].x, hy[2 * k + r].y);
+  FieldSet& fs = o->fs;
+  fs = FieldSet{};
+  const double ly = lam / (double(Py) * dy);
+  fs.ly2 = float(ly * ly);
+  double c, s;
+  cis_pi(2.0 * z / lam, &c, &s);
+  const double norm = 1.0 / (double(Py) * double(Px));
+  fs.cg = make_float2(float(c * norm), float(s * norm));
+  fs.cr = float(2.0 * M_PI * z / lam);
+  static const double gc[6] = {-1.0 / 8, -1.0 / 16, -5.0 / 128, -7.0 / 256, -21.0 / 1024, -33.0 / 2048};
+  const double cr = 2.0 * M_PI * z / lam;
+  for (int i = 0; i < 6; ++i) fs.ga[i] = float(cr * gc[i]);
+  const double fxm = freq(Px / 2, Px, dx), fym = freq(Py / 2, Py, dy);
+  fs.poly = lam * lam * (fxm * fxm + fym * fym) <= 0.05 ? 1 : 0;
+  o->kcut.clear();
+  if (method == TOP_AS) {
+    const double inv_l2 = 1.0 / (lam * lam);
+    if (((inv_l2 - fxm * fxm) - fym * fym) < 0.0) {
+      o->kcut.resize(Px);
+      for (int k = 0; k < Px; ++k) {
+        const double fx = freq(k, Px, dx);
+        const double a = inv_l2 - fx * fx;
+        int best = -1;
+        for (long long sy = 0; sy <= Py / 2; ++sy) {
+          const double fy = double(sy) / (double(Py) * dy);
+          if (a - fy * fy >= 0.0) best = int(sy); else break;
+        }
+        o->kcut[k] = best;
+      }
+    }
+  }
+}
+
+// Append a table to the host image at a 256-byte boundary; returns its byte offset.
+template <class T>
+size_t put(std::vector<unsigned char>& img, const std::vector<T>& v) {
+  const size_t off = align256(img.size());
+  img.resize(off + v.size() * sizeof(T));
+  if (!v.empty()) std::memcpy(img.data() + off, v.data(), v.size() * sizeof(T));
+  return off;
+}
+
+top_status propagate_noalloc(const top_grid* g, const void* in, void* out, const double* lam, const double* z,
+                             int64_t n_lz, cudaStream_t st) {
+  Geometry geo;
+  TOP_TRY(check_grid(g, &geo));
+  TOP_TRY(check_engines(geo));
+  TOP_TRY(check_lz(g, lam, z, n_lz, true));
+  TOP_TRY(check_as_remainder(geo, g, lam, z, n_lz));
+  if (g->input_repeat > 1) return fail(TOP_ERR_UNSUPPORTED, "top_propagate_noalloc takes input_repeat 0 or 1");
+  TOP_TRY(check_ptr(in, "input field"));
+  TOP_TRY(check_ptr(out, "output field"));
+  const int64_t B = g->batch;
+  const long long plane = (long long)geo.ny * geo.nx;
+
+  // scratch budget: twiddles, kMaxSets table slots, then the workspace of a chunk
+  EngineInfo ix, iy;
+  find_engine(geo.Px / 2, &ix);
+  find_engine(geo.Py / 2, &iy);
+  const size_t tw_bytes = align256(std::max(1, ix.tw_size) * sizeof(float2)) +
+                          align256(std::max(1, iy.tw_size) * sizeof(float2)) +
+                          align256(size_t(geo.Px / 2) * sizeof(float2)) + align256(size_t(geo.Py / 2) * sizeof(float2));
+  const size_t set_bytes = align256(size_t(geo.Px) * sizeof(float4)) + align256(size_t(geo.Py) * sizeof(float2)) +
+                           align256(size_t(geo.Px) * sizeof(int));
+  const size_t table_bytes = tw_bytes + kMaxSets * set_bytes;
+  const size_t ws_field = size_t(geo.Px) * size_t(geo.ny) * sizeof(float2);
+  const size_t cap = TOP_NOALLOC_SCRATCH_BYTES;
+  if (table_bytes + ws_field > cap)
+    return fail(TOP_ERR_UNSUPPORTED,
+                "one %dx%d field (padded %dx%d) needs %zu bytes of static scratch (workspace %zu + tables %zu), "
+                "above the %zu bytes of top_propagate_noalloc",
+                geo.ny, geo.nx, geo.Py, geo.Px, table_bytes + ws_field, ws_field, table_bytes, cap);
+  const int64_t chunk = std::min<int64_t>({B, int64_t(kMaxFields), int64_t((cap - table_bytes) / ws_field)});
+
+  void* scratch = nullptr;
+  TOP_TRY(noalloc_scratch(&scratch));
+  unsigned char* base = static_cast<unsigned char*>(scratch);
+  float2* ws = reinterpret_cast<float2*>(base + table_bytes);
+
+  std::vector<float2> twx, twy, wpx(geo.Px / 2), wpy(geo.Py / 2);
+  noalloc_engine_twiddles(geo.Px / 2, twx);
+  noalloc_engine_twiddles(geo.Py / 2, twy);
+  for (int q = 0; q < geo.Px / 2; ++q) wpx[q] = unit_root(q, geo.Px);
+  for (int q = 0; q < geo.Py / 2; ++q) wpy[q] = unit_root(q, geo.Py);
+
+  PassParams p{};
+  p.ny = geo.ny;
+  p.nx = geo.nx;
+  p.Py = geo.Py;
+  p.Px = geo.Px;
+  p.My = geo.Py / 2;
+  p.Mx = geo.Px / 2;
+  p.oy = geo.oy;
+  p.ox = geo.ox;
+  p.method = g->method;
+  p.adjoint = 0;
+  p.src_kind = SRC_FIELD;
+  p.epi_kind = EPI_FIELD;
+  p.ws = ws;
+  p.ws_stride = (long long)geo.Px * geo.ny;
+  p.in_stride = plane;
+  p.out_stride = plane;
+  p.psi_stride = plane;
+  p.xs_stride = plane;
+  p.gI_stride = plane;
+  p.outf_stride = plane;
+  p.part_stride = plane;
+  p.group = 1;
+  p.src_group = 1;
+  p.in_repeat = 1;
+
+  std::vector<unsigned char> img;
+  std::vector<NoallocSet> sets;
+  std::vector<std::pair<uint64_t, uint64_t>> keys;
+  int64_t pos = 0;
+  while (pos < B) {
+    // fields of this chunk and their distinct (lambda, z) sets
+    sets.clear();
+    keys.clear();
+    int64_t n = 0;
+    while (pos + n < B && n < chunk) {
+      const int64_t i = n_lz == 1 ? 0 : pos + n;
+      const std::pair<uint64_t, uint64_t> key{bits(lam[i]), bits(z[i])};
+      size_t k = 0;
+      while (k < keys.size() && keys[k] != key) ++k;
+      if (k == keys.size()) {
+        if ((int)keys.size() == kMaxSets) break;
+        keys.push_back(key);
+        sets.emplace_back();
+        noalloc_transfer(geo.Py, geo.Px, g->dy, g->dx, lam[i], z[i], g->method, &sets.back());
+      }
+      p.set_of[n] = (unsigned char)k;
+      ++n;
+    }
+    // host image of the tables -> one copy into the scratch, ordered on the stream
+    img.clear();
+    const size_t o_twx = put(img, twx), o_twy = put(img, twy), o_wpx = put(img, wpx), o_wpy = put(img, wpy);
+    p.twx = reinterpret_cast<const float2*>(base + o_twx);
+    p.twy = reinterpret_cast<const float2*>(base + o_twy);
+    p.wpx = reinterpret_cast<const float2*>(base + o_wpx);
+    p.wpy = reinterpret_cast<const float2*>(base + o_wpy);
+    p.nsets = int(sets.size());
+    for (size_t k = 0; k < sets.size(); ++k) {
+      FieldSet fs = sets[k].fs;
+      fs.hx = reinterpret_cast<const float4*>(base + put(img, sets[k].hx));
+      fs.eyh = reinterpret_cast<const float2*>(base + put(img, sets[k].eyh));
+      fs.kcut = sets[k].kcut.empty() ? nullptr : reinterpret_cast<const int*>(base + put(img, sets[k].kcut));
+      p.sets[k] = fs;
+    }
+    if (img.size() > table_bytes) return fail(TOP_ERR_INTERNAL, "static table image above its reserved size");
+    TOP_CUDA(cudaMemcpyAsync(base, img.data(), img.size(), cudaMemcpyHostToDevice, st), "cudaMemcpyAsync(static tables)");
+    p.nfields = int(n);
+    p.in = static_cast<const float2*>(in) + pos * plane;
+    p.out = static_cast<float2*>(out) + pos * plane;
+    TOP_CUDA(launch_pass(PASS_ROWS_FWD, p.Mx, p, st), "rows forward pass");
+    TOP_CUDA(launch_pass(PASS_COLS, p.My, p, st), "column pass");
+    TOP_CUDA(launch_pass(PASS_ROWS_INV, p.Mx, p, st), "rows inverse pass");
+    pos += n;
+  }
+  return TOP_OK;
+}
+
+}  // namespace
+
+extern "C" top_status top_propagate_noalloc(const top_grid* g, const void* in, void* out, const double* lambda,
+                                            const double* z, int64_t n_lz, void* stream) {
+  return propagate_noalloc(g, in, out, lambda, z, n_lz, static_cast<cudaStream_t>(stream));
+}
