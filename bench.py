@@ -181,11 +181,12 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def workload_config(sample=False):
+def workload_config(sample=False, objects=None):
     c = S.CFG4
+    objects = c["objects"] if objects is None else objects
     return {"workload": "polarised 4f imaging, fwd+bwd w.r.t. pupil phase" + (" (oracle sample)" if sample else ""),
-            "objects": c["objects"], "components": c["comps"], "wavelengths": c["wavelengths"],
-            "fields": c["objects"] * c["comps"] * c["wavelengths"], "grid": [c["n"], c["n"]], "spacing_m": c["d"],
+            "objects": objects, "components": c["comps"], "wavelengths": c["wavelengths"],
+            "fields": objects * c["comps"] * c["wavelengths"], "grid": [c["n"], c["n"]], "spacing_m": c["d"],
             "pad": c["pad"], "fft": [2 * c["n"], 2 * c["n"]], "method": "angular spectrum", "focal_m": c["f"],
             "props_per_field": {"fwd": 4, "bwd": 2}, "l2": "inputs and intermediates (3.2 GB per plane) exceed L2"}
 
@@ -203,14 +204,15 @@ def run_ours(args, rank, world):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     c = S.CFG4
+    objects = args.objects
     sysm = FourF(n=c["n"], d=c["d"], f=c["f"], lens_radius=c["lens_radius"], pupil_radius=c["pupil_radius"],
-                 objects=c["objects"], comps=c["comps"], wavelengths=tuple(S.cfg4_wavelengths(c["wavelengths"])),
+                 objects=objects, comps=c["comps"], wavelengths=tuple(S.cfg4_wavelengths(c["wavelengths"])),
                  pad=c["pad"])
-    obj_host = S.cfg4_objects(c["objects"], c["comps"], c["n"]).reshape(-1, c["n"], c["n"]).astype(np.complex64)
+    obj_host = S.cfg4_objects(objects, c["comps"], c["n"]).reshape(-1, c["n"], c["n"]).astype(np.complex64)
     obj_pinned = torch.from_numpy(obj_host).pin_memory()
     obj = obj_pinned.to(dev)
     phase = torch.from_numpy(S.cfg4_pupil_phase(c["n"]).astype(np.float32)).to(dev)
-    target = torch.from_numpy(S.cfg4_target(c["objects"], c["n"]).astype(np.float32)).to(dev)
+    target = torch.from_numpy(S.cfg4_target(objects, c["n"]).astype(np.float32)).to(dev)
     gphase = torch.empty_like(phase)
     bufs = {}
     dist = world > 1
@@ -301,7 +303,7 @@ def run_ours(args, rank, world):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "c64/f32 (FP64 phase tables)", "data": "synthetic",
-            "config": workload_config(), "roofline": roofline, "clocks": clocks, "e2e": e2e,
+            "config": workload_config(objects=objects), "roofline": roofline, "clocks": clocks, "e2e": e2e,
             "gpu_launches": launches}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(2, 0)
@@ -316,6 +318,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--objects", type=int, default=S.CFG4["objects"],
+                    help="objects per GPU (a smaller batch for profiler captures; the workload has 16)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

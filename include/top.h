@@ -158,13 +158,15 @@ top_status top_propagate(top_handle h, const top_grid* g, const void* in, void* 
  * must not stall other streams (a handle grows its workspace with a device-wide synchronise,
  * cudaFree and cudaMalloc) -- and for callers that hold no handle.
  *
- * Scratch: the transfer-function and twiddle tables and the frequency-domain workspace of
+ * Scratch: the twiddle and transfer-function tables and the frequency-domain workspace of
  * each chunk of fields live in one static device array of TOP_NOALLOC_SCRATCH_BYTES per
- * device (the current device of the calling thread). The tables are rebuilt in float64 on
- * the host and copied in on `stream` each call; nothing in the scratch needs to start at zero.
- * Fields are processed in chunks that fit; one field needs Px * ny * 8 bytes of workspace plus
- * the tables (1024^2 fields at 2x padding: 16 MiB each), and a grid whose single field does not
- * fit is rejected with TOP_ERR_UNSUPPORTED before anything is launched.
+ * device (the current device of the calling thread). Every call rewrites the tables on
+ * `stream` (twiddles copied from the host, transfer functions built by a kernel), so nothing
+ * in the scratch needs to start at zero. Fields are processed in chunks that fit: one field
+ * needs Px * ny * 8 bytes of workspace and each distinct (lambda, z) of a chunk a table of
+ * (Px/2 + 1)(Py/2 + 1) * 8 bytes (1024^2 fields at 2x padding: 16 MiB and 8 MiB). A grid
+ * whose single field and table do not fit is rejected with TOP_ERR_UNSUPPORTED before
+ * anything is launched.
  * The first call on a device looks up the scratch address (cudaGetSymbolAddress, which loads
  * the library's device code): make it before any stream capture. Calls share the scratch, so
  * two calls in flight at once on one device (other streams, other threads) race; order them on

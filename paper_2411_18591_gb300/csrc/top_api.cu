@@ -64,14 +64,7 @@ uint64_t bits(double d) {
 // ============================================================================= handle
 
 struct TransferEntry {
-  float4* hx = nullptr;
-  float2* eyh = nullptr;
-  int* kcut = nullptr;
-  float2 cg;
-  float cr;
-  float ly2;
-  float ga[6];
-  int poly;
+  float2* hq = nullptr;
 };
 
 struct top_ctx {
@@ -246,9 +239,11 @@ top_status split_twiddles(top_handle h, int P, const float2** out) {
 long long signed_index(long long k, long long P) { return k < (P + 1) / 2 ? k : k - P; }
 double freq(long long k, long long P, double d) { return double(signed_index(k, P)) / (double(P) * d); }
 
-// Separable transfer-function tables for one (lambda, z) (Eq. 5 and the Fresnel form), float64.
+// Quadrant table of the transfer function for one (lambda, z) (Eq. 5 and the Fresnel form),
+// built in float64 on the device on first use and cached; the build is waited for, so later
+// calls on any stream may read it.
 top_status transfer_tables(top_handle h, int Py, int Px, double dy, double dx, double lam, double z, int method,
-                           TransferEntry* out) {
+                           cudaStream_t st, TransferEntry* out) {
   const std::array<uint64_t, 7> key = {uint64_t(Py), uint64_t(Px), bits(dy), bits(dx), bits(lam), bits(z),
                                        uint64_t(method)};
   auto it = h->transfer.find(key);
@@ -257,61 +252,12 @@ top_status transfer_tables(top_handle h, int Py, int Px, double dy, double dx, d
     return TOP_OK;
   }
   TransferEntry te;
-  auto axis = [&](int P, double d, std::vector<float4>& t) {
-    t.resize(P);
-    for (int k = 0; k < P; ++k) {
-      const double f = freq(k, P, d);
-      double c, s;
-      cis_pi(-lam * z * f * f, &c, &s);  // exp(-i pi lambda z f^2)
-      t[k] = make_float4(float(c), float(s), float(lam * lam * f * f), 0.f);
-    }
-  };
-  std::vector<float4> hx, hy;
-  axis(Px, dx, hx);
-  axis(Py, dy, hy);
-  // y factors grouped by half (even, odd frequencies) so a column's half reads them contiguously
-  std::vector<float2> eyh(Py);
-  for (int r = 0; r < 2; ++r)
-    for (int k = 0; k < Py / 2; ++k) eyh[r * (Py / 2) + k] = make_float2(hy[2 * k + r].x, hy[2 * k + r].y);
-  TOP_TRY(upload(h, hx, &te.hx));
-  TOP_TRY(upload(h, eyh, &te.eyh));
-  const double ly = lam / (double(Py) * dy);
-  te.ly2 = float(ly * ly);
-  double c, s;
-  cis_pi(2.0 * z / lam, &c, &s);  // exp(2 pi i z / lambda)
-  const double norm = 1.0 / (double(Py) * double(Px));
-  te.cg = make_float2(float(c * norm), float(s * norm));
-  te.cr = float(2.0 * M_PI * z / lam);
-  {
-    // series of g(u) = sqrt(1 - u) - 1 + u/2 = -(1/8) u^2 - (1/16) u^3 - (5/128) u^4 - (7/256) u^5
-    //                   - (21/1024) u^6 - (33/2048) u^7 - ..., used when all propagating u <= 0.05
-    static const double c[6] = {-1.0 / 8, -1.0 / 16, -5.0 / 128, -7.0 / 256, -21.0 / 1024, -33.0 / 2048};
-    const double cr = 2.0 * M_PI * z / lam;
-    for (int i = 0; i < 6; ++i) te.ga[i] = float(cr * c[i]);
-    const double fxm = freq(Px / 2, Px, dx), fym = freq(Py / 2, Py, dy);
-    te.poly = lam * lam * (fxm * fxm + fym * fym) <= 0.05 ? 1 : 0;
-  }
-  if (method == TOP_AS) {
-    // evanescent cutoff: the radicand ((1/lambda^2) - fx^2) - fy^2 must be >= 0; it falls
-    // monotonically in |fy|, so each column keeps |signed ky| <= kcut[kx].
-    const double inv_l2 = 1.0 / (lam * lam);
-    const double fxm = freq(Px / 2, Px, dx), fym = freq(Py / 2, Py, dy);
-    const bool any_evanescent = ((inv_l2 - fxm * fxm) - fym * fym) < 0.0;
-    if (any_evanescent) {
-      std::vector<int> kc(Px);
-      for (int k = 0; k < Px; ++k) {
-        const double fx = freq(k, Px, dx);
-        const double a = inv_l2 - fx * fx;
-        int best = -1;
-        for (long long sy = 0; sy <= Py / 2; ++sy) {
-          const double fy = double(sy) / (double(Py) * dy);
-          if (a - fy * fy >= 0.0) best = int(sy); else break;
-        }
-        kc[k] = best;
-      }
-      TOP_TRY(upload(h, kc, &te.kcut));
-    }
-  }
+  void* p = nullptr;
+  TOP_CUDA(cudaMalloc(&p, size_t(Px / 2 + 1) * size_t(Py / 2 + 2) * sizeof(float2)), "cudaMalloc(transfer table)");
+  h->allocs.push_back(p);
+  te.hq = static_cast<float2*>(p);
+  TOP_CUDA(launch_transfer_table(te.hq, Py, Px, dy, dx, lam, z, method, st), "transfer table");
+  TOP_CUDA(cudaStreamSynchronize(st), "cudaStreamSynchronize(transfer table)");
   h->transfer[key] = te;
   *out = te;
   return TOP_OK;
@@ -444,25 +390,6 @@ top_status check_mod(const top_mod* m, const char* name) {
   return TOP_OK;
 }
 
-top_status check_as_remainder(const Geometry& geo, const top_grid* g, const double* lam, const double* z,
-                              int64_t n_lz) {
-  if (g->method != TOP_AS) return TOP_OK;
-  // largest non-separable phase cr * |g(u)| over propagating samples; float32 keeps it to ~1e-5 rad below 128 rad
-  const double fx = freq(geo.Px / 2, geo.Px, g->dx), fy = freq(geo.Py / 2, geo.Py, g->dy);
-  for (int64_t i = 0; i < n_lz; ++i) {
-    double u = lam[i] * lam[i] * (fx * fx + fy * fy);
-    if (u > 1.0) u = 1.0;
-    const double gu = (std::sqrt(1.0 - u) - 1.0 + 0.5 * u);
-    const double rmax = std::fabs(2.0 * M_PI * z[i] / lam[i] * gu);
-    if (rmax > 128.0)
-      return fail(TOP_ERR_UNSUPPORTED,
-                  "AS phase beyond the Fresnel terms reaches %.3g rad (> 128) for field %lld; use the Fresnel "
-                  "method, a smaller z or a larger spacing",
-                  rmax, (long long)i);
-  }
-  return TOP_OK;
-}
-
 ModDev mod_dev(const top_mod* m, int conj, const int2* circ) {
   ModDev d{};
   if (!m) return d;
@@ -518,7 +445,6 @@ top_status run_propagation(top_handle h, const Request& q, cudaStream_t st) {
   TOP_TRY(check_lz(g, q.lam, q.z, q.n_lz, true));
   TOP_TRY(check_mod(q.msrc, "source modulation"));
   TOP_TRY(check_mod(q.mepi, "epilogue modulation"));
-  TOP_TRY(check_as_remainder(geo, g, q.lam, q.z, q.n_lz));
   const int64_t B = g->batch;
   if (q.adjoint && g->input_repeat > 1) return fail(TOP_ERR_INVALID_ARG, "input_repeat applies to forward calls only");
   if (g->input_repeat > 1 && q.in && q.in == q.out)
@@ -569,16 +495,9 @@ top_status run_propagation(top_handle h, const Request& q, cudaStream_t st) {
   for (int64_t b = 0; b < B; ++b) {
     const int64_t i = q.n_lz == 1 ? 0 : b;
     TransferEntry te;
-    TOP_TRY(transfer_tables(h, geo.Py, geo.Px, g->dy, g->dx, q.lam[i], q.z[i], g->method, &te));
+    TOP_TRY(transfer_tables(h, geo.Py, geo.Px, g->dy, g->dx, q.lam[i], q.z[i], g->method, st, &te));
     FieldSet fs{};
-    fs.hx = te.hx;
-    fs.eyh = te.eyh;
-    fs.ly2 = te.ly2;
-    fs.kcut = te.kcut;
-    fs.cg = te.cg;
-    fs.cr = te.cr;
-    for (int i = 0; i < 6; ++i) fs.ga[i] = te.ga[i];
-    fs.poly = te.poly;
+    fs.hq = te.hq;
     if (q.msrc && (q.msrc->flags & TOP_MOD_LENS)) {
       TOP_TRY(lens_table(h, geo.nx, g->dx, q.lam[i], q.msrc->focal_length, &fs.src_lx));
       TOP_TRY(lens_table(h, geo.ny, g->dy, q.lam[i], q.msrc->focal_length, &fs.src_ly));
@@ -1258,7 +1177,7 @@ top_status noalloc_scratch(void** out) {
   return TOP_OK;
 }
 
-// Host images of the tables (the same float64 arithmetic as the handle's cached tables).
+// Host image of an engine's stage twiddles (the same float64 arithmetic as the handle's cached ones).
 void noalloc_engine_twiddles(int M, std::vector<float2>& tw) {
   EngineInfo info;
   find_engine(M, &info);
@@ -1272,62 +1191,6 @@ void noalloc_engine_twiddles(int M, std::vector<float2>& tw) {
     for (int j = 1; j < r; ++j)
       for (int i = 0; i < sp; ++i) tw[off + size_t(j - 1) * sp + i] = unit_root((long long)i * j, L);
     off += size_t(r - 1) * sp;
-  }
-}
-
-struct NoallocSet {
-  std::vector<float4> hx;
-  std::vector<float2> eyh;
-  std::vector<int> kcut;  // empty without evanescent samples
-  FieldSet fs;            // scalars; table pointers are set once the chunk is laid out
-};
-
-void noalloc_transfer(int Py, int Px, double dy, double dx, double lam, double z, int method, NoallocSet* o) {
-  auto axis = [&](int P, double d, std::vector<float4>& t) {
-    t.resize(P);
-    for (int k = 0; k < P; ++k) {
-      const double f = freq(k, P, d);
-      double c, s;
-      cis_pi(-lam * z * f * f, &c, &s);
-      t[k] = make_float4(float(c), float(s), float(lam * lam * f * f), 0.f);
-    }
-  };
-  std::vector<float4> hy;
-  axis(Px, dx, o->hx);
-  axis(Py, dy, hy);
-  o->eyh.resize(Py);
-  for (int r = 0; r < 2; ++r)
-    for (int k = 0; k < Py / 2; ++k) o->eyh[r * (Py / 2) + k] = make_float2(hy[2 * k + r].x, hy[2 * k + r].y);
-  FieldSet& fs = o->fs;
-  fs = FieldSet{};
-  const double ly = lam / (double(Py) * dy);
-  fs.ly2 = float(ly * ly);
-  double c, s;
-  cis_pi(2.0 * z / lam, &c, &s);
-  const double norm = 1.0 / (double(Py) * double(Px));
-  fs.cg = make_float2(float(c * norm), float(s * norm));
-  fs.cr = float(2.0 * M_PI * z / lam);
-  static const double gc[6] = {-1.0 / 8, -1.0 / 16, -5.0 / 128, -7.0 / 256, -21.0 / 1024, -33.0 / 2048};
-  const double cr = 2.0 * M_PI * z / lam;
-  for (int i = 0; i < 6; ++i) fs.ga[i] = float(cr * gc[i]);
-  const double fxm = freq(Px / 2, Px, dx), fym = freq(Py / 2, Py, dy);
-  fs.poly = lam * lam * (fxm * fxm + fym * fym) <= 0.05 ? 1 : 0;
-  o->kcut.clear();
-  if (method == TOP_AS) {
-    const double inv_l2 = 1.0 / (lam * lam);
-    if (((inv_l2 - fxm * fxm) - fym * fym) < 0.0) {
-      o->kcut.resize(Px);
-      for (int k = 0; k < Px; ++k) {
-        const double fx = freq(k, Px, dx);
-        const double a = inv_l2 - fx * fx;
-        int best = -1;
-        for (long long sy = 0; sy <= Py / 2; ++sy) {
-          const double fy = double(sy) / (double(Py) * dy);
-          if (a - fy * fy >= 0.0) best = int(sy); else break;
-        }
-        o->kcut[k] = best;
-      }
-    }
   }
 }
 
@@ -1346,30 +1209,36 @@ top_status propagate_noalloc(const top_grid* g, const void* in, void* out, const
   TOP_TRY(check_grid(g, &geo));
   TOP_TRY(check_engines(geo));
   TOP_TRY(check_lz(g, lam, z, n_lz, true));
-  TOP_TRY(check_as_remainder(geo, g, lam, z, n_lz));
   if (g->input_repeat > 1) return fail(TOP_ERR_UNSUPPORTED, "top_propagate_noalloc takes input_repeat 0 or 1");
   TOP_TRY(check_ptr(in, "input field"));
   TOP_TRY(check_ptr(out, "output field"));
   const int64_t B = g->batch;
   const long long plane = (long long)geo.ny * geo.nx;
 
-  // scratch budget: twiddles, kMaxSets table slots, then the workspace of a chunk
+  // scratch budget: the twiddles, table slots for the distinct (lambda, z) sets, then the workspace
   EngineInfo ix, iy;
   find_engine(geo.Px / 2, &ix);
   find_engine(geo.Py / 2, &iy);
   const size_t tw_bytes = align256(std::max(1, ix.tw_size) * sizeof(float2)) +
                           align256(std::max(1, iy.tw_size) * sizeof(float2)) +
                           align256(size_t(geo.Px / 2) * sizeof(float2)) + align256(size_t(geo.Py / 2) * sizeof(float2));
-  const size_t set_bytes = align256(size_t(geo.Px) * sizeof(float4)) + align256(size_t(geo.Py) * sizeof(float2)) +
-                           align256(size_t(geo.Px) * sizeof(int));
-  const size_t table_bytes = tw_bytes + kMaxSets * set_bytes;
+  const size_t set_bytes = align256(size_t(geo.Px / 2 + 1) * size_t(geo.Py / 2 + 2) * sizeof(float2));
   const size_t ws_field = size_t(geo.Px) * size_t(geo.ny) * sizeof(float2);
   const size_t cap = TOP_NOALLOC_SCRATCH_BYTES;
-  if (table_bytes + ws_field > cap)
+  if (tw_bytes + set_bytes + ws_field > cap)
     return fail(TOP_ERR_UNSUPPORTED,
                 "one %dx%d field (padded %dx%d) needs %zu bytes of static scratch (workspace %zu + tables %zu), "
                 "above the %zu bytes of top_propagate_noalloc",
-                geo.ny, geo.nx, geo.Py, geo.Px, table_bytes + ws_field, ws_field, table_bytes, cap);
+                geo.ny, geo.nx, geo.Py, geo.Px, tw_bytes + set_bytes + ws_field, ws_field, tw_bytes + set_bytes, cap);
+  int64_t distinct = 0;
+  {
+    std::vector<std::pair<uint64_t, uint64_t>> all;
+    for (int64_t i = 0; i < n_lz; ++i) all.emplace_back(bits(lam[i]), bits(z[i]));
+    std::sort(all.begin(), all.end());
+    distinct = std::unique(all.begin(), all.end()) - all.begin();
+  }
+  const int slots = int(std::min<int64_t>({int64_t(kMaxSets), distinct, int64_t((cap - tw_bytes - ws_field) / set_bytes)}));
+  const size_t table_bytes = tw_bytes + size_t(slots) * set_bytes;
   const int64_t chunk = std::min<int64_t>({B, int64_t(kMaxFields), int64_t((cap - table_bytes) / ws_field)});
 
   void* scratch = nullptr;
@@ -1377,11 +1246,16 @@ top_status propagate_noalloc(const top_grid* g, const void* in, void* out, const
   unsigned char* base = static_cast<unsigned char*>(scratch);
   float2* ws = reinterpret_cast<float2*>(base + table_bytes);
 
+  // twiddles: host image, one copy ordered on the stream
   std::vector<float2> twx, twy, wpx(geo.Px / 2), wpy(geo.Py / 2);
   noalloc_engine_twiddles(geo.Px / 2, twx);
   noalloc_engine_twiddles(geo.Py / 2, twy);
   for (int q = 0; q < geo.Px / 2; ++q) wpx[q] = unit_root(q, geo.Px);
   for (int q = 0; q < geo.Py / 2; ++q) wpy[q] = unit_root(q, geo.Py);
+  std::vector<unsigned char> img;
+  const size_t o_twx = put(img, twx), o_twy = put(img, twy), o_wpx = put(img, wpx), o_wpy = put(img, wpy);
+  if (img.size() > tw_bytes) return fail(TOP_ERR_INTERNAL, "static twiddle image above its reserved size");
+  TOP_CUDA(cudaMemcpyAsync(base, img.data(), img.size(), cudaMemcpyHostToDevice, st), "cudaMemcpyAsync(static twiddles)");
 
   PassParams p{};
   p.ny = geo.ny;
@@ -1396,6 +1270,10 @@ top_status propagate_noalloc(const top_grid* g, const void* in, void* out, const
   p.adjoint = 0;
   p.src_kind = SRC_FIELD;
   p.epi_kind = EPI_FIELD;
+  p.twx = reinterpret_cast<const float2*>(base + o_twx);
+  p.twy = reinterpret_cast<const float2*>(base + o_twy);
+  p.wpx = reinterpret_cast<const float2*>(base + o_wpx);
+  p.wpy = reinterpret_cast<const float2*>(base + o_wpy);
   p.ws = ws;
   p.ws_stride = (long long)geo.Px * geo.ny;
   p.in_stride = plane;
@@ -1409,13 +1287,10 @@ top_status propagate_noalloc(const top_grid* g, const void* in, void* out, const
   p.src_group = 1;
   p.in_repeat = 1;
 
-  std::vector<unsigned char> img;
-  std::vector<NoallocSet> sets;
   std::vector<std::pair<uint64_t, uint64_t>> keys;
   int64_t pos = 0;
   while (pos < B) {
-    // fields of this chunk and their distinct (lambda, z) sets
-    sets.clear();
+    // fields of this chunk and their distinct (lambda, z) sets, one table slot each
     keys.clear();
     int64_t n = 0;
     while (pos + n < B && n < chunk) {
@@ -1424,31 +1299,18 @@ top_status propagate_noalloc(const top_grid* g, const void* in, void* out, const
       size_t k = 0;
       while (k < keys.size() && keys[k] != key) ++k;
       if (k == keys.size()) {
-        if ((int)keys.size() == kMaxSets) break;
+        if ((int)keys.size() == slots) break;
         keys.push_back(key);
-        sets.emplace_back();
-        noalloc_transfer(geo.Py, geo.Px, g->dy, g->dx, lam[i], z[i], g->method, &sets.back());
+        float2* hq = reinterpret_cast<float2*>(base + tw_bytes + k * set_bytes);
+        TOP_CUDA(launch_transfer_table(hq, geo.Py, geo.Px, g->dy, g->dx, lam[i], z[i], g->method, st), "transfer table");
+        FieldSet fs{};
+        fs.hq = hq;
+        p.sets[k] = fs;
       }
       p.set_of[n] = (unsigned char)k;
       ++n;
     }
-    // host image of the tables -> one copy into the scratch, ordered on the stream
-    img.clear();
-    const size_t o_twx = put(img, twx), o_twy = put(img, twy), o_wpx = put(img, wpx), o_wpy = put(img, wpy);
-    p.twx = reinterpret_cast<const float2*>(base + o_twx);
-    p.twy = reinterpret_cast<const float2*>(base + o_twy);
-    p.wpx = reinterpret_cast<const float2*>(base + o_wpx);
-    p.wpy = reinterpret_cast<const float2*>(base + o_wpy);
-    p.nsets = int(sets.size());
-    for (size_t k = 0; k < sets.size(); ++k) {
-      FieldSet fs = sets[k].fs;
-      fs.hx = reinterpret_cast<const float4*>(base + put(img, sets[k].hx));
-      fs.eyh = reinterpret_cast<const float2*>(base + put(img, sets[k].eyh));
-      fs.kcut = sets[k].kcut.empty() ? nullptr : reinterpret_cast<const int*>(base + put(img, sets[k].kcut));
-      p.sets[k] = fs;
-    }
-    if (img.size() > table_bytes) return fail(TOP_ERR_INTERNAL, "static table image above its reserved size");
-    TOP_CUDA(cudaMemcpyAsync(base, img.data(), img.size(), cudaMemcpyHostToDevice, st), "cudaMemcpyAsync(static tables)");
+    p.nsets = int(keys.size());
     p.nfields = int(n);
     p.in = static_cast<const float2*>(in) + pos * plane;
     p.out = static_cast<float2*>(out) + pos * plane;

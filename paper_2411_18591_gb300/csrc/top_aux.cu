@@ -133,6 +133,55 @@ cudaError_t launch_reduce_partials(const float* part_phase, const float* part_am
   return cudaGetLastError();
 }
 
+// Transfer function (Eq. 5; the Fresnel form for method TOP_FRESNEL_TF) on one quadrant of
+// the padded frequency grid, in float64: f = |k| / (P d), the AS radicand evaluated as
+// ((1 / (lambda lambda)) - fx fx) - fy fy with every operation rounded on its own (no fused
+// multiply-add, so the evanescent decision is the same as an IEEE evaluation of that
+// expression), H = 0 where it is negative, else exp(2 pi i z sqrt(radicand)). Phases are
+// reduced in cycles (c - rint(c) is exact) before the sine and cosine.
+__global__ void __launch_bounds__(256) k_transfer_table(float2* hq, int Py, int Px, double dy, double dx, double lam,
+                                                        double z, int method) {
+  const int my = Py / 2, even = my / 2 + 1;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int akx = blockIdx.y;
+  if (j > my + 1) return;
+  float2* out = hq + (long long)akx * (my + 2) + j;
+  if (j == my + 1) {
+    *out = make_float2(0.f, 0.f);
+    return;
+  }
+  const int aky = j < even ? 2 * j : 2 * (j - even) + 1;
+  const double fx = double(akx) / (double(Px) * dx);
+  const double fy = double(aky) / (double(Py) * dy);
+  const double fx2 = __dmul_rn(fx, fx), fy2 = __dmul_rn(fy, fy);
+  const double norm = 1.0 / (double(Py) * double(Px));
+  double cyc;
+  if (method == TOP_AS) {
+    const double rad = __dsub_rn(__dsub_rn(1.0 / __dmul_rn(lam, lam), fx2), fy2);
+    if (rad < 0.0) {
+      *out = make_float2(0.f, 0.f);
+      return;
+    }
+    const double c = __dmul_rn(z, sqrt(rad));
+    cyc = c - rint(c);
+  } else {
+    const double a = z / lam;
+    const double b = 0.5 * lam * z * (fx2 + fy2);
+    cyc = (a - rint(a)) - (b - rint(b));
+  }
+  double sn, cs;
+  sincospi(2.0 * cyc, &sn, &cs);
+  *out = make_float2(float(cs * norm), float(sn * norm));
+}
+
+cudaError_t launch_transfer_table(float2* hq, int Py, int Px, double dy, double dx, double lam, double z, int method,
+                                  cudaStream_t s) {
+  const int my = Py / 2;
+  dim3 grid((my + 2 + 255) / 256, Px / 2 + 1);
+  TOP_LAUNCH(k_transfer_table, grid, 256, 0, s, hq, Py, Px, dy, dx, lam, z, method);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_mse(long long n, const float* I, const float* T, float* grad, double* partial, double* loss,
                        cudaStream_t s) {
   TOP_LAUNCH(k_mse_partial, kMseBlocks, 256, 0, s, n, I, T, grad, partial);

@@ -1,5 +1,6 @@
 // Auxiliary kernels: standalone modulation (Eq. 1) and its backward, deterministic
-// reductions of modulation-gradient partials, the MSE detector loss.
+// reductions of modulation-gradient partials, the MSE detector loss, the transfer-function
+// table (Eq. 5 and the Fresnel form).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -17,6 +18,9 @@ cudaError_t launch_reduce_partials(const float* part_phase, const float* part_am
                                    cudaStream_t s);
 cudaError_t launch_mse(long long n, const float* I, const float* T, float* grad, double* partial, double* loss,
                        cudaStream_t s);
+// Quadrant table of H / (Py Px) for one (lambda, z) in the FieldSet::hq layout (float64 arithmetic).
+cudaError_t launch_transfer_table(float2* hq, int Py, int Px, double dy, double dx, double lam, double z, int method,
+                                  cudaStream_t s);
 
 }  // namespace top
 

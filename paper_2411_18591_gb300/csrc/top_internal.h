@@ -15,27 +15,18 @@ namespace top {
 constexpr int kMaxSets = 24;      // distinct (lambda, z) parameter sets per launch
 constexpr int kMaxFields = 2048;  // fields per launch (larger batches run in chunks)
 
-// One (lambda, z) parameter set: separable factors of the transfer function and of
-// the lenses, precomputed in float64 on the host and rounded to float32.
-//   H(kx, ky) = cg * hx[kx].ex * ey[ky] * exp(i cr g(ux + uy)) (AS), cg * ex * ey (Fresnel)
-// with u = lambda^2 (fx^2 + fy^2), g(u) = sqrt(1 - u) - 1 + u/2 = -(u^2/4) / (sqrt(1-u) + 1 - u/2),
-// ex = exp(-i pi lambda z fx^2), cg = exp(2 pi i z / lambda) / (Py Px), cr = 2 pi z / lambda;
-// uy = ly2 * sky^2 with sky the signed index of ky and ly2 = (lambda / (Py dy))^2.
+// One (lambda, z) parameter set: the transfer function and the lens factors, computed in
+// float64 and rounded to float32. H depends on the frequencies only through fx^2 and fy^2, so
+// one quadrant is stored: hq[|kx| (My + 2) + j] = H(|kx|, |ky|) / (Py Px) for |kx| <= Px / 2,
+// with the even |ky| = 2 j at j < My/2 + 1, the odd |ky| = 2 (j - My/2 - 1) + 1 after them and
+// one zero entry that makes rows whole 16-byte units (one row per |kx|; a column half reads the
+// even or the odd part of its row).
 struct FieldSet {
-  const float4* hx;      // [Px] by frequency index kx: {ex.re, ex.im, ux, 0}
-  const float2* eyh;     // [Py] ey by half: eyh[r My + k] = ey[2k + r]
-  const int* kcut;       // [Px] or null: largest |signed ky| that propagates in column kx (-1: none)
+  const float2* hq;      // [Px/2 + 1][My + 2]
   const float2* src_lx;  // lens factor tables of the source-side modulation: [nx], [ny]
   const float2* src_ly;
   const float2* epi_lx;  // lens factor tables of the epilogue-side modulation
   const float2* epi_ly;
-  float2 cg;
-  float cr;
-  float ly2;
-  // cr * g(u) as u^2 (a[0] + u (a[1] + ... + u a[5])) when every propagating u is <= 0.05 (poly = 1):
-  // the binomial series of sqrt(1 - u) - 1 + u/2 through u^7, truncation below 2e-9 relative there
-  float ga[6];
-  int poly;
 };
 
 // Element modulation (Eq. 1) applied in a prologue or epilogue.

@@ -2,8 +2,8 @@
 //
 //   R1  rows:    modulate (Eq. 1), zero-pad along x, forward DFT along x,
 //                store transposed:  ws[field][kx][y]
-//   C   columns: zero-pad along y, forward DFT along y, multiply by H(kx, ky),
-//                inverse DFT along y, crop:  ws[field][kx][y] in place
+//   C   columns: zero-pad along y, forward DFT along y, multiply by H(kx, ky) / (Py Px)
+//                (a float64-built table), inverse DFT along y, crop:  ws[field][kx][y] in place
 //   R2  rows:    inverse DFT along x, crop, epilogue (modulation, |psi|^2,
 //                incoherent sums of Eq. 14, or modulation gradients)
 //
@@ -23,7 +23,6 @@
 // and the column pass reads pairs of lines as one 16-byte stream.
 #pragma once
 
-#include <climits>
 #include <type_traits>
 #include <utility>
 
@@ -83,12 +82,26 @@ struct ColShape {
                               : (EN::NS == 2 && THREADS == 256) ? 2 : 1;
   // line stride: room for the column and an exchange buffer, and LS = 16 / CB (mod 16) so that the
   // CB lines of a copy instruction fall on distinct banks
-  __host__ __device__ static int line_stride(int ny) {
+  __host__ __device__ static constexpr int line_stride(int ny) {
     const int l = ny > EN::BUF ? ny : EN::BUF;
     return l + ((16 / CB - l) % 16 + 16) % 16;
   }
-  static size_t smem(int ny) { return sizeof(float2) * size_t(COLS) * (line_stride(ny) + EN::BUF); }
-  static constexpr size_t SMEM_MAX = sizeof(float2) * COLS * ((2 * EN::M > EN::BUF ? 2 * EN::M : EN::BUF) + 16 + EN::BUF);
+  // With padding exactly 2 (ny = M) the transfer-function rows of the block's columns (HS entries
+  // each) are staged in shared memory too, where that keeps two blocks per SM; otherwise the
+  // rows are read from global memory.
+  static constexpr int HS = EN::M + 2;
+  template <bool X2>
+  static constexpr bool stage_h() {
+    return X2 && sizeof(float2) * COLS * (line_stride(EN::M) + EN::BUF + HS) <= 110 * 1024;
+  }
+  template <bool X2>
+  static size_t smem(int ny) {
+    return sizeof(float2) * (size_t(COLS) * (line_stride(ny) + EN::BUF) + (stage_h<X2>() ? COLS * HS : 0));
+  }
+  static constexpr size_t SMEM_MAX =
+      sizeof(float2) * COLS * ((2 * EN::M > EN::BUF ? 2 * EN::M : EN::BUF) + 16 + EN::BUF > line_stride(EN::M) + EN::BUF + HS
+                                   ? (2 * EN::M > EN::BUF ? 2 * EN::M : EN::BUF) + 16 + EN::BUF
+                                   : line_stride(EN::M) + EN::BUF + HS);
   static_assert(COLS % CB == 0, "columns come in whole copy units");
   static_assert(SMEM_MAX <= 227 * 1024, "column block above the shared-memory limit");
 };
@@ -134,17 +147,6 @@ __device__ __forceinline__ float2 cis(float a) {
   } else {
     sincosf(a, &s, &c);
   }
-  return make_float2(c, s);
-}
-
-// exp(i a) for |a| below a few thousand rad (the transfer-function remainder is bounded by 128 rad
-// on the host): the same reduction without the library path.
-__device__ __forceinline__ float2 cis_small(float a) {
-  const float n = rintf(a * 0.15915494309189535f);
-  float r = fmaf(-n, 6.28125f, a);
-  r = fmaf(-n, 1.9353071795864769e-3f, r);
-  float s, c;
-  __sincosf(r, &s, &c);
   return make_float2(c, s);
 }
 
@@ -276,46 +278,29 @@ __global__ void __launch_bounds__(RowShape<EX>::THREADS) k_rows_fwd(const __grid
 
 // ----------------------------------------------------------------------------- C
 
-// Multiply the bins of half r of a column by H(kx, ky) / (cg ex[kx]), conjugated for the adjoint:
-// ey[ky] exp(i cr g(ux + uy)) with ky = 2k + r. The column factor cg ex[kx] is applied after the
-// inverse transform. MODE 0: Fresnel (no remainder); 1: AS with the series of g; 2: AS, exact g.
-// The loop has no branches: the evanescent cutoff is a select (kc = INT_MAX: none) and the
-// adjoint a sign.
-template <class EY, int MODE>
-__device__ __forceinline__ void apply_transfer(float2 (&v)[EY::E], const PassParams& p, const FieldSet& fs, float ux,
-                                               int kc, int r, int t) {
-  const float sg = p.adjoint ? -1.f : 1.f;
-  const float2* ey = fs.eyh + r * p.My;
-  const int half_py = (p.Py + 1) / 2;
+// Multiply the bins of half r of column kx by H(kx, ky) / (Py Px), conjugated for the adjoint,
+// from the quadrant row of |kx| (shared or global memory): bin k of the half holds ky = 2k + r,
+// whose |signed ky| is 2k + r below the middle and Py - 2k - r above it, so the even half reads
+// entries k or M - k of the row's even part and the odd half entries k or M - 1 - k of its odd part.
+template <class EY, bool SHARED>
+__device__ __forceinline__ void apply_transfer(float2 (&v)[EY::E], const float2* row, int r, bool adjoint, int t) {
+  constexpr int M = EY::M;
+  const float sg = adjoint ? -1.f : 1.f;
+  const float2* part = row + r * (M / 2 + 1);
+  const int mirror = M - r;
+  // eight loads at a time: the compiler barrier keeps it from hoisting all E loads at once
+  constexpr int CH = EY::E % 8 == 0 ? 8 : EY::E;
 #pragma unroll
-  for (int e = 0; e < EY::E; ++e) {
-    const int k = EY::bin(t, e);
-    float2 h = ldg2(ey + k);
-    if constexpr (MODE != 0) {
-      const int ky = 2 * k + r;
-      const int sy = ky < half_py ? ky : ky - p.Py;
-      const float fsy = float(sy);
-      const float u = fmaf(fs.ly2 * fsy, fsy, ux);
-      float rr;
-      if constexpr (MODE == 1) {
-        rr = fmaf(u, fs.ga[5], fs.ga[4]);
-        rr = fmaf(u, rr, fs.ga[3]);
-        rr = fmaf(u, rr, fs.ga[2]);
-        rr = fmaf(u, rr, fs.ga[1]);
-        rr = fmaf(u, rr, fs.ga[0]);
-        rr *= u * u;
-      } else {
-        // cr (-(u^2/4)) / (sqrt(1-u) + 1 - u/2), free of cancellation
-        const float sq = sqrtf(fmaxf(1.f - u, 0.f));
-        rr = __fdividef(fs.cr * (-0.25f * u * u), sq + 1.f - 0.5f * u);
-      }
-      h = c_mul(h, cis_small(rr));
-      const bool ev = abs(sy) > kc;
-      h.x = ev ? 0.f : h.x;
-      h.y = ev ? 0.f : h.y;
+  for (int e0 = 0; e0 < EY::E; e0 += CH) {
+#pragma unroll
+    for (int e = e0; e < e0 + CH; ++e) {
+      const int k = EY::bin(t, e);
+      const int j = k < M / 2 ? k : mirror - k;
+      float2 h = SHARED ? part[j] : ldg2(part + j);
+      h.y *= sg;
+      v[e] = c_mul(v[e], h);
     }
-    h.y *= sg;
-    v[e] = c_mul(v[e], h);
+    asm volatile("" ::: "memory");
   }
 }
 
@@ -347,7 +332,14 @@ __global__ void __launch_bounds__(ColShape<EY>::THREADS, ColShape<EY>::MINB) k_c
   float2* line = smem + cl * LS;                            // [COLS][LS]
   float2* obuf = smem + COLS * LS + cl * EY::BUF;           // the odd half's exchange buffer and output
   float2* xbuf = r ? obuf : line;
+  float2* hrows = smem + COLS * (LS + EY::BUF);             // [COLS][HS] transfer-function rows
   float2* ws = p.ws + (long long)f * p.ws_stride;
+  auto abs_kx = [&](int c) {  // |signed kx| of the block's column c (the last column repeats past the end)
+    const int kp = min(kpos0 + c, p.Px - 1);
+    const int rx = kp >= p.Mx ? 1 : 0;
+    const int kx = 2 * (kp - rx * p.Mx) + rx;
+    return kx <= p.Px / 2 ? kx : p.Px - kx;
+  };
 
   // (A) de-interleave each unit of CB columns into contiguous lines: copy j of a unit holds
   // sample j / CB of its line j % CB
@@ -355,24 +347,24 @@ __global__ void __launch_bounds__(ColShape<EY>::THREADS, ColShape<EY>::MINB) k_c
     for (int j = threadIdx.x; j < CB * ny; j += NT)
       top_cp_async8(smem + (u + j % CB) * LS + j / CB, ws + col_src<CB>(j, kpos0 + u, ny));
   }
+  if constexpr (SH::template stage_h<X2>()) {
+    constexpr int H4 = SH::HS / 2;  // 16-byte units per row
+    for (int i = threadIdx.x; i < COLS * H4; i += NT) {
+      const int c = i / H4, q = i - c * H4;
+      top_cp_async16(hrows + c * SH::HS + 2 * q, fs.hq + (long long)abs_kx(c) * SH::HS + 2 * q);
+    }
+  }
   top_cp_async_wait_all();
   __syncthreads();
-  const int col = min(kpos0 + cl, p.Px - 1);
-  const int rx = col >= p.Mx ? 1 : 0;
-  const int kx = 2 * (col - rx * p.Mx) + rx;
-  const float4 hx = __ldg(fs.hx + kx);
-  const int kc = fs.kcut ? __ldg(fs.kcut + kx) : INT_MAX;
 
   float2 v[E];
   fold<EY, X2, 1>(v, line, ny, p.oy, r, p.wpy, t);
   __syncthreads();  // the lines become the even halves' exchange buffers
   EY::fwd(v, xbuf, t, p.twy);
-  if (p.method != TOP_AS) {
-    apply_transfer<EY, 0>(v, p, fs, hx.z, kc, r, t);
-  } else if (fs.poly) {
-    apply_transfer<EY, 1>(v, p, fs, hx.z, kc, r, t);
+  if constexpr (SH::template stage_h<X2>()) {
+    apply_transfer<EY, true>(v, hrows + cl * SH::HS, r, p.adjoint, t);
   } else {
-    apply_transfer<EY, 2>(v, p, fs, hx.z, kc, r, t);
+    apply_transfer<EY, false>(v, fs.hq + (long long)abs_kx(cl) * SH::HS, r, p.adjoint, t);
   }
   EY::inv(v, xbuf, t, p.twy);
   EY::sync_group();  // every lane is past the last reads of its exchange buffer
@@ -395,20 +387,18 @@ __global__ void __launch_bounds__(ColShape<EY>::THREADS, ColShape<EY>::MINB) k_c
   }
   __syncthreads();
   if (!r) {
-    // combine with the column factor of H (conjugated for the adjoint) into the column's line
-    float2 cx = c_mul(fs.cg, make_float2(hx.x, hx.y));
-    if (p.adjoint) cx = c_conj(cx);
+    // combine the halves into the column's line
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int pos = EY::in_pos(t, e);
       const float2 o = obuf[pos];
       if constexpr (X2) {
-        if (pos < M / 2) line[pos + M / 2] = c_mul(c_sub(v[e], o), cx);
-        else line[pos - M / 2] = c_mul(c_add(v[e], o), cx);
+        if (pos < M / 2) line[pos + M / 2] = c_sub(v[e], o);
+        else line[pos - M / 2] = c_add(v[e], o);
       } else {
         const int y0 = pos - p.oy, y1 = pos + M - p.oy;
-        if (y0 >= 0 && y0 < ny) line[y0] = c_mul(c_add(v[e], o), cx);
-        if (y1 >= 0 && y1 < ny) line[y1] = c_mul(c_sub(v[e], o), cx);
+        if (y0 >= 0 && y0 < ny) line[y0] = c_add(v[e], o);
+        if (y1 >= 0 && y1 < ny) line[y1] = c_sub(v[e], o);
       }
     }
   }
@@ -572,7 +562,7 @@ cudaError_t launch_cols_t(const PassParams& p, cudaStream_t s) {
   static const cudaError_t attr = set_smem(k_cols<EY, X2>, SH::SMEM_MAX);
   if (attr != cudaSuccess) return attr;
   dim3 grid((p.Px + SH::COLS - 1) / SH::COLS, p.nfields);
-  TOP_LAUNCH((k_cols<EY, X2>), grid, SH::THREADS, SH::smem(p.ny), s, p);
+  TOP_LAUNCH((k_cols<EY, X2>), grid, SH::THREADS, SH::template smem<X2>(p.ny), s, p);
   return cudaGetLastError();
 }
 
