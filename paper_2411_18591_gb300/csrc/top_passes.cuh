@@ -455,30 +455,37 @@ __device__ __forceinline__ void epilogue(const PassParams& p, const FieldSet& fs
   }
 }
 
-// Combine the two inverse halves of each row in shared memory ([r][ROWS][M], natural order) over
-// the cropped window and hand every output sample to the epilogue (one cooperative loop).
+// Combine the two inverse halves of each row in shared memory ([r][ROWS][M], natural order; the
+// odd half already carries exp(2 pi i pos / P)) over the cropped window and hand every output
+// sample to the epilogue (one cooperative loop; with padding exactly 2 its trip count is fixed).
 template <class EX, bool X2, int KIND>
 __device__ __forceinline__ void combine_rows(const PassParams& p, const FieldSet& fs, const float2* smem, int f, int g,
                                              bool first, int y0, int nrows) {
   using SH = RowShape<EX>;
   constexpr int M = EX::M, ROWS = SH::ROWS, NT = SH::THREADS;
-  const int nx = p.nx;
-  for (int rr = 0; rr < nrows; ++rr) {
-    for (int x = threadIdx.x; x < nx; x += NT) {
-      int pos;
-      bool upper;
-      if constexpr (X2) {
-        upper = x >= M / 2;
-        pos = upper ? x - M / 2 : x + M / 2;
-      } else {
-        const int pp = x + p.ox;
-        upper = pp >= M;
-        pos = upper ? pp - M : pp;
-      }
-      const float2 o = c_mulc(smem[(ROWS + rr) * M + pos], ldg2(p.wpx + pos));
-      const float2 ev = smem[rr * M + pos];
-      epilogue<KIND>(p, fs, f, g, first, y0 + rr, x, upper ? c_sub(ev, o) : c_add(ev, o));
+  auto one = [&](int rr, int x) {
+    int pos;
+    bool upper;
+    if constexpr (X2) {
+      upper = x >= M / 2;
+      pos = upper ? x - M / 2 : x + M / 2;
+    } else {
+      const int pp = x + p.ox;
+      upper = pp >= M;
+      pos = upper ? pp - M : pp;
     }
+    const float2 o = smem[(ROWS + rr) * M + pos];
+    const float2 ev = smem[rr * M + pos];
+    epilogue<KIND>(p, fs, f, g, first, y0 + rr, x, upper ? c_sub(ev, o) : c_add(ev, o));
+  };
+  if constexpr (X2 && M % NT == 0) {
+    for (int rr = 0; rr < nrows; ++rr) {
+#pragma unroll 4
+      for (int i = 0; i < M / NT; ++i) one(rr, threadIdx.x + i * NT);
+    }
+  } else {
+    for (int rr = 0; rr < nrows; ++rr)
+      for (int x = threadIdx.x; x < p.nx; x += NT) one(rr, x);
   }
 }
 
@@ -522,9 +529,28 @@ __global__ void __launch_bounds__(RowShape<EX>::THREADS) k_rows_inv(const __grid
     }
     EX::inv(v, smem + grp * EX::BUF, t, p.twx);
     __syncthreads();  // the exchange buffers alias the half-row buffers
-    // both halves in natural order -> shared [r][ROWS][M]
+    // both halves in natural order -> shared [r][ROWS][M], the odd one times exp(2 pi i pos / P)
+    float2* hrow = smem + (r * ROWS + row) * M;
+    if (r) {
+      if constexpr (X2) {
+        const float2 wt = ldg2(p.wpx + t);
+        for_slots(
+            [&](auto ec) {
+              constexpr int e = decltype(ec)::value;
+              hrow[EX::in_pos(t, e)] = c_mulc(v[e], slot_split_twiddle<EX, e>(wt));
+            },
+            std::make_integer_sequence<int, E>{});
+      } else {
 #pragma unroll
-    for (int e = 0; e < E; ++e) smem[(r * ROWS + row) * M + EX::in_pos(t, e)] = v[e];
+        for (int e = 0; e < E; ++e) {
+          const int pos = EX::in_pos(t, e);
+          hrow[pos] = c_mulc(v[e], ldg2(p.wpx + pos));
+        }
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < E; ++e) hrow[EX::in_pos(t, e)] = v[e];
+    }
     __syncthreads();
     // combine the halves over the cropped window, epilogue, coalesced store
     if (p.epi_kind == EPI_FIELD) {
