@@ -57,6 +57,12 @@ struct RowShape {
   static constexpr int ROWBUF = ROWS * 2 * EN::M;  // input rows (n <= P = 2M) or E/O halves of the inverse
   static constexpr int MAX2 = TILE > XCH ? TILE : XCH;
   static constexpr size_t SMEM = sizeof(float2) * (MAX2 > ROWBUF ? MAX2 : ROWBUF);
+  // R1 stages the planes its source needs besides the field rows after SMEM (at most five floats
+  // per sample: intensity gradient, phase, amplitude, complex mask)
+  static constexpr size_t SMEM_SRC_MAX = SMEM + sizeof(float) * 5 * ROWS * 2 * EN::M < 227 * 1024
+                                             ? SMEM + sizeof(float) * 5 * ROWS * 2 * EN::M
+                                             : 227 * 1024;
+  static_assert(SMEM % 16 == 0, "staged planes start on a 16-byte boundary");
   static_assert(THREADS <= 1024, "row block too large");
   static_assert(EN::M % 2 == 0, "the four-line workspace blocks need P = 2M to be a multiple of 4");
 };
@@ -180,6 +186,27 @@ __device__ __forceinline__ float2 load_src(const PassParams& p, const FieldSet& 
   return s;
 }
 
+// Floats per R1 block of the planes staged besides the field rows: the intensity gradient
+// (SRC_INTENSITY) and the phase, amplitude and complex mask of the source modulation.
+__host__ __device__ inline size_t src_plane_floats(const PassParams& p, int rows) {
+  const size_t plane = size_t(rows) * size_t(p.nx);
+  size_t n = 0;
+  if (p.src_kind == SRC_INTENSITY) n += plane;
+  if (p.msrc.flags & TOP_MOD_PHASE) n += plane;
+  if (p.msrc.flags & TOP_MOD_AMPLITUDE) n += plane;
+  if (p.msrc.flags & TOP_MOD_COMPLEX) n += 2 * plane;
+  return n;
+}
+
+// Whether R1 copies its source rows (and planes) into shared memory with asynchronous 16-byte
+// copies: every row start must be 16-byte aligned and the planes must fit.
+template <class EN>
+__host__ __device__ inline bool src_staged(const PassParams& p) {
+  const size_t extra = src_plane_floats(p, RowShape<EN>::ROWS);
+  if (extra == 0) return p.nx % 2 == 0;
+  return p.nx % 4 == 0 && RowShape<EN>::SMEM + sizeof(float) * extra <= RowShape<EN>::SMEM_SRC_MAX;
+}
+
 // Slots of half r folded from a line of n samples at offset o, sample x at line[x * LS] (the odd
 // half carries exp(-2 pi i p / 2M); the copy at p + M picks up the opposite sign). X2: n = M and
 // o = M/2 (padding exactly 2), where every slot has one source, (pos + M/2) mod M, lying in the
@@ -232,17 +259,66 @@ __global__ void __launch_bounds__(RowShape<EX>::THREADS) k_rows_fwd(const __grid
   const int nx = p.nx, ny = p.ny;
 
   // (A) modulated input rows -> shared [ROWS][nx]
-  if (p.src_kind == SRC_FIELD && !p.msrc.flags && (nx & 1) == 0) {
-    // plain field rows: one contiguous block, copied as 16-byte pieces
-    const float4* src = reinterpret_cast<const float4*>(p.in + (long long)(f / p.in_repeat) * p.in_stride +
-                                                        (long long)y0 * nx);
-    float4* dst4 = reinterpret_cast<float4*>(smem);
-    const int n4 = nrows * nx / 2, all4 = ROWS * nx / 2;
-    for (int i = threadIdx.x; i < all4; i += NT) {
-      if (i < n4) top_cp_async16(dst4 + i, src + i);
-      else dst4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (src_staged<EX>(p)) {
+    // the field rows and the planes the source needs, each one contiguous block copied as
+    // 16-byte pieces, then the source arithmetic in place
+    const bool inten = p.src_kind == SRC_INTENSITY;
+    const ModDev& m = p.msrc;
+    const long long row0 = (long long)y0 * nx;
+    const float2* src = inten ? p.psi + (long long)f * p.psi_stride + row0
+                              : p.in + (long long)(f / p.in_repeat) * p.in_stride + row0;
+    {
+      const float4* s4 = reinterpret_cast<const float4*>(src);
+      float4* d4 = reinterpret_cast<float4*>(smem);
+      const int n4 = nrows * nx / 2, all4 = ROWS * nx / 2;
+      for (int i = threadIdx.x; i < all4; i += NT) {
+        if (i < n4) top_cp_async16(d4 + i, s4 + i);
+        else d4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
     }
+    float* planes = reinterpret_cast<float*>(smem + SH::SMEM / sizeof(float2));
+    const int plane = ROWS * nx;
+    auto stage = [&](const float* from, int floats_per_sample) {
+      float* dst = planes;
+      planes += plane * floats_per_sample;
+      const float4* s4 = reinterpret_cast<const float4*>(from);
+      float4* d4 = reinterpret_cast<float4*>(dst);
+      const int n4 = nrows * nx * floats_per_sample / 4;
+      for (int i = threadIdx.x; i < n4; i += NT) top_cp_async16(d4 + i, s4 + i);
+      return dst;
+    };
+    const long long midx = (long long)f * m.stride + row0;
+    const float* gi = inten ? stage(p.gI + (long long)(f / p.src_group) * p.gI_stride + row0, 1) : nullptr;
+    const float* ph = (m.flags & TOP_MOD_PHASE) ? stage(m.phase + midx, 1) : nullptr;
+    const float* am = (m.flags & TOP_MOD_AMPLITUDE) ? stage(m.amp + midx, 1) : nullptr;
+    const float2* cm = (m.flags & TOP_MOD_COMPLEX)
+                           ? reinterpret_cast<const float2*>(stage(reinterpret_cast<const float*>(m.cmask + midx), 2))
+                           : nullptr;
     top_cp_async_wait_all();
+    if (inten || m.flags) {
+      __syncthreads();
+      const float w2 = inten ? 2.f * (p.weights ? __ldg(p.weights + f) : 1.f) : 1.f;
+      for (int rr = 0; rr < nrows; ++rr) {
+        const int y = y0 + rr;
+        const int2 rg = (m.flags & TOP_MOD_CIRC) ? __ldg(m.circ + y) : make_int2(0, nx - 1);
+        const float2 ly = (m.flags & TOP_MOD_LENS) ? ldg2(fs.src_ly + y) : make_float2(1.f, 0.f);
+        for (int x = threadIdx.x; x < nx; x += NT) {
+          const int i = rr * nx + x;
+          float2 s = smem[i];
+          if (inten) s = c_scale(s, w2 * gi[i]);
+          if (m.flags) {
+            float2 mv = make_float2(1.f, 0.f);
+            if (m.flags & TOP_MOD_COMPLEX) mv = cm[i];
+            if (m.flags & TOP_MOD_AMPLITUDE) mv = c_scale(mv, am[i]);
+            if (m.flags & TOP_MOD_PHASE) mv = c_mul(mv, cis(ph[i]));
+            if (m.flags & TOP_MOD_LENS) mv = c_mul(mv, c_mul(ldg2(fs.src_lx + x), ly));
+            if (x < rg.x || x > rg.y) mv = make_float2(0.f, 0.f);
+            s = c_mul(s, m.conj ? c_conj(mv) : mv);
+          }
+          smem[i] = s;
+        }
+      }
+    }
   } else {
 #pragma unroll 2
     for (int rr = 0; rr < ROWS; ++rr) {
@@ -575,10 +651,11 @@ inline cudaError_t set_smem(K kernel, size_t bytes) {
 template <class EX, bool X2>
 cudaError_t launch_rows_fwd_t(const PassParams& p, cudaStream_t s) {
   using SH = RowShape<EX>;
-  static const cudaError_t attr = set_smem(k_rows_fwd<EX, X2>, SH::SMEM);
+  static const cudaError_t attr = set_smem(k_rows_fwd<EX, X2>, SH::SMEM_SRC_MAX);
   if (attr != cudaSuccess) return attr;
   dim3 grid((p.ny + SH::ROWS - 1) / SH::ROWS, p.nfields);
-  TOP_LAUNCH((k_rows_fwd<EX, X2>), grid, SH::THREADS, SH::SMEM, s, p);
+  const size_t bytes = SH::SMEM + (src_staged<EX>(p) ? sizeof(float) * src_plane_floats(p, SH::ROWS) : 0);
+  TOP_LAUNCH((k_rows_fwd<EX, X2>), grid, SH::THREADS, bytes, s, p);
   return cudaGetLastError();
 }
 
