@@ -198,6 +198,7 @@ def run_ours(args, rank, world):
     import __graft_entry__ as ge
     ge.build()
     from paper_2411_18591_gb300 import binding as Bd
+    from paper_2411_18591_gb300 import dist as D
     from paper_2411_18591_gb300.fourf import FourF
 
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -208,11 +209,13 @@ def run_ours(args, rank, world):
     sysm = FourF(n=c["n"], d=c["d"], f=c["f"], lens_radius=c["lens_radius"], pupil_radius=c["pupil_radius"],
                  objects=objects, comps=c["comps"], wavelengths=tuple(S.cfg4_wavelengths(c["wavelengths"])),
                  pad=c["pad"])
-    obj_host = S.cfg4_objects(objects, c["comps"], c["n"]).reshape(-1, c["n"], c["n"]).astype(np.complex64)
+    # weak scaling: rank r takes objects [r K, (r + 1) K) of one seeded global set
+    first = rank * objects
+    obj_host = S.cfg4_objects(objects, c["comps"], c["n"], first=first).reshape(-1, c["n"], c["n"]).astype(np.complex64)
     obj_pinned = torch.from_numpy(obj_host).pin_memory()
     obj = obj_pinned.to(dev)
     phase = torch.from_numpy(S.cfg4_pupil_phase(c["n"]).astype(np.float32)).to(dev)
-    target = torch.from_numpy(S.cfg4_target(objects, c["n"]).astype(np.float32)).to(dev)
+    target = torch.from_numpy(S.cfg4_target(objects, c["n"], first=first).astype(np.float32)).to(dev)
     gphase = torch.empty_like(phase)
     bufs = {}
     dist = world > 1
@@ -222,7 +225,7 @@ def run_ours(args, rank, world):
     def step(x):
         loss, _ = sysm.step(x, phase, target, gphase, bufs)
         if dist:
-            tdist.all_reduce(gphase)
+            D.average_gradient(gphase)  # the one exchange of a step: mean pupil-phase gradient
         return loss
 
     for _ in range(max(3, args.warmup)):

@@ -28,10 +28,11 @@ _M1 = np.uint64(0xBF58476D1CE4E5B9)
 _M2 = np.uint64(0x94D049BB133111EB)
 
 
-def splitmix64(seed: int, count: int) -> np.ndarray:
-    """``count`` consecutive SplitMix64 outputs for ``seed`` as uint64."""
+def splitmix64(seed: int, count: int, start: int = 0) -> np.ndarray:
+    """Outputs ``start`` .. ``start + count - 1`` of the SplitMix64 stream of ``seed`` as uint64
+    (the generator is a counter, so any stretch can be drawn directly)."""
     with np.errstate(over="ignore"):
-        idx = np.arange(1, count + 1, dtype=np.uint64)
+        idx = np.arange(start + 1, start + count + 1, dtype=np.uint64)
         z = np.uint64(seed & 0xFFFFFFFFFFFFFFFF) + idx * _GOLDEN
         z = (z ^ (z >> np.uint64(30))) * _M1
         z = (z ^ (z >> np.uint64(27))) * _M2
@@ -39,11 +40,11 @@ def splitmix64(seed: int, count: int) -> np.ndarray:
     return z
 
 
-def uniform(seed: int, shape, low: float = 0.0, high: float = 1.0) -> np.ndarray:
-    """Uniform doubles in [low, high) from the top 53 bits of SplitMix64."""
+def uniform(seed: int, shape, low: float = 0.0, high: float = 1.0, start: int = 0) -> np.ndarray:
+    """Uniform doubles in [low, high) from the top 53 bits of SplitMix64 (stream offset ``start``)."""
     shape = (shape,) if isinstance(shape, int) else tuple(shape)
     n = int(np.prod(shape)) if shape else 1
-    u = (splitmix64(seed, n) >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+    u = (splitmix64(seed, n, start) >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
     return (low + (high - low) * u).reshape(shape)
 
 
@@ -176,10 +177,11 @@ def cfg3_field(desc) -> np.ndarray:
     return to_c64(phase_screen_field(desc["seed"], desc["n"]))
 
 
-def cfg4_objects(objects: int = 16, comps: int = 3, n: int = 1024):
-    """Polarised 4f workload inputs: amplitude objects per (object, component)."""
+def cfg4_objects(objects: int = 16, comps: int = 3, n: int = 1024, first: int = 0):
+    """Polarised 4f workload inputs: amplitude objects per (object, component); objects
+    ``first`` .. ``first + objects - 1`` of one seeded stream (a data-parallel shard)."""
     seed = BASE_SEED + 3
-    amp = uniform(sub_seed(seed, 0), (objects, comps, n, n))
+    amp = uniform(sub_seed(seed, 0), (objects, comps, n, n), start=first * comps * n * n)
     return amp
 
 
@@ -195,8 +197,8 @@ def cfg4_pupil_phase(n: int = 1024) -> np.ndarray:
     return uniform(sub_seed(BASE_SEED + 3, 1), (n, n), -math.pi, math.pi)
 
 
-def cfg4_target(objects: int = 16, n: int = 1024) -> np.ndarray:
-    return 0.5 * uniform(sub_seed(BASE_SEED + 3, 2), (objects, n, n))
+def cfg4_target(objects: int = 16, n: int = 1024, first: int = 0) -> np.ndarray:
+    return 0.5 * uniform(sub_seed(BASE_SEED + 3, 2), (objects, n, n), start=first * n * n)
 
 
 def cfg5a_coherence(n: int = 64):
