@@ -57,10 +57,16 @@ struct RowShape {
   static constexpr int ROWBUF = ROWS * 2 * EN::M;  // input rows (n <= P = 2M) or E/O halves of the inverse
   static constexpr int MAX2 = TILE > XCH ? TILE : XCH;
   static constexpr size_t SMEM = sizeof(float2) * (MAX2 > ROWBUF ? MAX2 : ROWBUF);
+  // the inverse pass keeps four 128-thread blocks per SM (128 registers)
+  static constexpr int MINB_INV = THREADS == 128 ? 4 : 1;
   // R1 stages the planes its source needs besides the field rows after SMEM (at most five floats
   // per sample: intensity gradient, phase, amplitude, complex mask)
   static constexpr size_t SMEM_SRC_MAX = SMEM + sizeof(float) * 5 * ROWS * 2 * EN::M < 227 * 1024
                                              ? SMEM + sizeof(float) * 5 * ROWS * 2 * EN::M
+                                             : 227 * 1024;
+  // R2 stages its epilogue planes (accumulators, masks, the saved modulation input) after SMEM
+  static constexpr size_t SMEM_EPI_MAX = SMEM + sizeof(float) * 10 * ROWS * 2 * EN::M < 227 * 1024
+                                             ? SMEM + sizeof(float) * 10 * ROWS * 2 * EN::M
                                              : 227 * 1024;
   static_assert(SMEM % 16 == 0, "staged planes start on a 16-byte boundary");
   static_assert(THREADS <= 1024, "row block too large");
@@ -487,6 +493,95 @@ __global__ void __launch_bounds__(ColShape<EY>::THREADS, ColShape<EY>::MINB) k_c
 
 // ----------------------------------------------------------------------------- R2
 
+// Rows of the R2 epilogue held in shared memory ([ROWS][nx] each, sample i = rr nx + x): the
+// accumulators of a group (intensity, modulation-gradient partials), written back once after the
+// group's last field, and the planes the epilogue reads (mask factors, the saved modulation input).
+struct EpiPlanes {
+  float* acc_i;
+  float* acc_ph;
+  float* acc_am;
+  float2* acc_cm;
+  const float* ph;
+  const float* am;
+  const float2* cm;
+  const float2* xs;
+};
+
+// Floats per sample of the staged epilogue planes.
+__host__ __device__ inline int epi_plane_floats(const PassParams& p) {
+  int n = 0;
+  const uint32_t fl = p.mepi.flags;
+  if (p.epi_kind == EPI_INTENSITY) n += 1;
+  if (p.epi_kind == EPI_MODGRAD) {
+    if (p.part_phase) n += 1;
+    if (p.part_amp) n += 1;
+    if (p.part_mask) n += 2;
+    if (p.part_phase || p.part_amp || p.part_mask) n += 2;  // saved input
+  }
+  if (fl & TOP_MOD_PHASE) n += 1;
+  if (fl & TOP_MOD_AMPLITUDE) n += 1;
+  if (fl & TOP_MOD_COMPLEX) n += 2;
+  return n;
+}
+
+// Whether R2 stages its epilogue planes: there is something to stage, rows are 16-byte units
+// and the planes fit.
+template <class EN>
+__host__ __device__ inline bool epi_staged(const PassParams& p) {
+  const int n = epi_plane_floats(p);
+  return n > 0 && p.nx % 4 == 0 &&
+         RowShape<EN>::SMEM + sizeof(float) * size_t(n) * RowShape<EN>::ROWS * p.nx <= RowShape<EN>::SMEM_EPI_MAX;
+}
+
+// M(x, y) of Eq. 1 from staged planes (sample i of the block) with the aperture range rg of the row
+__device__ __forceinline__ float2 mod_value_planes(const EpiPlanes& e, uint32_t flags, int conj, const float2* lx,
+                                                   float2 ly, int2 rg, int i, int x) {
+  float2 r = make_float2(1.f, 0.f);
+  if (flags & TOP_MOD_COMPLEX) r = e.cm[i];
+  if (flags & TOP_MOD_AMPLITUDE) r = c_scale(r, e.am[i]);
+  if (flags & TOP_MOD_PHASE) r = c_mul(r, cis(e.ph[i]));
+  if (flags & TOP_MOD_LENS) r = c_mul(r, c_mul(ldg2(lx + x), ly));
+  if ((flags & TOP_MOD_CIRC) && (x < rg.x || x > rg.y)) r = make_float2(0.f, 0.f);
+  return conj ? c_conj(r) : r;
+}
+
+// Epilogue of one output sample val = psi(y, x) of field f in group g, from staged planes.
+template <int KIND>
+__device__ __forceinline__ void epilogue_planes(const PassParams& p, const FieldSet& fs, const EpiPlanes& e, int f,
+                                                bool first, int y, int x, int i, float2 ly, int2 rg, float2 val) {
+  const long long idx = (long long)y * p.nx + x;
+  const ModDev& m = p.mepi;
+  if constexpr (KIND == EPI_FIELD) {
+    if (m.flags) val = c_mul(val, mod_value_planes(e, m.flags, m.conj, fs.epi_lx, ly, rg, i, x));
+    p.out[(long long)f * p.out_stride + idx] = val;
+  } else if constexpr (KIND == EPI_INTENSITY) {
+    if (m.flags) val = c_mul(val, mod_value_planes(e, m.flags, m.conj, fs.epi_lx, ly, rg, i, x));
+    if (p.out) p.out[(long long)f * p.out_stride + idx] = val;
+    const float w = p.weights ? __ldg(p.weights + f) : 1.f;
+    const float v = w * fmaf(val.x, val.x, val.y * val.y);
+    e.acc_i[i] = first ? v : e.acc_i[i] + v;
+  } else {
+    const float2 mv = mod_value_planes(e, m.flags, 0, fs.epi_lx, ly, rg, i, x);
+    if (p.out) p.out[(long long)f * p.out_stride + idx] = c_mulc(val, mv);
+    if (e.xs) {
+      const float2 xs = e.xs[i];
+      if (e.acc_ph) {
+        const float2 ys = c_mul(mv, xs);
+        e.acc_ph[i] += fmaf(val.y, ys.x, -val.x * ys.y);
+      }
+      if (e.acc_am) {
+        const float2 mna = mod_value_planes(e, m.flags & ~TOP_MOD_AMPLITUDE, 0, fs.epi_lx, ly, rg, i, x);
+        const float2 d = c_mul(mna, xs);
+        e.acc_am[i] += fmaf(val.x, d.x, val.y * d.y);
+      }
+      if (e.acc_cm) {
+        const float2 mnc = mod_value_planes(e, m.flags & ~TOP_MOD_COMPLEX, 0, fs.epi_lx, ly, rg, i, x);
+        e.acc_cm[i] = c_add(e.acc_cm[i], c_mulc(val, c_mul(mnc, xs)));
+      }
+    }
+  }
+}
+
 // Epilogue of one output sample val = psi(y, x) of field f in group g.
 template <int KIND>
 __device__ __forceinline__ void epilogue(const PassParams& p, const FieldSet& fs, int f, int g, bool first, int y,
@@ -536,9 +631,33 @@ __device__ __forceinline__ void epilogue(const PassParams& p, const FieldSet& fs
 // sample to the epilogue (one cooperative loop; with padding exactly 2 its trip count is fixed).
 template <class EX, bool X2, int KIND>
 __device__ __forceinline__ void combine_rows(const PassParams& p, const FieldSet& fs, const float2* smem, int f, int g,
-                                             bool first, int y0, int nrows) {
+                                             bool first, int y0, int nrows, const EpiPlanes* ep) {
   using SH = RowShape<EX>;
   constexpr int M = EX::M, ROWS = SH::ROWS, NT = SH::THREADS;
+  if (ep) {
+    const ModDev& m = p.mepi;
+    for (int rr = 0; rr < nrows; ++rr) {
+      const int y = y0 + rr;
+      const int2 rg = (m.flags & TOP_MOD_CIRC) ? __ldg(m.circ + y) : make_int2(0, p.nx - 1);
+      const float2 ly = (m.flags & TOP_MOD_LENS) ? ldg2(fs.epi_ly + y) : make_float2(1.f, 0.f);
+      for (int x = threadIdx.x; x < p.nx; x += NT) {
+        int pos;
+        bool upper;
+        if constexpr (X2) {
+          upper = x >= M / 2;
+          pos = upper ? x - M / 2 : x + M / 2;
+        } else {
+          const int pp = x + p.ox;
+          upper = pp >= M;
+          pos = upper ? pp - M : pp;
+        }
+        const float2 o = smem[(ROWS + rr) * M + pos];
+        const float2 ev = smem[rr * M + pos];
+        epilogue_planes<KIND>(p, fs, *ep, f, first, y, x, rr * p.nx + x, ly, rg, upper ? c_sub(ev, o) : c_add(ev, o));
+      }
+    }
+    return;
+  }
   auto one = [&](int rr, int x) {
     int pos;
     bool upper;
@@ -566,7 +685,7 @@ __device__ __forceinline__ void combine_rows(const PassParams& p, const FieldSet
 }
 
 template <class EX, bool X2>
-__global__ void __launch_bounds__(RowShape<EX>::THREADS) k_rows_inv(const __grid_constant__ PassParams p) {
+__global__ void __launch_bounds__(RowShape<EX>::THREADS, RowShape<EX>::MINB_INV) k_rows_inv(const __grid_constant__ PassParams p) {
   using SH = RowShape<EX>;
   constexpr int G = EX::G, E = EX::E, M = EX::M, ROWS = SH::ROWS, LD = SH::LD, NT = SH::THREADS;
   TOP_DYN_SMEM(float2, smem);
@@ -580,10 +699,78 @@ __global__ void __launch_bounds__(RowShape<EX>::THREADS) k_rows_inv(const __grid
   const int f1 = min(f0 + p.group, p.nfields);
   const int ny = p.ny;
 
+  // staged epilogue planes: accumulators and shared mask rows once per block, the saved input
+  // and per-field mask rows once per field (copied while the field is transformed)
+  const bool staged = epi_staged<EX>(p);
+  EpiPlanes ep{};
+  const int nx = p.nx;
+  const int plane = ROWS * nx;
+  const long long row0 = (long long)y0 * nx;
+  const ModDev& m = p.mepi;
+  const bool grads = p.epi_kind == EPI_MODGRAD && (p.part_phase || p.part_amp || p.part_mask);
+  if (staged) {
+    float* pl = reinterpret_cast<float*>(smem + SH::SMEM / sizeof(float2));
+    auto carve = [&](int floats_per_sample) {
+      float* d = pl;
+      pl += plane * floats_per_sample;
+      return d;
+    };
+    auto copy_in = [&](float* dst, const float* src, int floats_per_sample) {
+      const float4* s4 = reinterpret_cast<const float4*>(src);
+      float4* d4 = reinterpret_cast<float4*>(dst);
+      const int n4 = nrows * nx * floats_per_sample / 4;
+      for (int i = threadIdx.x; i < n4; i += NT) top_cp_async16(d4 + i, s4 + i);
+    };
+    if (p.epi_kind == EPI_INTENSITY) ep.acc_i = carve(1);
+    if (grads) {
+      const long long pidx = (long long)g * p.part_stride + row0;
+      auto acc = [&](float* dst, const float* src, int fps) {
+        if (p.part_accumulate) {
+          copy_in(dst, src, fps);
+        } else {
+          for (int i = threadIdx.x; i < nrows * nx * fps; i += NT) dst[i] = 0.f;
+        }
+      };
+      if (p.part_phase) { ep.acc_ph = carve(1); acc(ep.acc_ph, p.part_phase + pidx, 1); }
+      if (p.part_amp) { ep.acc_am = carve(1); acc(ep.acc_am, p.part_amp + pidx, 1); }
+      if (p.part_mask) {
+        ep.acc_cm = reinterpret_cast<float2*>(carve(2));
+        acc(reinterpret_cast<float*>(ep.acc_cm), reinterpret_cast<const float*>(p.part_mask + pidx), 2);
+      }
+      ep.xs = reinterpret_cast<const float2*>(carve(2));
+    }
+    if (m.flags & TOP_MOD_PHASE) ep.ph = carve(1);
+    if (m.flags & TOP_MOD_AMPLITUDE) ep.am = carve(1);
+    if (m.flags & TOP_MOD_COMPLEX) ep.cm = reinterpret_cast<const float2*>(carve(2));
+    if (m.stride == 0) {
+      if (ep.ph) copy_in(const_cast<float*>(ep.ph), m.phase + row0, 1);
+      if (ep.am) copy_in(const_cast<float*>(ep.am), m.amp + row0, 1);
+      if (ep.cm) copy_in(reinterpret_cast<float*>(const_cast<float2*>(ep.cm)), reinterpret_cast<const float*>(m.cmask + row0), 2);
+    }
+  }
+  auto stage_field = [&](int f) {
+    auto copy_in = [&](float* dst, const float* src, int floats_per_sample) {
+      const float4* s4 = reinterpret_cast<const float4*>(src);
+      float4* d4 = reinterpret_cast<float4*>(dst);
+      const int n4 = nrows * nx * floats_per_sample / 4;
+      for (int i = threadIdx.x; i < n4; i += NT) top_cp_async16(d4 + i, s4 + i);
+    };
+    if (grads)
+      copy_in(reinterpret_cast<float*>(const_cast<float2*>(ep.xs)),
+              reinterpret_cast<const float*>(p.xs + (long long)f * p.xs_stride + row0), 2);
+    if (m.stride != 0) {
+      const long long midx = (long long)f * m.stride + row0;
+      if (ep.ph) copy_in(const_cast<float*>(ep.ph), m.phase + midx, 1);
+      if (ep.am) copy_in(const_cast<float*>(ep.am), m.amp + midx, 1);
+      if (ep.cm) copy_in(reinterpret_cast<float*>(const_cast<float2*>(ep.cm)), reinterpret_cast<const float*>(m.cmask + midx), 2);
+    }
+  };
+
 #pragma unroll 1
   for (int f = f0; f < f1; ++f) {
     const FieldSet& fs = p.sets[p.set_of[f]];
     const float2* ws = p.ws + (long long)f * p.ws_stride;
+    if (staged) stage_field(f);
     float2 v[E];
     if constexpr (SH::DIRECT) {
       // bins straight from the workspace: four consecutive lanes read one 32-byte sector
@@ -627,16 +814,32 @@ __global__ void __launch_bounds__(RowShape<EX>::THREADS) k_rows_inv(const __grid
 #pragma unroll
       for (int e = 0; e < E; ++e) hrow[EX::in_pos(t, e)] = v[e];
     }
+    if (staged) top_cp_async_wait_all();
     __syncthreads();
     // combine the halves over the cropped window, epilogue, coalesced store
+    const EpiPlanes* epp = staged ? &ep : nullptr;
     if (p.epi_kind == EPI_FIELD) {
-      combine_rows<EX, X2, EPI_FIELD>(p, fs, smem, f, g, f == f0, y0, nrows);
+      combine_rows<EX, X2, EPI_FIELD>(p, fs, smem, f, g, f == f0, y0, nrows, epp);
     } else if (p.epi_kind == EPI_INTENSITY) {
-      combine_rows<EX, X2, EPI_INTENSITY>(p, fs, smem, f, g, f == f0, y0, nrows);
+      combine_rows<EX, X2, EPI_INTENSITY>(p, fs, smem, f, g, f == f0, y0, nrows, epp);
     } else {
-      combine_rows<EX, X2, EPI_MODGRAD>(p, fs, smem, f, g, f == f0, y0, nrows);
+      combine_rows<EX, X2, EPI_MODGRAD>(p, fs, smem, f, g, f == f0, y0, nrows, epp);
     }
     __syncthreads();
+  }
+  if (staged) {
+    // accumulators of the group back to global memory
+    auto copy_out = [&](float* dst, const float* src, int floats_per_sample) {
+      float4* d4 = reinterpret_cast<float4*>(dst);
+      const float4* s4 = reinterpret_cast<const float4*>(src);
+      const int n4 = nrows * nx * floats_per_sample / 4;
+      for (int i = threadIdx.x; i < n4; i += NT) d4[i] = s4[i];
+    };
+    if (ep.acc_i) copy_out(p.outf + (long long)g * p.outf_stride + row0, ep.acc_i, 1);
+    const long long pidx = (long long)g * p.part_stride + row0;
+    if (ep.acc_ph) copy_out(p.part_phase + pidx, ep.acc_ph, 1);
+    if (ep.acc_am) copy_out(p.part_amp + pidx, ep.acc_am, 1);
+    if (ep.acc_cm) copy_out(reinterpret_cast<float*>(p.part_mask + pidx), reinterpret_cast<const float*>(ep.acc_cm), 2);
   }
 }
 
@@ -672,10 +875,12 @@ cudaError_t launch_cols_t(const PassParams& p, cudaStream_t s) {
 template <class EX, bool X2>
 cudaError_t launch_rows_inv_t(const PassParams& p, cudaStream_t s) {
   using SH = RowShape<EX>;
-  static const cudaError_t attr = set_smem(k_rows_inv<EX, X2>, SH::SMEM);
+  static const cudaError_t attr = set_smem(k_rows_inv<EX, X2>, SH::SMEM_EPI_MAX);
   if (attr != cudaSuccess) return attr;
   dim3 grid((p.ny + SH::ROWS - 1) / SH::ROWS, (p.nfields + p.group - 1) / p.group);
-  TOP_LAUNCH((k_rows_inv<EX, X2>), grid, SH::THREADS, SH::SMEM, s, p);
+  const size_t bytes =
+      SH::SMEM + (epi_staged<EX>(p) ? sizeof(float) * size_t(epi_plane_floats(p)) * SH::ROWS * p.nx : 0);
+  TOP_LAUNCH((k_rows_inv<EX, X2>), grid, SH::THREADS, bytes, s, p);
   return cudaGetLastError();
 }
 
