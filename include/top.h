@@ -147,6 +147,28 @@ top_status top_propagate(top_handle h, const top_grid* g, const void* in, void* 
                          const double* lambda, const double* z, int64_t n_lz,
                          const top_mod* pre, const top_mod* post, void* stream);
 
+/* One stage of a system chain: the field entering the stage is multiplied by `pre` (Eq. 1;
+ * NULL: none) and propagated by `z` (Eq. 4). `keep`, when non-NULL, receives the stage's output
+ * field (complex64 [batch][ny][nx] device, caller-owned); the last stage's must be NULL. */
+typedef struct top_stage {
+  double z;
+  const top_mod* pre;
+  void* keep;
+} top_stage;
+
+/* A system of §2 (elements in sequence, Fig. 1) on every field: x_0 = in and
+ * x_k = P_{z_k}(pre_k x_{k-1}) for k = 1 .. nstages, with the inverse row pass of each stage and
+ * the forward row pass of the next fused into one kernel, so x_k reaches global memory only
+ * through stages[k-1].keep. The last field x_K goes to `out` (may be NULL when `intensity` is
+ * given) and, when `intensity` is non-NULL, |x_K|^2 summed over each `group` consecutive fields
+ * (Eq. 14) to intensity [batch / group][ny][nx] (float32). g->input_repeat as in top_propagate.
+ * lambda: host, n_lz values (1 or batch), shared by every stage. Results equal the same
+ * sequence of top_propagate calls; a boundary whose modulation planes would not fit in shared
+ * memory runs as two launches (through `keep`, or a field-sized scratch in the workspace). */
+top_status top_fused_chain(top_handle h, const top_grid* g, const void* in, void* out, float* intensity,
+                           int64_t group, const double* lambda, int64_t n_lz, const top_stage* stages,
+                           int nstages, void* stream);
+
 /* Bytes of the library's static device scratch used by top_propagate_noalloc. */
 #define TOP_NOALLOC_SCRATCH_BYTES (64u << 20)
 

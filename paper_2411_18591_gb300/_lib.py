@@ -35,6 +35,10 @@ class TopModGrads(C.Structure):
                 ("grad_mask", C.c_void_p)]
 
 
+class TopStage(C.Structure):
+    _fields_ = [("z", C.c_double), ("pre", C.POINTER(TopMod)), ("keep", C.c_void_p)]
+
+
 class TopError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"{STATUS.get(status, status)}: {message}")
@@ -59,6 +63,7 @@ SIGNATURES = {
     "top_zcritical": (C.c_double, [C.c_double, C.c_double, C.c_double]),
     "top_propagate": (C.c_int, [_P, _GRID, _P, _P, _D, _D, _I64, _MOD, _MOD, _P]),
     "top_propagate_noalloc": (C.c_int, [_GRID, _P, _P, _D, _D, _I64, _P]),
+    "top_fused_chain": (C.c_int, [_P, _GRID, _P, _P, _P, _I64, _D, _I64, C.POINTER(TopStage), C.c_int, _P]),
     "top_propagate_backward": (C.c_int, [_P, _GRID, _P, _P, _D, _D, _I64, _MOD, _MOD, _GRADS, _P]),
     "top_propagate_intensity": (C.c_int, [_P, _GRID, _P, _P, _P, _I64, _P, _D, _D, _I64, _MOD, _MOD, _P]),
     "top_propagate_intensity_backward": (C.c_int, [_P, _GRID, _P, _P, _P, _I64, _P, _D, _D, _I64, _MOD, _MOD,

@@ -15,7 +15,7 @@ from typing import Optional, Sequence
 import torch
 
 from . import _lib
-from ._lib import TopGrid, TopMod, TopModGrads, check, doubles
+from ._lib import TopGrid, TopMod, TopModGrads, TopStage, check, doubles
 
 METHODS = {"as": _lib.TOP_AS, "angular_spectrum": _lib.TOP_AS, "fresnel": _lib.TOP_FRESNEL_TF,
            "fresnel_tf": _lib.TOP_FRESNEL_TF, _lib.TOP_AS: _lib.TOP_AS, _lib.TOP_FRESNEL_TF: _lib.TOP_FRESNEL_TF}
@@ -155,6 +155,56 @@ def top_propagate(field: torch.Tensor, dy: float, dx: float, lam, z, pad: float 
     check(_lib.load().top_propagate(handle(field.device), C.byref(g), field.data_ptr(), out.data_ptr(), lams, zs, n,
                                     _mod(pre), _mod(post), _stream(field)))
     return out
+
+
+@dataclass
+class Stage:
+    """One stage of a system chain: multiply by ``pre`` (Eq. 1), then propagate by ``z`` (Eq. 4);
+    ``keep`` (complex64, the batch's shape) receives the stage's output field."""
+    z: float
+    pre: Optional[Modulation] = None
+    keep: Optional[torch.Tensor] = None
+
+
+def top_fused_chain(field: torch.Tensor, dy: float, dx: float, lam, stages: Sequence[Stage], pad: float = 2.0,
+                    method="as", out: Optional[torch.Tensor] = None, intensity_group: Optional[int] = None,
+                    input_repeat: int = 1, want_field: bool = True):
+    """x_K of x_k = P_{z_k}(pre_k x_{k-1}), x_0 = field, with the row passes between stages fused.
+
+    Returns (out, intensity): ``out`` the last field (None if ``want_field`` is False and an
+    intensity is asked for), ``intensity`` the sum of |x_K|^2 over each ``intensity_group``
+    consecutive fields (Eq. 14) or None.
+    """
+    _field(field, "field")
+    b, ny, nx = _shape3(field)
+    b *= input_repeat
+    if out is None and (want_field or intensity_group is None):
+        out = torch.empty((b, ny, nx), dtype=field.dtype, device=field.device)
+    elif out is not None:
+        _field(out, "out")
+    inten = None
+    group = 1
+    if intensity_group is not None:
+        group = int(intensity_group)
+        if group < 1 or b % group:
+            raise ValueError("intensity_group must divide the batch")
+        inten = torch.empty((b // group, ny, nx), dtype=torch.float32, device=field.device)
+    lams = [lam] if isinstance(lam, (int, float)) else list(lam)
+    mods = []
+    arr = (TopStage * len(stages))()
+    for i, st in enumerate(stages):
+        arr[i].z = float(st.z)
+        if st.pre is not None:
+            m = st.pre.to_c()
+            mods.append(m)
+            arr[i].pre = C.pointer(m)
+        if st.keep is not None:
+            _field(st.keep, "keep")
+            arr[i].keep = st.keep.data_ptr()
+    g = make_grid(b, ny, nx, dy, dx, pad, method, input_repeat)
+    check(_lib.load().top_fused_chain(handle(field.device), C.byref(g), field.data_ptr(), _ptr(out), _ptr(inten), group,
+                                      doubles(lams), len(lams), arr, len(stages), _stream(field)))
+    return out, inten
 
 
 def top_propagate_noalloc(field: torch.Tensor, dy: float, dx: float, lam, z, pad: float = 2.0, method="as", *,

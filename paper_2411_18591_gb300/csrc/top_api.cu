@@ -159,17 +159,17 @@ bool find_engine(int M, EngineInfo* info) {
          engine_info_large(M, info) || engine_info_mixed(M, info);
 }
 
-cudaError_t launch_pass(int kind, int M, const PassParams& p, cudaStream_t s) {
+cudaError_t launch_pass(int kind, int M, const PassParams& p, cudaStream_t s, const PassParams* next = nullptr) {
   bool found = false;
-  cudaError_t e = launch_pass_small(kind, M, p, s, &found);
+  cudaError_t e = launch_pass_small(kind, M, p, next, s, &found);
   if (found) return e;
-  e = launch_pass_mid(kind, M, p, s, &found);
+  e = launch_pass_mid(kind, M, p, next, s, &found);
   if (found) return e;
-  e = launch_pass_m1024(kind, M, p, s, &found);
+  e = launch_pass_m1024(kind, M, p, next, s, &found);
   if (found) return e;
-  e = launch_pass_large(kind, M, p, s, &found);
+  e = launch_pass_large(kind, M, p, next, s, &found);
   if (found) return e;
-  e = launch_pass_mixed(kind, M, p, s, &found);
+  e = launch_pass_mixed(kind, M, p, next, s, &found);
   if (found) return e;
   return cudaErrorInvalidValue;
 }
@@ -673,6 +673,205 @@ top_status run_propagation(top_handle h, const Request& q, cudaStream_t st) {
   return TOP_OK;
 }
 
+// ============================================================================= fused system chain
+
+// x_0 = in, x_k = P_{z_k}(pre_k x_{k-1}); the inverse row pass of stage k and the forward row
+// pass of stage k+1 run as one kernel where the next source's staged planes fit (else the pair
+// runs as two launches through `keep` or a field scratch in the workspace, with the same results).
+top_status run_chain(top_handle h, const top_grid* g, const void* in, void* out, float* inten, int64_t group,
+                     const double* lam, int64_t n_lz, const top_stage* stages, int K, cudaStream_t st) {
+  Geometry geo;
+  TOP_TRY(check_grid(g, &geo));
+  TOP_TRY(check_engines(geo));
+  TOP_TRY(check_lz(g, lam, nullptr, n_lz, false));
+  if (!stages || K < 1) return fail(TOP_ERR_INVALID_ARG, "a chain needs at least one stage");
+  for (int k = 0; k < K; ++k) {
+    if (!std::isfinite(stages[k].z)) return fail(TOP_ERR_INVALID_ARG, "stage %d: z must be finite", k);
+    TOP_TRY(check_mod(stages[k].pre, "stage modulation"));
+    if (stages[k].keep) TOP_TRY(check_ptr(stages[k].keep, "stage keep buffer"));
+  }
+  if (stages[K - 1].keep) return fail(TOP_ERR_INVALID_ARG, "the last stage's field goes to out; its keep must be NULL");
+  const int64_t B = g->batch;
+  TOP_TRY(check_ptr(in, "input field"));
+  if (!out && !inten) return fail(TOP_ERR_INVALID_ARG, "a chain needs out, intensity or both");
+  if (out) TOP_TRY(check_ptr(out, "output field"));
+  if (inten) {
+    TOP_TRY(check_ptr(inten, "intensity"));
+    if (group < 1 || B % group != 0)
+      return fail(TOP_ERR_INVALID_ARG, "group (%lld) must be >= 1 and divide batch (%lld)", (long long)group, (long long)B);
+    if (group > kMaxFields) return fail(TOP_ERR_UNSUPPORTED, "group larger than %d fields", kMaxFields);
+  }
+  const int64_t in_repeat = g->input_repeat > 1 ? g->input_repeat : 1;
+  if (in_repeat > 1) {
+    if (in == out) return fail(TOP_ERR_INVALID_ARG, "input_repeat > 1 needs distinct input and output buffers");
+    for (int k = 0; k < K; ++k)
+      if (stages[k].keep == in) return fail(TOP_ERR_INVALID_ARG, "input_repeat > 1 needs keep buffers apart from the input");
+  }
+  TOP_TRY(bind(h));
+
+  const float2 *twx, *twy, *wpx, *wpy;
+  TOP_TRY(engine_twiddles(h, geo.Px / 2, &twx));
+  TOP_TRY(engine_twiddles(h, geo.Py / 2, &twy));
+  TOP_TRY(split_twiddles(h, geo.Px, &wpx));
+  TOP_TRY(split_twiddles(h, geo.Py, &wpy));
+  std::vector<const int2*> circ(K, nullptr);
+  for (int k = 0; k < K; ++k)
+    if (stages[k].pre && (stages[k].pre->flags & TOP_MOD_CIRC))
+      TOP_TRY(circ_table(h, geo.ny, geo.nx, g->dy, g->dx, stages[k].pre->radius, &circ[k]));
+  // per stage and field: the transfer table of (lambda, z_k) and the lens tables of pre_k
+  std::vector<std::vector<FieldSet>> fsets(K, std::vector<FieldSet>(B));
+  for (int k = 0; k < K; ++k) {
+    const top_mod* m = stages[k].pre;
+    for (int64_t b = 0; b < B; ++b) {
+      const int64_t i = n_lz == 1 ? 0 : b;
+      TransferEntry te;
+      TOP_TRY(transfer_tables(h, geo.Py, geo.Px, g->dy, g->dx, lam[i], stages[k].z, g->method, st, &te));
+      FieldSet fs{};
+      fs.hq = te.hq;
+      if (m && (m->flags & TOP_MOD_LENS)) {
+        TOP_TRY(lens_table(h, geo.nx, g->dx, lam[i], m->focal_length, &fs.src_lx));
+        TOP_TRY(lens_table(h, geo.ny, g->dy, lam[i], m->focal_length, &fs.src_ly));
+      }
+      fsets[k][b] = fs;
+    }
+  }
+  auto same = [](const FieldSet& a, const FieldSet& b) { return std::memcmp(&a, &b, sizeof(FieldSet)) == 0; };
+
+  // stage boundaries that fuse: the next source's planes fit and are 16-byte rows
+  EngineInfo ex;
+  find_engine(geo.Px / 2, &ex);
+  std::vector<char> fused(K, 0);  // fused[k]: stage k-1 -> k in one kernel
+  bool scratch = false;
+  for (int k = 1; k < K; ++k) {
+    PassParams probe{};
+    probe.nx = geo.nx;
+    probe.src_kind = SRC_FIELD;
+    probe.msrc = mod_dev(stages[k].pre, 0, nullptr);
+    const size_t planes = src_plane_floats(probe, ex.rows);
+    // the field rows sit past the two half rows, the planes past the rows and the row-pass region
+    const size_t rows_end = sizeof(float2) * (size_t(2) * ex.rows * ex.M + size_t(ex.rows) * geo.nx);
+    const size_t bytes = std::max(rows_end, ex.row_smem) + sizeof(float) * planes;
+    fused[k] = (planes == 0 || geo.nx % 4 == 0) && bytes <= kChainSmemMax;
+    if (!fused[k] && !stages[k - 1].keep) scratch = true;
+  }
+
+  const long long plane = (long long)geo.ny * geo.nx;
+  const int64_t align = std::lcm(inten ? group : int64_t(1), in_repeat);
+  if (align > kMaxFields) return fail(TOP_ERR_UNSUPPORTED, "intensity group larger than %d fields", kMaxFields);
+  const size_t ws_field = size_t(geo.Px) * size_t(geo.ny) * sizeof(float2);
+  const size_t scr_field = scratch ? size_t(plane) * sizeof(float2) : 0;
+  int64_t chunk = std::min<int64_t>(B, kMaxFields);
+  chunk = std::max<int64_t>(align, chunk - chunk % align);
+  auto need = [&](int64_t c) { return size_t(c) * (ws_field + scr_field) + 256; };
+  while (chunk > align && need(chunk) > h->ws_limit) chunk = std::max<int64_t>(align, (chunk / 2) - (chunk / 2) % align);
+  if (need(chunk) > h->ws_limit)
+    return fail(TOP_ERR_OOM, "one group of fields needs %zu bytes of workspace, above the limit %llu", need(chunk),
+                (unsigned long long)h->ws_limit);
+  TOP_TRY(ensure_workspace(h, need(chunk)));
+  float2* ws = static_cast<float2*>(h->ws);
+  float2* scr = scratch ? ws + size_t(chunk) * size_t(geo.Px) * size_t(geo.ny) : nullptr;
+
+  PassParams base{};
+  base.ny = geo.ny;
+  base.nx = geo.nx;
+  base.Py = geo.Py;
+  base.Px = geo.Px;
+  base.My = geo.Py / 2;
+  base.Mx = geo.Px / 2;
+  base.oy = geo.oy;
+  base.ox = geo.ox;
+  base.method = g->method;
+  base.src_kind = SRC_FIELD;
+  base.epi_kind = EPI_FIELD;
+  base.twx = twx;
+  base.twy = twy;
+  base.wpx = wpx;
+  base.wpy = wpy;
+  base.ws = ws;
+  base.ws_stride = (long long)geo.Px * geo.ny;
+  base.in_stride = plane;
+  base.out_stride = plane;
+  base.psi_stride = plane;
+  base.xs_stride = plane;
+  base.gI_stride = plane;
+  base.outf_stride = plane;
+  base.part_stride = plane;
+  base.group = 1;
+  base.src_group = 1;
+  base.in_repeat = 1;
+
+  std::vector<PassParams> ps(K, base);
+  int64_t pos = 0;
+  while (pos < B) {
+    // grow the chunk by aligned groups while the distinct parameter sets fit
+    int64_t n = 0;
+    std::vector<int64_t> rep;  // a field of each chunk-local set
+    unsigned char set_of[kMaxFields];
+    while (pos + n < B && n < chunk) {
+      const int64_t gend = std::min<int64_t>(B, pos + n + align);
+      std::vector<int64_t> rep2 = rep;
+      unsigned char idx[kMaxFields];
+      bool ok = true;
+      for (int64_t b = pos + n; b < gend; ++b) {
+        size_t k = 0;
+        while (k < rep2.size() && !same(fsets[0][rep2[k]], fsets[0][b])) ++k;
+        if (k == rep2.size()) {
+          if ((int)rep2.size() == kMaxSets) { ok = false; break; }
+          rep2.push_back(b);
+        }
+        idx[b - pos - n] = (unsigned char)k;
+      }
+      if (!ok) break;
+      rep = rep2;
+      std::memcpy(set_of + n, idx, size_t(gend - pos - n));
+      n = gend - pos;
+    }
+    if (n == 0) return fail(TOP_ERR_UNSUPPORTED, "a group of fields uses more than %d (lambda, z) sets", kMaxSets);
+    for (int k = 0; k < K; ++k) {
+      PassParams& p = ps[k];
+      p.nfields = int(n);
+      p.nsets = int(rep.size());
+      for (size_t q = 0; q < rep.size(); ++q) p.sets[q] = fsets[k][rep[q]];
+      std::memcpy(p.set_of, set_of, size_t(n));
+      p.msrc = offset_mod(mod_dev(stages[k].pre, 0, circ[k]), pos);
+      p.in = nullptr;
+      p.in_repeat = 1;
+      p.out = stages[k].keep ? static_cast<float2*>(stages[k].keep) + pos * plane : nullptr;
+      p.epi_kind = EPI_FIELD;
+      p.group = 1;
+      p.outf = nullptr;
+    }
+    ps[0].in = static_cast<const float2*>(in) + (pos / in_repeat) * plane;
+    ps[0].in_repeat = int(in_repeat);
+    PassParams& last = ps[K - 1];
+    last.out = out ? static_cast<float2*>(out) + pos * plane : nullptr;
+    if (inten) {
+      last.epi_kind = EPI_INTENSITY;
+      last.group = int(group);
+      last.outf = inten + (pos / group) * plane;
+    }
+    TOP_TRY(timed(h, KK_ROWS_FWD, st, "rows forward pass", [&] { return launch_pass(PASS_ROWS_FWD, geo.Px / 2, ps[0], st); }));
+    TOP_TRY(timed(h, KK_COLS, st, "column pass", [&] { return launch_pass(PASS_COLS, geo.Py / 2, ps[0], st); }));
+    for (int k = 1; k < K; ++k) {
+      if (fused[k]) {
+        TOP_TRY(timed(h, KK_ROWS_INV, st, "fused row pass",
+                      [&] { return launch_pass(PASS_ROWS_CHAIN, geo.Px / 2, ps[k - 1], st, &ps[k]); }));
+      } else {
+        // two launches through the kept field or the scratch
+        PassParams pa = ps[k - 1], pb = ps[k];
+        if (!pa.out) pa.out = scr;
+        pb.in = pa.out;
+        TOP_TRY(timed(h, KK_ROWS_INV, st, "rows inverse pass", [&] { return launch_pass(PASS_ROWS_INV, geo.Px / 2, pa, st); }));
+        TOP_TRY(timed(h, KK_ROWS_FWD, st, "rows forward pass", [&] { return launch_pass(PASS_ROWS_FWD, geo.Px / 2, pb, st); }));
+      }
+      TOP_TRY(timed(h, KK_COLS, st, "column pass", [&] { return launch_pass(PASS_COLS, geo.Py / 2, ps[k], st); }));
+    }
+    TOP_TRY(timed(h, KK_ROWS_INV, st, "rows inverse pass", [&] { return launch_pass(PASS_ROWS_INV, geo.Px / 2, last, st); }));
+    pos += n;
+  }
+  return TOP_OK;
+}
+
 }  // namespace
 
 // ============================================================================= C ABI
@@ -754,6 +953,13 @@ top_status top_propagate(top_handle h, const top_grid* g, const void* in, void* 
   q.msrc = pre; q.msrc_conj = 0;
   q.epi_kind = EPI_FIELD; q.out = out; q.mepi = post; q.mepi_conj = 0;
   return run_propagation(h, q, static_cast<cudaStream_t>(stream));
+}
+
+top_status top_fused_chain(top_handle h, const top_grid* g, const void* in, void* out, float* intensity,
+                           int64_t group, const double* lambda, int64_t n_lz, const top_stage* stages, int nstages,
+                           void* stream) {
+  if (!h) return fail(TOP_ERR_INVALID_ARG, "handle is NULL");
+  return run_chain(h, g, in, out, intensity, group, lambda, n_lz, stages, nstages, static_cast<cudaStream_t>(stream));
 }
 
 top_status top_propagate_backward(top_handle h, const top_grid* g, const void* grad_out, void* grad_in,

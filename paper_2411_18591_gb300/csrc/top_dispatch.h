@@ -14,13 +14,18 @@ struct EngineInfo {
   int NS;     // number of radix stages
   int R[4];   // radices
   int tw_size;
+  int rows;         // rows per block of the row passes
+  size_t row_smem;  // shared memory of a row block before any staged planes
 };
 
-enum PassKind : int { PASS_ROWS_FWD = 0, PASS_COLS = 1, PASS_ROWS_INV = 2 };
+// PASS_ROWS_CHAIN: the inverse row pass of one propagation fused with the forward row pass of
+// the next (the second parameter block).
+enum PassKind : int { PASS_ROWS_FWD = 0, PASS_COLS = 1, PASS_ROWS_INV = 2, PASS_ROWS_CHAIN = 3 };
 
 #define TOP_DECLARE_UNIT(name)                                                                        \
   bool engine_info_##name(int M, EngineInfo* info);                                                   \
-  cudaError_t launch_pass_##name(int kind, int M, const PassParams& p, cudaStream_t s, bool* found);
+  cudaError_t launch_pass_##name(int kind, int M, const PassParams& p, const PassParams* next, cudaStream_t s, \
+                                 bool* found);
 
 TOP_DECLARE_UNIT(small)
 TOP_DECLARE_UNIT(mid)

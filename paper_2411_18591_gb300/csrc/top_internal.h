@@ -94,6 +94,21 @@ struct PassParams {
 };
 
 // Kernel launch timing kinds (instrumentation)
+// Floats per R1 block of the planes staged besides the field rows: the intensity gradient
+// (SRC_INTENSITY) and the phase, amplitude and complex mask of the source modulation.
+__host__ __device__ inline size_t src_plane_floats(const PassParams& p, int rows) {
+  const size_t plane = size_t(rows) * size_t(p.nx);
+  size_t n = 0;
+  if (p.src_kind == SRC_INTENSITY) n += plane;
+  if (p.msrc.flags & TOP_MOD_PHASE) n += plane;
+  if (p.msrc.flags & TOP_MOD_AMPLITUDE) n += plane;
+  if (p.msrc.flags & TOP_MOD_COMPLEX) n += 2 * plane;
+  return n;
+}
+
+// Largest dynamic shared memory of a fused chain block (R2 of one propagation + R1 of the next).
+constexpr size_t kChainSmemMax = 227 * 1024;
+
 enum KernelKind : int { KK_ROWS_FWD = 0, KK_COLS, KK_ROWS_INV, KK_AUX, KK_COUNT };
 
 }  // namespace top

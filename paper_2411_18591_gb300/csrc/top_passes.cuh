@@ -192,18 +192,6 @@ __device__ __forceinline__ float2 load_src(const PassParams& p, const FieldSet& 
   return s;
 }
 
-// Floats per R1 block of the planes staged besides the field rows: the intensity gradient
-// (SRC_INTENSITY) and the phase, amplitude and complex mask of the source modulation.
-__host__ __device__ inline size_t src_plane_floats(const PassParams& p, int rows) {
-  const size_t plane = size_t(rows) * size_t(p.nx);
-  size_t n = 0;
-  if (p.src_kind == SRC_INTENSITY) n += plane;
-  if (p.msrc.flags & TOP_MOD_PHASE) n += plane;
-  if (p.msrc.flags & TOP_MOD_AMPLITUDE) n += plane;
-  if (p.msrc.flags & TOP_MOD_COMPLEX) n += 2 * plane;
-  return n;
-}
-
 // Whether R1 copies its source rows (and planes) into shared memory with asynchronous 16-byte
 // copies: every row start must be 16-byte aligned and the planes must fit.
 template <class EN>
@@ -250,96 +238,90 @@ __device__ __forceinline__ void fold(float2 (&v)[EN::E], const float2* line, int
 
 // ----------------------------------------------------------------------------- R1
 
-template <class EX, bool X2>
-__global__ void __launch_bounds__(RowShape<EX>::THREADS) k_rows_fwd(const __grid_constant__ PassParams p) {
-  using SH = RowShape<EX>;
-  constexpr int G = EX::G, E = EX::E, M = EX::M, ROWS = SH::ROWS, LD = SH::LD, NT = SH::THREADS;
-  TOP_DYN_SMEM(float2, smem);
-  int grp, t;
-  group_lane<G>(threadIdx.x, grp, t);
-  const int row = grp >> 1, r = grp & 1;  // two groups per row: the even and odd halves
-  const int y0 = blockIdx.x * ROWS;
-  const int nrows = min(ROWS, p.ny - y0);
-  const int f = blockIdx.y;
-  const FieldSet& fs = p.sets[p.set_of[f]];
-  const int nx = p.nx, ny = p.ny;
+// Planes of an R1 source staged in shared memory (null when not needed).
+struct SrcPlanes {
+  const float* gi;
+  const float* ph;
+  const float* am;
+  const float2* cm;
+};
 
-  // (A) modulated input rows -> shared [ROWS][nx]
-  if (src_staged<EX>(p)) {
-    // the field rows and the planes the source needs, each one contiguous block copied as
-    // 16-byte pieces, then the source arithmetic in place
-    const bool inten = p.src_kind == SRC_INTENSITY;
-    const ModDev& m = p.msrc;
-    const long long row0 = (long long)y0 * nx;
-    const float2* src = inten ? p.psi + (long long)f * p.psi_stride + row0
-                              : p.in + (long long)(f / p.in_repeat) * p.in_stride + row0;
-    {
-      const float4* s4 = reinterpret_cast<const float4*>(src);
-      float4* d4 = reinterpret_cast<float4*>(smem);
-      const int n4 = nrows * nx / 2, all4 = ROWS * nx / 2;
-      for (int i = threadIdx.x; i < all4; i += NT) {
-        if (i < n4) top_cp_async16(d4 + i, s4 + i);
-        else d4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+// Issue the 16-byte async copies of the planes the source of field f needs (rows y0 .. y0 +
+// nrows - 1) into `planes` (src_plane_floats(p, ROWS) floats).
+template <class EX>
+__device__ __forceinline__ SrcPlanes stage_src_planes(const PassParams& p, int f, int y0, int nrows, float* planes) {
+  using SH = RowShape<EX>;
+  constexpr int ROWS = SH::ROWS, NT = SH::THREADS;
+  const int nx = p.nx, plane = ROWS * nx;
+  const ModDev& m = p.msrc;
+  const long long row0 = (long long)y0 * nx;
+  auto stage = [&](const float* from, int floats_per_sample) {
+    float* dst = planes;
+    planes += plane * floats_per_sample;
+    const float4* s4 = reinterpret_cast<const float4*>(from);
+    float4* d4 = reinterpret_cast<float4*>(dst);
+    const int n4 = nrows * nx * floats_per_sample / 4;
+    for (int i = threadIdx.x; i < n4; i += NT) top_cp_async16(d4 + i, s4 + i);
+    return dst;
+  };
+  const long long midx = (long long)f * m.stride + row0;
+  SrcPlanes sp{};
+  if (p.src_kind == SRC_INTENSITY) sp.gi = stage(p.gI + (long long)(f / p.src_group) * p.gI_stride + row0, 1);
+  if (m.flags & TOP_MOD_PHASE) sp.ph = stage(m.phase + midx, 1);
+  if (m.flags & TOP_MOD_AMPLITUDE) sp.am = stage(m.amp + midx, 1);
+  if (m.flags & TOP_MOD_COMPLEX)
+    sp.cm = reinterpret_cast<const float2*>(stage(reinterpret_cast<const float*>(m.cmask + midx), 2));
+  return sp;
+}
+
+// The source arithmetic in place on rows [ROWS][nx] of shared memory: 2 w g_I psi for the
+// intensity backward, times the source modulation M (Eq. 1).
+template <class EX>
+__device__ __forceinline__ void modulate_src_rows(const PassParams& p, const FieldSet& fs, int f, int y0, int nrows,
+                                                  float2* rows, const SrcPlanes& sp) {
+  constexpr int NT = RowShape<EX>::THREADS;
+  const int nx = p.nx;
+  const ModDev& m = p.msrc;
+  const bool inten = p.src_kind == SRC_INTENSITY;
+  const float w2 = inten ? 2.f * (p.weights ? __ldg(p.weights + f) : 1.f) : 1.f;
+  for (int rr = 0; rr < nrows; ++rr) {
+    const int y = y0 + rr;
+    const int2 rg = (m.flags & TOP_MOD_CIRC) ? __ldg(m.circ + y) : make_int2(0, nx - 1);
+    const float2 ly = (m.flags & TOP_MOD_LENS) ? ldg2(fs.src_ly + y) : make_float2(1.f, 0.f);
+    for (int x = threadIdx.x; x < nx; x += NT) {
+      const int i = rr * nx + x;
+      float2 s = rows[i];
+      if (inten) s = c_scale(s, w2 * sp.gi[i]);
+      if (m.flags) {
+        float2 mv = make_float2(1.f, 0.f);
+        if (m.flags & TOP_MOD_COMPLEX) mv = sp.cm[i];
+        if (m.flags & TOP_MOD_AMPLITUDE) mv = c_scale(mv, sp.am[i]);
+        if (m.flags & TOP_MOD_PHASE) mv = c_mul(mv, cis(sp.ph[i]));
+        if (m.flags & TOP_MOD_LENS) mv = c_mul(mv, c_mul(ldg2(fs.src_lx + x), ly));
+        if (x < rg.x || x > rg.y) mv = make_float2(0.f, 0.f);
+        s = c_mul(s, m.conj ? c_conj(mv) : mv);
       }
-    }
-    float* planes = reinterpret_cast<float*>(smem + SH::SMEM / sizeof(float2));
-    const int plane = ROWS * nx;
-    auto stage = [&](const float* from, int floats_per_sample) {
-      float* dst = planes;
-      planes += plane * floats_per_sample;
-      const float4* s4 = reinterpret_cast<const float4*>(from);
-      float4* d4 = reinterpret_cast<float4*>(dst);
-      const int n4 = nrows * nx * floats_per_sample / 4;
-      for (int i = threadIdx.x; i < n4; i += NT) top_cp_async16(d4 + i, s4 + i);
-      return dst;
-    };
-    const long long midx = (long long)f * m.stride + row0;
-    const float* gi = inten ? stage(p.gI + (long long)(f / p.src_group) * p.gI_stride + row0, 1) : nullptr;
-    const float* ph = (m.flags & TOP_MOD_PHASE) ? stage(m.phase + midx, 1) : nullptr;
-    const float* am = (m.flags & TOP_MOD_AMPLITUDE) ? stage(m.amp + midx, 1) : nullptr;
-    const float2* cm = (m.flags & TOP_MOD_COMPLEX)
-                           ? reinterpret_cast<const float2*>(stage(reinterpret_cast<const float*>(m.cmask + midx), 2))
-                           : nullptr;
-    top_cp_async_wait_all();
-    if (inten || m.flags) {
-      __syncthreads();
-      const float w2 = inten ? 2.f * (p.weights ? __ldg(p.weights + f) : 1.f) : 1.f;
-      for (int rr = 0; rr < nrows; ++rr) {
-        const int y = y0 + rr;
-        const int2 rg = (m.flags & TOP_MOD_CIRC) ? __ldg(m.circ + y) : make_int2(0, nx - 1);
-        const float2 ly = (m.flags & TOP_MOD_LENS) ? ldg2(fs.src_ly + y) : make_float2(1.f, 0.f);
-        for (int x = threadIdx.x; x < nx; x += NT) {
-          const int i = rr * nx + x;
-          float2 s = smem[i];
-          if (inten) s = c_scale(s, w2 * gi[i]);
-          if (m.flags) {
-            float2 mv = make_float2(1.f, 0.f);
-            if (m.flags & TOP_MOD_COMPLEX) mv = cm[i];
-            if (m.flags & TOP_MOD_AMPLITUDE) mv = c_scale(mv, am[i]);
-            if (m.flags & TOP_MOD_PHASE) mv = c_mul(mv, cis(ph[i]));
-            if (m.flags & TOP_MOD_LENS) mv = c_mul(mv, c_mul(ldg2(fs.src_lx + x), ly));
-            if (x < rg.x || x > rg.y) mv = make_float2(0.f, 0.f);
-            s = c_mul(s, m.conj ? c_conj(mv) : mv);
-          }
-          smem[i] = s;
-        }
-      }
-    }
-  } else {
-#pragma unroll 2
-    for (int rr = 0; rr < ROWS; ++rr) {
-      for (int x = threadIdx.x; x < nx; x += NT)
-        smem[rr * nx + x] = rr < nrows ? load_src(p, fs, f, y0 + rr, x) : make_float2(0.f, 0.f);
+      rows[i] = s;
     }
   }
-  __syncthreads();
+}
+
+// Fold, forward-transform and store the bins of rows [ROWS][nx] (shared memory; they may alias
+// the exchange buffers at `smem`, which are written only after a block barrier).
+template <class EX, bool X2>
+__device__ __forceinline__ void forward_rows(const PassParams& p, int f, int y0, int nrows, const float2* rows,
+                                             float2* smem, int grp, int t) {
+  using SH = RowShape<EX>;
+  constexpr int E = EX::E, M = EX::M, ROWS = SH::ROWS, LD = SH::LD, NT = SH::THREADS;
+  const int row = grp >> 1, r = grp & 1;
+  const int nx = p.nx, ny = p.ny;
   float2 v[E];
-  fold<EX, X2, 1>(v, smem + row * nx, nx, p.ox, r, p.wpx, t);
-  __syncthreads();  // the rows alias the exchange buffers
+  fold<EX, X2, 1>(v, rows + row * nx, nx, p.ox, r, p.wpx, t);
+  __syncthreads();  // the rows may alias the exchange buffers
   EX::fwd(v, smem + grp * EX::BUF, t, p.twx);
   float2* ws = p.ws + (long long)f * p.ws_stride;
   if constexpr (SH::DIRECT) {
-    // (B) bins straight to the workspace: four consecutive lanes fill one 32-byte sector
+    // bins straight to the workspace: four consecutive lanes fill one 32-byte sector
     if (row < nrows) {
 #pragma unroll
       for (int e = 0; e < E; ++e) ws[ws_index(r * M + EX::bin(t, e), y0 + row, ny)] = v[e];
@@ -349,13 +331,58 @@ __global__ void __launch_bounds__(RowShape<EX>::THREADS) k_rows_fwd(const __grid
 #pragma unroll
     for (int e = 0; e < E; ++e) smem[(r * M + EX::bin(t, e)) * LD + row] = v[e];
     __syncthreads();
-    // (B) the tile, ROWS rows x 4 lines per block, to the workspace in address order
+    // the tile, ROWS rows x 4 lines per block, to the workspace in address order
     for (int i = threadIdx.x; i < 2 * M * ROWS; i += NT) {
       const int c = i & 3, q = i >> 2;
       const int yo = q % ROWS, blk = q / ROWS;
       if (yo < nrows) ws[((long long)blk * ny + y0 + yo) * 4 + c] = smem[(4 * blk + c) * LD + yo];
     }
   }
+}
+
+template <class EX, bool X2>
+__global__ void __launch_bounds__(RowShape<EX>::THREADS) k_rows_fwd(const __grid_constant__ PassParams p) {
+  using SH = RowShape<EX>;
+  constexpr int ROWS = SH::ROWS, NT = SH::THREADS;
+  TOP_DYN_SMEM(float2, smem);
+  int grp, t;
+  group_lane<EX::G>(threadIdx.x, grp, t);
+  const int y0 = blockIdx.x * ROWS;
+  const int nrows = min(ROWS, p.ny - y0);
+  const int f = blockIdx.y;
+  const FieldSet& fs = p.sets[p.set_of[f]];
+  const int nx = p.nx;
+
+  // modulated input rows -> shared [ROWS][nx]
+  if (src_staged<EX>(p)) {
+    // the field rows and the planes the source needs, each one contiguous block copied as
+    // 16-byte pieces, then the source arithmetic in place
+    const bool inten = p.src_kind == SRC_INTENSITY;
+    const long long row0 = (long long)y0 * nx;
+    const float2* src = inten ? p.psi + (long long)f * p.psi_stride + row0
+                              : p.in + (long long)(f / p.in_repeat) * p.in_stride + row0;
+    const float4* s4 = reinterpret_cast<const float4*>(src);
+    float4* d4 = reinterpret_cast<float4*>(smem);
+    const int n4 = nrows * nx / 2, all4 = ROWS * nx / 2;
+    for (int i = threadIdx.x; i < all4; i += NT) {
+      if (i < n4) top_cp_async16(d4 + i, s4 + i);
+      else d4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    const SrcPlanes sp = stage_src_planes<EX>(p, f, y0, nrows, reinterpret_cast<float*>(smem + SH::SMEM / sizeof(float2)));
+    top_cp_async_wait_all();
+    if (inten || p.msrc.flags) {
+      __syncthreads();
+      modulate_src_rows<EX>(p, fs, f, y0, nrows, smem, sp);
+    }
+  } else {
+#pragma unroll 2
+    for (int rr = 0; rr < ROWS; ++rr) {
+      for (int x = threadIdx.x; x < nx; x += NT)
+        smem[rr * nx + x] = rr < nrows ? load_src(p, fs, f, y0 + rr, x) : make_float2(0.f, 0.f);
+    }
+  }
+  __syncthreads();
+  forward_rows<EX, X2>(p, f, y0, nrows, smem, smem, grp, t);
 }
 
 // ----------------------------------------------------------------------------- C
@@ -684,6 +711,62 @@ __device__ __forceinline__ void combine_rows(const PassParams& p, const FieldSet
   }
 }
 
+// Load the bins of rows y0 .. y0 + nrows - 1 of field f, inverse-transform them and leave both
+// halves in natural order in shared memory [r][ROWS][M] at `smem`, the odd one times
+// exp(2 pi i pos / P). Ends before the barrier that makes the halves visible.
+template <class EX, bool X2>
+__device__ __forceinline__ void inverse_rows(const PassParams& p, int f, int y0, int nrows, float2* smem, int grp,
+                                             int t) {
+  using SH = RowShape<EX>;
+  constexpr int E = EX::E, M = EX::M, ROWS = SH::ROWS, LD = SH::LD, NT = SH::THREADS;
+  const int row = grp >> 1, r = grp & 1;
+  const int ny = p.ny;
+  const float2* ws = p.ws + (long long)f * p.ws_stride;
+  float2 v[E];
+  if constexpr (SH::DIRECT) {
+    // bins straight from the workspace: four consecutive lanes read one 32-byte sector
+    const bool valid = row < nrows;
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+      v[e] = valid ? ws[ws_index(r * M + EX::bin(t, e), y0 + row, ny)] : make_float2(0.f, 0.f);
+  } else {
+    // the tile [2M][LD] from the workspace in address order (ROWS rows x 4 lines per block)
+    for (int i = threadIdx.x; i < 2 * M * ROWS; i += NT) {
+      const int c = i & 3, q = i >> 2;
+      const int yo = q % ROWS, blk = q / ROWS;
+      smem[(4 * blk + c) * LD + yo] = yo < nrows ? ws[((long long)blk * ny + y0 + yo) * 4 + c] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < E; ++e) v[e] = smem[(r * M + EX::bin(t, e)) * LD + row];
+    __syncthreads();  // the tile aliases the exchange buffers
+  }
+  EX::inv(v, smem + grp * EX::BUF, t, p.twx);
+  __syncthreads();  // the exchange buffers alias the half-row buffers
+  // both halves in natural order -> shared [r][ROWS][M], the odd one times exp(2 pi i pos / P)
+  float2* hrow = smem + (r * ROWS + row) * M;
+  if (r) {
+    if constexpr (X2) {
+      const float2 wt = ldg2(p.wpx + t);
+      for_slots(
+          [&](auto ec) {
+            constexpr int e = decltype(ec)::value;
+            hrow[EX::in_pos(t, e)] = c_mulc(v[e], slot_split_twiddle<EX, e>(wt));
+          },
+          std::make_integer_sequence<int, E>{});
+    } else {
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int pos = EX::in_pos(t, e);
+        hrow[pos] = c_mulc(v[e], ldg2(p.wpx + pos));
+      }
+    }
+  } else {
+#pragma unroll
+    for (int e = 0; e < E; ++e) hrow[EX::in_pos(t, e)] = v[e];
+  }
+}
+
 template <class EX, bool X2>
 __global__ void __launch_bounds__(RowShape<EX>::THREADS, RowShape<EX>::MINB_INV) k_rows_inv(const __grid_constant__ PassParams p) {
   using SH = RowShape<EX>;
@@ -771,49 +854,7 @@ __global__ void __launch_bounds__(RowShape<EX>::THREADS, RowShape<EX>::MINB_INV)
     const FieldSet& fs = p.sets[p.set_of[f]];
     const float2* ws = p.ws + (long long)f * p.ws_stride;
     if (staged) stage_field(f);
-    float2 v[E];
-    if constexpr (SH::DIRECT) {
-      // bins straight from the workspace: four consecutive lanes read one 32-byte sector
-      const bool valid = row < nrows;
-#pragma unroll
-      for (int e = 0; e < E; ++e)
-        v[e] = valid ? ws[ws_index(r * M + EX::bin(t, e), y0 + row, ny)] : make_float2(0.f, 0.f);
-    } else {
-      // the tile [2M][LD] from the workspace in address order (ROWS rows x 4 lines per block)
-      for (int i = threadIdx.x; i < 2 * M * ROWS; i += NT) {
-        const int c = i & 3, q = i >> 2;
-        const int yo = q % ROWS, blk = q / ROWS;
-        smem[(4 * blk + c) * LD + yo] = yo < nrows ? ws[((long long)blk * ny + y0 + yo) * 4 + c] : make_float2(0.f, 0.f);
-      }
-      __syncthreads();
-#pragma unroll
-      for (int e = 0; e < E; ++e) v[e] = smem[(r * M + EX::bin(t, e)) * LD + row];
-      __syncthreads();  // the tile aliases the exchange buffers
-    }
-    EX::inv(v, smem + grp * EX::BUF, t, p.twx);
-    __syncthreads();  // the exchange buffers alias the half-row buffers
-    // both halves in natural order -> shared [r][ROWS][M], the odd one times exp(2 pi i pos / P)
-    float2* hrow = smem + (r * ROWS + row) * M;
-    if (r) {
-      if constexpr (X2) {
-        const float2 wt = ldg2(p.wpx + t);
-        for_slots(
-            [&](auto ec) {
-              constexpr int e = decltype(ec)::value;
-              hrow[EX::in_pos(t, e)] = c_mulc(v[e], slot_split_twiddle<EX, e>(wt));
-            },
-            std::make_integer_sequence<int, E>{});
-      } else {
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-          const int pos = EX::in_pos(t, e);
-          hrow[pos] = c_mulc(v[e], ldg2(p.wpx + pos));
-        }
-      }
-    } else {
-#pragma unroll
-      for (int e = 0; e < E; ++e) hrow[EX::in_pos(t, e)] = v[e];
-    }
+    inverse_rows<EX, X2>(p, f, y0, nrows, smem, grp, t);
     if (staged) top_cp_async_wait_all();
     __syncthreads();
     // combine the halves over the cropped window, epilogue, coalesced store
@@ -841,6 +882,79 @@ __global__ void __launch_bounds__(RowShape<EX>::THREADS, RowShape<EX>::MINB_INV)
     if (ep.acc_am) copy_out(p.part_amp + pidx, ep.acc_am, 1);
     if (ep.acc_cm) copy_out(reinterpret_cast<float*>(p.part_mask + pidx), reinterpret_cast<const float*>(ep.acc_cm), 2);
   }
+}
+
+// ----------------------------------------------------------------------------- R2 + R1 fused
+
+// Shared memory of a fused chain block, in float2 units: the row-pass region, whose tail past
+// the two half rows [2][ROWS][M] also holds the field rows between the two propagations (they
+// are written after the exchanges of the inverse transform and read before those of the forward
+// one), then the next propagation's source planes, which arrive during the inverse transform.
+template <class EN>
+__host__ __device__ inline size_t chain_rows_off() {
+  return size_t(2) * RowShape<EN>::ROWS * EN::M;
+}
+template <class EN>
+__host__ __device__ inline size_t chain_planes_off(int nx) {
+  const size_t end_rows = chain_rows_off<EN>() + size_t(RowShape<EN>::ROWS) * nx;
+  const size_t region = RowShape<EN>::SMEM / sizeof(float2);
+  return end_rows > region ? end_rows : region;
+}
+template <class EN>
+__host__ __device__ inline size_t chain_smem(const PassParams& next) {
+  return sizeof(float2) * chain_planes_off<EN>(next.nx) + sizeof(float) * src_plane_floats(next, RowShape<EN>::ROWS);
+}
+
+// The inverse row pass of one propagation (pa) fused with the forward row pass of the next (pb)
+// in a system chain (Eq. 1 and Eq. 4 in turn): the field between them stays in shared memory
+// and reaches global memory only when it is kept (pa.out). pb's bins replace pa's in the
+// workspace, row tile by row tile, each block reading its tile before writing it.
+template <class EX, bool X2>
+__global__ void __launch_bounds__(RowShape<EX>::THREADS, RowShape<EX>::MINB_INV)
+    k_rows_chain(const __grid_constant__ PassParams pa, const __grid_constant__ PassParams pb) {
+  using SH = RowShape<EX>;
+  constexpr int M = EX::M, ROWS = SH::ROWS, NT = SH::THREADS;
+  TOP_DYN_SMEM(float2, smem);
+  int grp, t;
+  group_lane<EX::G>(threadIdx.x, grp, t);
+  const int y0 = blockIdx.x * ROWS;
+  const int nrows = min(ROWS, pa.ny - y0);
+  const int f = blockIdx.y;
+  const int nx = pa.nx;
+  float2* rows = smem + chain_rows_off<EX>();  // [ROWS][nx]
+  // the next propagation's modulation planes arrive while this one is finished
+  const SrcPlanes sp = stage_src_planes<EX>(pb, f, y0, nrows, reinterpret_cast<float*>(smem + chain_planes_off<EX>(nx)));
+  inverse_rows<EX, X2>(pa, f, y0, nrows, smem, grp, t);
+  __syncthreads();
+  for (int rr = 0; rr < ROWS; ++rr) {
+    for (int x = threadIdx.x; x < nx; x += NT) {
+      float2 val = make_float2(0.f, 0.f);
+      if (rr < nrows) {
+        int pos;
+        bool upper;
+        if constexpr (X2) {
+          upper = x >= M / 2;
+          pos = upper ? x - M / 2 : x + M / 2;
+        } else {
+          const int pp = x + pa.ox;
+          upper = pp >= M;
+          pos = upper ? pp - M : pp;
+        }
+        const float2 o = smem[(ROWS + rr) * M + pos];
+        const float2 ev = smem[rr * M + pos];
+        val = upper ? c_sub(ev, o) : c_add(ev, o);
+        if (pa.out) pa.out[(long long)f * pa.out_stride + (long long)(y0 + rr) * nx + x] = val;
+      }
+      rows[rr * nx + x] = val;
+    }
+  }
+  top_cp_async_wait_all();
+  __syncthreads();
+  if (pb.msrc.flags) {
+    modulate_src_rows<EX>(pb, pb.sets[pb.set_of[f]], f, y0, nrows, rows, sp);
+    __syncthreads();
+  }
+  forward_rows<EX, X2>(pb, f, y0, nrows, rows, smem, grp, t);
 }
 
 // ----------------------------------------------------------------------------- launchers
@@ -884,6 +998,18 @@ cudaError_t launch_rows_inv_t(const PassParams& p, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+template <class EX, bool X2>
+cudaError_t launch_rows_chain_t(const PassParams& pa, const PassParams& pb, cudaStream_t s) {
+  using SH = RowShape<EX>;
+  static const cudaError_t attr = set_smem(k_rows_chain<EX, X2>, kChainSmemMax);
+  if (attr != cudaSuccess) return attr;
+  const size_t bytes = chain_smem<EX>(pb);
+  if (bytes > kChainSmemMax) return cudaErrorInvalidValue;
+  dim3 grid((pa.ny + SH::ROWS - 1) / SH::ROWS, pa.nfields);
+  TOP_LAUNCH((k_rows_chain<EX, X2>), grid, SH::THREADS, bytes, s, pa, pb);
+  return cudaGetLastError();
+}
+
 // padding exactly 2 along an axis: n = M and the field sits at M/2
 inline bool exact2(int n, int M, int o) { return n == M && o == M / 2; }
 
@@ -895,6 +1021,11 @@ cudaError_t launch_rows_fwd(const PassParams& p, cudaStream_t s) {
 template <class EY>
 cudaError_t launch_cols(const PassParams& p, cudaStream_t s) {
   return exact2(p.ny, p.My, p.oy) ? launch_cols_t<EY, true>(p, s) : launch_cols_t<EY, false>(p, s);
+}
+
+template <class EX>
+cudaError_t launch_rows_chain(const PassParams& pa, const PassParams& pb, cudaStream_t s) {
+  return exact2(pa.nx, pa.Mx, pa.ox) ? launch_rows_chain_t<EX, true>(pa, pb, s) : launch_rows_chain_t<EX, false>(pa, pb, s);
 }
 
 template <class EX>

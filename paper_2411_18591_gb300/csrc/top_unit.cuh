@@ -13,12 +13,15 @@ inline void fill_engine_info(EngineInfo* info) {
   info->NS = EN::NS;
   for (int s = 0; s < 4; ++s) info->R[s] = s < EN::NS ? EN::radix(s) : 1;
   info->tw_size = EN::TW_SIZE;
+  info->rows = RowShape<EN>::ROWS;
+  info->row_smem = RowShape<EN>::SMEM;
 }
 
 template <class EN>
-inline cudaError_t launch_pass_of(int kind, const PassParams& p, cudaStream_t s) {
+inline cudaError_t launch_pass_of(int kind, const PassParams& p, const PassParams* next, cudaStream_t s) {
   if (kind == PASS_ROWS_FWD) return launch_rows_fwd<EN>(p, s);
   if (kind == PASS_COLS) return launch_cols<EN>(p, s);
+  if (kind == PASS_ROWS_CHAIN) return next ? launch_rows_chain<EN>(p, *next, s) : cudaErrorInvalidValue;
   return launch_rows_inv<EN>(p, s);
 }
 
@@ -31,14 +34,15 @@ inline cudaError_t launch_pass_of(int kind, const PassParams& p, cudaStream_t s)
 #define TOP_LAUNCH_CASE(EN) \
   case EN::M:               \
     *found = true;          \
-    return launch_pass_of<EN>(kind, p, s);
+    return launch_pass_of<EN>(kind, p, next, s);
 
 #define TOP_DEFINE_UNIT(name, LIST)                                                                 \
   namespace top {                                                                                   \
   bool engine_info_##name(int M, EngineInfo* info) {                                                \
     switch (M) { LIST(TOP_INFO_CASE) default: return false; }                                       \
   }                                                                                                 \
-  cudaError_t launch_pass_##name(int kind, int M, const PassParams& p, cudaStream_t s, bool* found) { \
+  cudaError_t launch_pass_##name(int kind, int M, const PassParams& p, const PassParams* next, cudaStream_t s, \
+                                 bool* found) {                                                     \
     *found = false;                                                                                 \
     switch (M) { LIST(TOP_LAUNCH_CASE) default: return cudaSuccess; }                               \
   }                                                                                                 \

@@ -3,9 +3,10 @@
 A sequence of library calls, no arithmetic of its own:
 
   F1  psi1 = lens1 * P_f(obj)               (object broadcast over the wavelengths, input_repeat)
-  F2  psi2 = P_f(psi1)                       (in place)
+  F2  psi2 = P_f(psi1)                       (kept for the pupil gradient)
   F3  psi3 = lens2 * P_f(pupil * psi2)       (pupil = circ(R) exp(i phi))
   F4  psi4 = P_f(psi3), I = sum over each object's component and wavelength fields of |psi4|^2 (Eq. 14)
+      (F1-F4 run as one fused chain: the row passes between consecutive propagations are one kernel)
   L   = mean((I - T)^2), dL/dI
   B4  g3 = P_f^H(2 dL/dI psi4)               (intensity backward)
   B3  dL/dphi = sum_b Im(g_y conj(pupil psi2)),  g_y = P_f^H(conj(lens2) g3)
@@ -74,28 +75,15 @@ class FourF:
         a, b = bufs["a"], bufs["b"]
         lens = self.lens()
         pupil = self.pupil(phase)
-        B.top_propagate(obj, d, d, lam, f, pad, m, post=lens, out=a, input_repeat=self.repeat)       # F1
-        B.top_propagate(a, d, d, lam, f, pad, m, out=a)                                               # F2 (psi2 in a)
-        B.top_propagate(a, d, d, lam, f, pad, m, pre=pupil, post=lens, out=b)                         # F3
-        inten, _ = _intensity_into(b, b, self, lam)                                                   # F4 (psi4 in b)
+        # F1-F4 as one fused chain: psi2 kept in a, psi4 and the grouped intensity out of the last stage
+        stages = [B.Stage(f), B.Stage(f, pre=lens, keep=a), B.Stage(f, pre=pupil), B.Stage(f, pre=lens)]
+        _, inten = B.top_fused_chain(obj, d, d, lam, stages, pad, m, out=b, intensity_group=self.group,
+                                     input_repeat=self.repeat)
         loss, g_i = B.top_mse_loss(inten, target)
         _intensity_backward_into(b, g_i, b, self, lam)                                                # B4 (g3 in b)
         B.top_propagate_backward(b, d, d, lam, f, pad, m, pre=pupil, post=lens, saved_in=a,
                                  want_grad_in=False, grad_phase=grad_phase)                           # B3
         return loss, inten
-
-
-def _intensity_into(field, out_field, sysm: FourF, lam):
-    import ctypes as C
-    from . import _lib
-    b, ny, nx = field.shape
-    inten = torch.empty((b // sysm.group, ny, nx), dtype=torch.float32, device=field.device)
-    lams, zs, n = B._lz(lam, sysm.f, b)
-    g = B.make_grid(b, ny, nx, sysm.d, sysm.d, sysm.pad, sysm.method)
-    _lib.check(_lib.load().top_propagate_intensity(B.handle(field.device), C.byref(g), field.data_ptr(),
-                                                   out_field.data_ptr(), inten.data_ptr(), sysm.group, None, lams,
-                                                   zs, n, None, None, B._stream(field)))
-    return inten, out_field
 
 
 def _intensity_backward_into(psi, g_i, grad_in, sysm: FourF, lam):
