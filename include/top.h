@@ -147,6 +147,16 @@ top_status top_propagate(top_handle h, const top_grid* g, const void* in, void* 
                          const double* lambda, const double* z, int64_t n_lz,
                          const top_mod* pre, const top_mod* post, void* stream);
 
+/* A ragged batch (fields of different sizes, spacings, wavelengths and distances, §5.3-style
+ * mixed workloads): field i has its own grid grids[i] (batch 1, input_repeat 0 or 1),
+ * wavelength lambda[i], distance z[i] and device buffers in[i] -> out[i] (complex64 [ny][nx],
+ * 16-byte aligned; in[i] == out[i] allowed). out[i] = P_z(in[i]) (Eq. 4), or the adjoint
+ * P_z^H when `backward` is non-zero. Fields with the same padded geometry and method share
+ * launches (per-field pointers replace the batch strides); grids, in, out, lambda, z are host
+ * arrays of `count` entries. Results equal top_propagate / top_propagate_backward per field. */
+top_status top_propagate_ragged(top_handle h, int count, const top_grid* grids, const void* const* in,
+                                void* const* out, const double* lambda, const double* z, int backward, void* stream);
+
 /* One stage of a system chain: the field entering the stage is multiplied by `pre` (Eq. 1;
  * NULL: none) and propagated by `z` (Eq. 4). `keep`, when non-NULL, receives the stage's output
  * field (complex64 [batch][ny][nx] device, caller-owned); the last stage's must be NULL. */

@@ -157,6 +157,38 @@ def top_propagate(field: torch.Tensor, dy: float, dx: float, lam, z, pad: float 
     return out
 
 
+def top_propagate_ragged(fields: Sequence[torch.Tensor], spacings, lams, zs, pad: float = 2.0, method="as",
+                         backward: bool = False, out: Optional[Sequence[torch.Tensor]] = None):
+    """Propagate (or back-propagate) fields of different sizes in one call: field i ([ny, nx]
+    complex64) with spacing spacings[i] (a number or a (dy, dx) pair), wavelength lams[i] and
+    distance zs[i]. Returns the output fields (``out`` if given)."""
+    n = len(fields)
+    if n == 0:
+        return []
+    if out is None:
+        out = [torch.empty_like(f) for f in fields]
+    if not (len(spacings) == len(lams) == len(zs) == len(out) == n):
+        raise ValueError("fields, spacings, lams, zs and out must have the same length")
+    grids = (TopGrid * n)()
+    ins = (C.c_void_p * n)()
+    outs = (C.c_void_p * n)()
+    for i, (f, o) in enumerate(zip(fields, out)):
+        _field(f, "field")
+        _field(o, "out")
+        if f.dim() != 2 or o.shape != f.shape:
+            raise ValueError("ragged fields are [ny, nx] and out[i] must match field i")
+        sp = spacings[i]
+        dy, dx = (sp, sp) if isinstance(sp, (int, float)) else sp
+        grids[i] = make_grid(1, f.shape[0], f.shape[1], dy, dx, pad, method)
+        ins[i] = f.data_ptr()
+        outs[i] = o.data_ptr()
+    dev = fields[0].device if n else torch.device("cuda", torch.cuda.current_device())
+    check(_lib.load().top_propagate_ragged(handle(dev), n, grids, ins, outs, doubles([float(v) for v in lams]),
+                                           doubles([float(v) for v in zs]), 1 if backward else 0,
+                                           C.c_void_p(torch.cuda.current_stream(dev).cuda_stream)))
+    return out
+
+
 @dataclass
 class Stage:
     """One stage of a system chain: multiply by ``pre`` (Eq. 1), then propagate by ``z`` (Eq. 4);

@@ -872,6 +872,137 @@ top_status run_chain(top_handle h, const top_grid* g, const void* in, void* out,
   return TOP_OK;
 }
 
+// ============================================================================= ragged batches
+
+// Fields of different sizes, spacings, wavelengths and distances, each with its own buffers.
+// Fields with the same padded geometry and method run together, per-field pointers replacing
+// the batch strides (device arrays in the workspace tail).
+top_status run_ragged(top_handle h, int count, const top_grid* grids, const void* const* in, void* const* out,
+                      const double* lam, const double* z, int backward, cudaStream_t st) {
+  if (count < 0) return fail(TOP_ERR_INVALID_ARG, "count must be >= 0");
+  if (count == 0) return TOP_OK;
+  if (!grids || !in || !out || !lam || !z) return fail(TOP_ERR_INVALID_ARG, "grids, in, out, lambda and z must not be NULL");
+  std::vector<Geometry> geos(count);
+  for (int i = 0; i < count; ++i) {
+    const top_grid* g = &grids[i];
+    TOP_TRY(check_grid(g, &geos[i]));
+    TOP_TRY(check_engines(geos[i]));
+    if (g->batch != 1) return fail(TOP_ERR_INVALID_ARG, "ragged field %d: batch must be 1 (got %lld)", i, (long long)g->batch);
+    if (g->input_repeat > 1) return fail(TOP_ERR_INVALID_ARG, "ragged field %d: input_repeat must be 0 or 1", i);
+    if (!(std::isfinite(lam[i]) && lam[i] > 0)) return fail(TOP_ERR_INVALID_ARG, "lambda[%d] must be finite and > 0", i);
+    if (!std::isfinite(z[i])) return fail(TOP_ERR_INVALID_ARG, "z[%d] must be finite", i);
+    TOP_TRY(check_ptr(in[i], "ragged input field"));
+    TOP_TRY(check_ptr(out[i], "ragged output field"));
+  }
+  TOP_TRY(bind(h));
+  // groups of one geometry and method, in first-appearance order
+  std::vector<std::vector<int>> groups;
+  std::vector<std::array<int, 5>> keys;
+  for (int i = 0; i < count; ++i) {
+    const Geometry& q = geos[i];
+    const std::array<int, 5> key = {q.ny, q.nx, q.Py, q.Px, grids[i].method};
+    size_t k = 0;
+    while (k < keys.size() && keys[k] != key) ++k;
+    if (k == keys.size()) {
+      keys.push_back(key);
+      groups.emplace_back();
+    }
+    groups[k].push_back(i);
+  }
+  for (const auto& grp : groups) {
+    const Geometry geo = geos[grp[0]];
+    const int method = grids[grp[0]].method;
+    const long long plane = (long long)geo.ny * geo.nx;
+    const float2 *twx, *twy, *wpx, *wpy;
+    TOP_TRY(engine_twiddles(h, geo.Px / 2, &twx));
+    TOP_TRY(engine_twiddles(h, geo.Py / 2, &twy));
+    TOP_TRY(split_twiddles(h, geo.Px, &wpx));
+    TOP_TRY(split_twiddles(h, geo.Py, &wpy));
+    const int64_t nf = int64_t(grp.size());
+    std::vector<FieldSet> fsets(nf);
+    for (int64_t j = 0; j < nf; ++j) {
+      const int i = grp[j];
+      TransferEntry te;
+      TOP_TRY(transfer_tables(h, geo.Py, geo.Px, grids[i].dy, grids[i].dx, lam[i], z[i], method, st, &te));
+      fsets[j] = FieldSet{};
+      fsets[j].hq = te.hq;
+    }
+    const size_t ws_field = size_t(geo.Px) * size_t(geo.ny) * sizeof(float2);
+    const size_t ptr_field = 2 * sizeof(void*);
+    int64_t chunk = std::min<int64_t>(nf, kMaxFields);
+    auto need = [&](int64_t c) { return size_t(c) * ws_field + 256 + size_t(c) * ptr_field; };
+    while (chunk > 1 && need(chunk) > h->ws_limit) chunk /= 2;
+    if (need(chunk) > h->ws_limit)
+      return fail(TOP_ERR_OOM, "one field needs %zu bytes of workspace, above the limit %llu", need(chunk),
+                  (unsigned long long)h->ws_limit);
+    TOP_TRY(ensure_workspace(h, need(chunk)));
+    float2* ws = static_cast<float2*>(h->ws);
+    char* tail = reinterpret_cast<char*>(h->ws) + size_t(chunk) * ws_field;
+    tail = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(tail) + 255) & ~uintptr_t(255));
+    const float2** d_in = reinterpret_cast<const float2**>(tail);
+    float2** d_out = reinterpret_cast<float2**>(tail + size_t(chunk) * sizeof(void*));
+
+    PassParams p{};
+    p.ny = geo.ny;
+    p.nx = geo.nx;
+    p.Py = geo.Py;
+    p.Px = geo.Px;
+    p.My = geo.Py / 2;
+    p.Mx = geo.Px / 2;
+    p.oy = geo.oy;
+    p.ox = geo.ox;
+    p.method = method;
+    p.adjoint = backward ? 1 : 0;
+    p.src_kind = SRC_FIELD;
+    p.epi_kind = EPI_FIELD;
+    p.twx = twx;
+    p.twy = twy;
+    p.wpx = wpx;
+    p.wpy = wpy;
+    p.ws = ws;
+    p.ws_stride = (long long)geo.Px * geo.ny;
+    p.in_stride = plane;
+    p.out_stride = plane;
+    p.group = 1;
+    p.src_group = 1;
+    p.in_repeat = 1;
+    p.in_list = d_in;
+    p.out_list = d_out;
+    auto same = [](const FieldSet& a, const FieldSet& b) { return std::memcmp(&a, &b, sizeof(FieldSet)) == 0; };
+    std::vector<const void*> ptrs(2 * size_t(chunk));
+    int64_t pos = 0;
+    while (pos < nf) {
+      int64_t n = 0;
+      p.nsets = 0;
+      while (pos + n < nf && n < chunk) {
+        int k = 0;
+        while (k < p.nsets && !same(p.sets[k], fsets[pos + n])) ++k;
+        if (k == p.nsets) {
+          if (p.nsets == kMaxSets) break;
+          p.sets[p.nsets++] = fsets[pos + n];
+        }
+        p.set_of[n] = (unsigned char)k;
+        ++n;
+      }
+      for (int64_t j = 0; j < n; ++j) {
+        ptrs[j] = in[grp[pos + j]];
+        ptrs[size_t(chunk) + j] = out[grp[pos + j]];
+      }
+      // the pointer arrays are rewritten in stream order after the previous chunk's kernels
+      TOP_CUDA(cudaMemcpyAsync(d_in, ptrs.data(), size_t(n) * sizeof(void*), cudaMemcpyHostToDevice, st),
+               "cudaMemcpyAsync(ragged input pointers)");
+      TOP_CUDA(cudaMemcpyAsync(d_out, ptrs.data() + chunk, size_t(n) * sizeof(void*), cudaMemcpyHostToDevice, st),
+               "cudaMemcpyAsync(ragged output pointers)");
+      p.nfields = int(n);
+      TOP_TRY(timed(h, KK_ROWS_FWD, st, "rows forward pass", [&] { return launch_pass(PASS_ROWS_FWD, p.Mx, p, st); }));
+      TOP_TRY(timed(h, KK_COLS, st, "column pass", [&] { return launch_pass(PASS_COLS, p.My, p, st); }));
+      TOP_TRY(timed(h, KK_ROWS_INV, st, "rows inverse pass", [&] { return launch_pass(PASS_ROWS_INV, p.Mx, p, st); }));
+      pos += n;
+    }
+  }
+  return TOP_OK;
+}
+
 }  // namespace
 
 // ============================================================================= C ABI
@@ -953,6 +1084,12 @@ top_status top_propagate(top_handle h, const top_grid* g, const void* in, void* 
   q.msrc = pre; q.msrc_conj = 0;
   q.epi_kind = EPI_FIELD; q.out = out; q.mepi = post; q.mepi_conj = 0;
   return run_propagation(h, q, static_cast<cudaStream_t>(stream));
+}
+
+top_status top_propagate_ragged(top_handle h, int count, const top_grid* grids, const void* const* in,
+                                void* const* out, const double* lambda, const double* z, int backward, void* stream) {
+  if (!h) return fail(TOP_ERR_INVALID_ARG, "handle is NULL");
+  return run_ragged(h, count, grids, in, out, lambda, z, backward, static_cast<cudaStream_t>(stream));
 }
 
 top_status top_fused_chain(top_handle h, const top_grid* g, const void* in, void* out, float* intensity,

@@ -69,6 +69,10 @@ struct PassParams {
 
   // buffers (element strides per field)
   const float2* in;   long long in_stride;
+  // ragged batches: per-field device pointers (device arrays of nfields entries) that replace
+  // in + f * in_stride and out + f * out_stride when non-null
+  const float2* const* in_list;
+  float2* const* out_list;
   float2* ws;         long long ws_stride;   // pass workspace [field][Px][ny]
   float2* out;        long long out_stride;
   float* outf;        long long outf_stride; // intensity output per group / partial sums per group

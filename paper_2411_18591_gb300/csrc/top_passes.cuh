@@ -178,11 +178,19 @@ __device__ __forceinline__ float2 mod_value(const ModDev& m, uint32_t flags, int
   return conj ? c_conj(r) : r;
 }
 
+// Source field f of R1 and output field f of R2 (per-field pointers for ragged batches).
+__device__ __forceinline__ const float2* field_in(const PassParams& p, int f) {
+  return p.in_list ? p.in_list[f] : p.in + (long long)(f / p.in_repeat) * p.in_stride;
+}
+__device__ __forceinline__ float2* field_out(const PassParams& p, int f) {
+  return p.out_list ? p.out_list[f] : p.out + (long long)f * p.out_stride;
+}
+
 __device__ __forceinline__ float2 load_src(const PassParams& p, const FieldSet& fs, int f, int y, int x) {
   const long long idx = (long long)y * p.nx + x;
   float2 s;
   if (p.src_kind == SRC_FIELD) {
-    s = ldg2(p.in + (long long)(f / p.in_repeat) * p.in_stride + idx);
+    s = ldg2(field_in(p, f) + idx);
   } else {
     const float gi = __ldg(p.gI + (long long)(f / p.src_group) * p.gI_stride + idx);
     const float w = p.weights ? __ldg(p.weights + f) : 1.f;
@@ -360,7 +368,7 @@ __global__ void __launch_bounds__(RowShape<EX>::THREADS) k_rows_fwd(const __grid
     const bool inten = p.src_kind == SRC_INTENSITY;
     const long long row0 = (long long)y0 * nx;
     const float2* src = inten ? p.psi + (long long)f * p.psi_stride + row0
-                              : p.in + (long long)(f / p.in_repeat) * p.in_stride + row0;
+                              : field_in(p, f) + row0;
     const float4* s4 = reinterpret_cast<const float4*>(src);
     float4* d4 = reinterpret_cast<float4*>(smem);
     const int n4 = nrows * nx / 2, all4 = ROWS * nx / 2;
@@ -580,7 +588,7 @@ __device__ __forceinline__ void epilogue_planes(const PassParams& p, const Field
   const ModDev& m = p.mepi;
   if constexpr (KIND == EPI_FIELD) {
     if (m.flags) val = c_mul(val, mod_value_planes(e, m.flags, m.conj, fs.epi_lx, ly, rg, i, x));
-    p.out[(long long)f * p.out_stride + idx] = val;
+    field_out(p, f)[idx] = val;
   } else if constexpr (KIND == EPI_INTENSITY) {
     if (m.flags) val = c_mul(val, mod_value_planes(e, m.flags, m.conj, fs.epi_lx, ly, rg, i, x));
     if (p.out) p.out[(long long)f * p.out_stride + idx] = val;
@@ -616,7 +624,7 @@ __device__ __forceinline__ void epilogue(const PassParams& p, const FieldSet& fs
   const long long idx = (long long)y * p.nx + x;
   if constexpr (KIND == EPI_FIELD) {
     if (p.mepi.flags) val = c_mul(val, mod_value(p.mepi, p.mepi.flags, p.mepi.conj, fs.epi_lx, fs.epi_ly, f, y, x, p.nx));
-    p.out[(long long)f * p.out_stride + idx] = val;
+    field_out(p, f)[idx] = val;
   } else if constexpr (KIND == EPI_INTENSITY) {
     if (p.mepi.flags) val = c_mul(val, mod_value(p.mepi, p.mepi.flags, p.mepi.conj, fs.epi_lx, fs.epi_ly, f, y, x, p.nx));
     if (p.out) p.out[(long long)f * p.out_stride + idx] = val;
