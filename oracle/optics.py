@@ -14,7 +14,12 @@ paper (TorchOptics, arXiv 2411.18591):
   of the zero-padded field by the transfer function H_z (Eq. 5), then inverts,
   with "configurable zero-padding" (§3);
 * the Fresnel variant (§3) uses the Fresnel transfer function;
-* the critical distance is Eq. 6;
+* Direct Integration (DI, §3) evaluates Eq. 2 as a convolution with h_z of Eq. 3
+  sampled at the grid's lags: the DFT of those samples (times dx dy) multiplies the
+  spectrum of the zero-padded field; with P >= 2n - 1 the cropped result is exactly the
+  direct sum of Eq. 2;
+* the critical distance is Eq. 6, and the automatic choice takes AS below it and DI
+  above it (§3);
 * mutual coherence is modulated by M(r1) M*(r2) (Eq. 12) and propagated with
   h_z on r1 and h_z* on r2 (Eq. 13);
 * polychromatic intensity is the incoherent sum over wavelengths (Eq. 14).
@@ -44,6 +49,8 @@ import numpy as np
 
 AS = 0
 FRESNEL_TF = 1
+DI = 2
+AUTO = 3
 
 
 # ----------------------------------------------------------------------------- grid
@@ -115,6 +122,32 @@ def idft2(x: np.ndarray, naive: bool = False) -> np.ndarray:
 
 # ----------------------------------------------------------------------------- transfer function
 
+def impulse_response(x, y, lam: float, z: float):
+    """h_z of Eq. 3 at lateral offsets (x, y): z / (i lambda d) (1 + i / (k d)) exp(i k d) / d,
+    d = sqrt(x^2 + y^2 + z^2), k = 2 pi / lambda."""
+    k = 2.0 * math.pi / lam
+    d = np.sqrt(x * x + y * y + z * z)
+    return z / (1j * lam * d) * (1.0 + 1j / (k * d)) * np.exp(1j * k * d) / d
+
+
+def di_transfer_function(py: int, px: int, dy: float, dx: float, lam: float, z: float) -> np.ndarray:
+    """DI (§3): the forward DFT of h_z (Eq. 3) sampled at the signed lags of the padded grid
+    (lag m of an axis is its signed FFT index), times dx dy, shape [Py, Px]. Multiplying the
+    spectrum of a zero-padded field by it is the circular convolution with those samples; for
+    an n-sample field and P >= 2n - 1 the cropped window is the direct sum of Eq. 2."""
+    x = signed_index(px).astype(np.float64) * dx
+    y = signed_index(py).astype(np.float64) * dy
+    h = impulse_response(x[None, :], y[:, None], lam, z) * (dx * dy)
+    return np.fft.fft2(h)
+
+
+def choose_method(ny: int, nx: int, dy: float, dx: float, lam: float, z: float) -> int:
+    """Eq. 6 per axis, z_crit = L dx / lambda with L = n d the grid length: AS when z is below
+    the smaller of the two critical distances, else DI."""
+    zc = min(z_critical(nx * dx, dx, lam), z_critical(ny * dy, dy, lam))
+    return AS if z < zc else DI
+
+
 def transfer_function(py: int, px: int, dy: float, dx: float, lam: float, z: float,
                       method: int = AS) -> np.ndarray:
     """H_z on the padded frequency grid, shape [Py, Px] (Eq. 5, §3).
@@ -137,6 +170,8 @@ def transfer_function(py: int, px: int, dy: float, dx: float, lam: float, z: flo
         return np.where(prop, np.exp(2j * math.pi * z * kz), 0.0)
     if method == FRESNEL_TF:
         return np.exp(2j * math.pi * z / lam) * np.exp(-1j * math.pi * lam * z * (fx2 + fy2))
+    if method == DI:
+        return di_transfer_function(py, px, dy, dx, lam, z)
     raise ValueError("unknown method")
 
 
@@ -167,7 +202,10 @@ def propagate(field: np.ndarray, dy: float, dx: float, lam: float, z: float, pad
     for i in range(b):
         buf = np.zeros((py, px), dtype=np.complex128)
         buf[oy:oy + ny, ox:ox + nx] = f[i]
-        h = transfer_function(py, px, dy, dx, float(lams[i]), float(zs[i]), method)
+        m = choose_method(ny, nx, dy, dx, float(lams[i]), float(zs[i])) if method == AUTO else method
+        if m == DI and (py < 2 * ny - 1 or px < 2 * nx - 1):
+            raise ValueError("DI needs a padded size of at least 2 n - 1 per axis")
+        h = transfer_function(py, px, dy, dx, float(lams[i]), float(zs[i]), m)
         if adjoint:
             h = np.conj(h)
         res = idft2(dft2(buf, naive) * h, naive)

@@ -241,6 +241,54 @@ def test_rayleigh_sommerfeld_bruteforce_matches_as():
     assert rel_l2(asr[c:-c, c:-c], rs[c:-c, c:-c]) < 1e-7
 
 
+def test_direct_integration_is_the_rayleigh_sommerfeld_sum():
+    """DI (Eq. 2-3 by FFT with P >= 2n - 1) equals the brute-force sum of Eq. 2 to rounding, on a
+    non-square grid with dx != dy, at a short and a long distance."""
+    ny, nx, dy, dx, lam = 24, 32, 3e-6, 2e-6, 0.6e-6
+    f0 = to_c64(normal(41, (ny, nx)) + 1j * normal(42, (ny, nx))).astype(np.complex128)
+    for z, pad in ((40e-6, 2.0), (2e-3, 2.5)):
+        rs = O.rs_bruteforce(f0, dy, dx, lam, z)
+        di = O.propagate(f0, dy, dx, lam, z, pad, O.DI)[0]
+        assert rel_l2(di, rs) < 1e-12
+    with pytest.raises(ValueError):
+        O.propagate(f0, dy, dx, lam, 2e-3, 1.5, O.DI)
+
+
+def test_direct_integration_beyond_z_critical_follows_the_beam():
+    """Far beyond z_critical (Eq. 6) the AS transfer function is undersampled while DI keeps
+    following the Gaussian beam (exact paraxial solution; the beam is wide against lambda, so
+    its non-paraxial correction is far below the tolerance)."""
+    n, d, lam, w0 = 64, 5e-6, 0.5e-6, 10e-6
+    zc = O.z_critical(n * d, d, lam)
+    z = 4 * zc  # the beam has spread to w(z) = 204 um on a 320 um grid
+    f0 = gaussian_beam(n, n, d, d, w0)
+    ref = paraxial_gaussian(n, n, d, d, lam, z, w0, w0)
+    err_di = rel_l2(O.propagate(f0, d, d, lam, z, 2.0, O.DI)[0], ref)
+    err_as = rel_l2(O.propagate(f0, d, d, lam, z, 2.0, O.AS)[0], ref)
+    assert err_di < 5e-4  # the paraxial model's own error, (lambda / (pi w0))^2 = 2.5e-4
+    assert err_as > 5 * err_di
+
+
+def test_automatic_method_follows_eq6():
+    ny, nx, dy, dx, lam = 16, 24, 4e-6, 5e-6, 0.5e-6
+    f0 = to_c64(normal(43, (ny, nx)) + 1j * normal(44, (ny, nx))).astype(np.complex128)
+    zc = min(O.z_critical(nx * dx, dx, lam), O.z_critical(ny * dy, dy, lam))
+    assert zc == pytest.approx(ny * dy * dy / lam)
+    below = O.propagate(f0, dy, dx, lam, 0.5 * zc, 2.0, O.AUTO)
+    above = O.propagate(f0, dy, dx, lam, 2.0 * zc, 2.0, O.AUTO)
+    assert np.array_equal(below, O.propagate(f0, dy, dx, lam, 0.5 * zc, 2.0, O.AS))
+    assert np.array_equal(above, O.propagate(f0, dy, dx, lam, 2.0 * zc, 2.0, O.DI))
+
+
+def test_direct_integration_adjoint_identity():
+    ny, nx, d, lam, z = 16, 16, 4e-6, 0.5e-6, 3e-3
+    x = to_c64(normal(45, (ny, nx)) + 1j * normal(46, (ny, nx))).astype(np.complex128)
+    y = to_c64(normal(47, (ny, nx)) + 1j * normal(48, (ny, nx))).astype(np.complex128)
+    px = O.propagate(x, d, d, lam, z, 2.0, O.DI)[0]
+    phy = O.propagate_adjoint(y, d, d, lam, z, 2.0, O.DI)[0]
+    assert abs(np.vdot(y, px) - np.vdot(phy, x)) < 1e-12 * abs(np.vdot(y, px))
+
+
 # ----------------------------------------------------------------------------- coherence
 
 def test_gsm_spreading_mandel_wolf():
@@ -369,13 +417,16 @@ def _pins_pass():
         test_identity_at_z0(O.AS, 2.0)
         for ab in [(3, 1), (-4, 2)]:
             test_plane_wave_is_eigenvector(*ab)
+        test_direct_integration_is_the_rayleigh_sommerfeld_sum()
+        test_automatic_method_follows_eq6()
     except AssertionError:
         return False
     return True
 
 
 @pytest.mark.parametrize("mistake", ["h_sign", "h_conj_adjoint", "swap_axes", "no_norm", "crop_shift",
-                                     "freq_order", "fresnel_sign", "drop_global_phase"])
+                                     "freq_order", "fresnel_sign", "drop_global_phase", "di_no_area",
+                                     "di_unsigned_lags", "di_conj_kernel", "auto_inverted"])
 def test_planted_mistakes(monkeypatch, mistake):
     """A plausible slip planted in the oracle must make at least one pin fail."""
     assert _pins_pass()
@@ -407,4 +458,17 @@ def test_planted_mistakes(monkeypatch, mistake):
         monkeypatch.setattr(O.optics, "transfer_function",
                             lambda py, px, dy, dx, lam, z, m=O.AS:
                             tf(py, px, dy, dx, lam, z, m) * np.exp(-2j * math.pi * z / lam))
+    elif mistake == "di_no_area":
+        di = O.optics.di_transfer_function
+        monkeypatch.setattr(O.optics, "di_transfer_function", lambda py, px, dy, dx, lam, z:
+                            di(py, px, dy, dx, lam, z) / (dx * dy))
+    elif mistake == "di_unsigned_lags":
+        monkeypatch.setattr(O.optics, "signed_index", lambda p: np.arange(p))
+    elif mistake == "di_conj_kernel":
+        h = O.optics.impulse_response
+        monkeypatch.setattr(O.optics, "impulse_response", lambda x, y, lam, z: np.conj(h(x, y, lam, z)))
+    elif mistake == "auto_inverted":
+        ch = O.optics.choose_method
+        monkeypatch.setattr(O.optics, "choose_method",
+                            lambda *a: O.DI if ch(*a) == O.AS else O.AS)
     assert not _pins_pass()
