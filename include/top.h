@@ -64,7 +64,12 @@ typedef enum top_status {
 } top_status;
 
 /* Propagation method (§3): angular spectrum (Eq. 4-5) or Fresnel transfer function. */
-typedef enum top_method { TOP_AS = 0, TOP_FRESNEL_TF = 1 } top_method;
+/* TOP_AS: angular spectrum (Eq. 4-5). TOP_FRESNEL_TF: Fresnel transfer function (§3).
+ * TOP_DI: Direct Integration (§3): Eq. 2 as the convolution with h_z (Eq. 3) sampled at the
+ * grid's lags, by FFT; needs a padded size of at least 2n - 1 per axis and z > 0.
+ * TOP_AUTO: per field, AS when z < z_critical (Eq. 6, the smaller of n dx^2 / lambda and
+ * n dy^2 / lambda) and DI otherwise, the paper's default choice. */
+typedef enum top_method { TOP_AS = 0, TOP_FRESNEL_TF = 1, TOP_DI = 2, TOP_AUTO = 3 } top_method;
 
 typedef struct top_ctx* top_handle;
 

@@ -12,6 +12,8 @@ STATUS = {0: "TOP_OK", 1: "TOP_ERR_INVALID_ARG", 2: "TOP_ERR_UNSUPPORTED", 3: "T
 
 TOP_AS = 0
 TOP_FRESNEL_TF = 1
+TOP_DI = 2
+TOP_AUTO = 3
 TOP_MOD_COMPLEX = 0x1
 TOP_MOD_AMPLITUDE = 0x2
 TOP_MOD_PHASE = 0x4

@@ -18,7 +18,9 @@ from . import _lib
 from ._lib import TopGrid, TopMod, TopModGrads, TopStage, check, doubles
 
 METHODS = {"as": _lib.TOP_AS, "angular_spectrum": _lib.TOP_AS, "fresnel": _lib.TOP_FRESNEL_TF,
-           "fresnel_tf": _lib.TOP_FRESNEL_TF, _lib.TOP_AS: _lib.TOP_AS, _lib.TOP_FRESNEL_TF: _lib.TOP_FRESNEL_TF}
+           "fresnel_tf": _lib.TOP_FRESNEL_TF, "di": _lib.TOP_DI, "direct": _lib.TOP_DI, "auto": _lib.TOP_AUTO,
+           _lib.TOP_AS: _lib.TOP_AS, _lib.TOP_FRESNEL_TF: _lib.TOP_FRESNEL_TF, _lib.TOP_DI: _lib.TOP_DI,
+           _lib.TOP_AUTO: _lib.TOP_AUTO}
 
 _handles: dict = {}
 _handle_lock = threading.Lock()

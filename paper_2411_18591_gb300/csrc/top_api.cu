@@ -239,6 +239,57 @@ top_status split_twiddles(top_handle h, int P, const float2** out) {
 long long signed_index(long long k, long long P) { return k < (P + 1) / 2 ? k : k - P; }
 double freq(long long k, long long P, double d) { return double(signed_index(k, P)) / (double(P) * d); }
 
+// Direct Integration table: the forward 2-D DFT of h_z (Eq. 3) sampled at the padded grid's signed
+// lags (times dx dy), divided by Py Px, into the quadrant layout (h_z is even in x and y, so its
+// transform is too). The samples are taken in float64 and transformed by the library's own row
+// pass and a forward-only column pass, through temporary buffers freed before returning.
+top_status di_table(top_handle h, int Py, int Px, double dy, double dx, double lam, double z, cudaStream_t st,
+                    float2* hq) {
+  const float2 *twx, *twy, *wpx, *wpy;
+  TOP_TRY(engine_twiddles(h, Px / 2, &twx));
+  TOP_TRY(engine_twiddles(h, Py / 2, &twy));
+  TOP_TRY(split_twiddles(h, Px, &wpx));
+  TOP_TRY(split_twiddles(h, Py, &wpy));
+  const size_t plane = size_t(Py) * size_t(Px);
+  void* buf = nullptr;
+  TOP_CUDA(cudaMalloc(&buf, 2 * plane * sizeof(float2)), "cudaMalloc(DI kernel samples)");
+  float2* samples = static_cast<float2*>(buf);
+  float2* ws = samples + plane;
+  PassParams p{};
+  p.ny = Py;
+  p.nx = Px;
+  p.Py = Py;
+  p.Px = Px;
+  p.My = Py / 2;
+  p.Mx = Px / 2;
+  p.method = TOP_DI;
+  p.src_kind = SRC_FIELD;
+  p.epi_kind = EPI_FIELD;
+  p.in = samples;
+  p.in_stride = (long long)plane;
+  p.in_repeat = 1;
+  p.ws = ws;
+  p.ws_stride = (long long)plane;
+  p.twx = twx;
+  p.twy = twy;
+  p.wpx = wpx;
+  p.wpy = wpy;
+  p.nfields = 1;
+  p.nsets = 1;
+  p.group = 1;
+  p.src_group = 1;
+  p.hq_out = hq;
+  p.hq_scale = float(1.0 / (double(Py) * double(Px)));
+  cudaError_t e = launch_di_samples(samples, Py, Px, dy, dx, lam, z, st);
+  if (e == cudaSuccess) e = launch_pass(PASS_ROWS_FWD, Px / 2, p, st);
+  if (e == cudaSuccess) e = launch_pass(PASS_COLS, Py / 2, p, st);
+  const cudaError_t es = cudaStreamSynchronize(st);
+  cudaFree(buf);
+  if (e != cudaSuccess) return cuda_fail(e, "DI table");
+  if (es != cudaSuccess) return cuda_fail(es, "cudaStreamSynchronize(DI table)");
+  return TOP_OK;
+}
+
 // Quadrant table of the transfer function for one (lambda, z) (Eq. 5 and the Fresnel form),
 // built in float64 on the device on first use and cached; the build is waited for, so later
 // calls on any stream may read it.
@@ -256,11 +307,35 @@ top_status transfer_tables(top_handle h, int Py, int Px, double dy, double dx, d
   TOP_CUDA(cudaMalloc(&p, size_t(Px / 2 + 1) * size_t(Py / 2 + 2) * sizeof(float2)), "cudaMalloc(transfer table)");
   h->allocs.push_back(p);
   te.hq = static_cast<float2*>(p);
-  TOP_CUDA(launch_transfer_table(te.hq, Py, Px, dy, dx, lam, z, method, st), "transfer table");
+  if (method == TOP_DI) {
+    TOP_TRY(di_table(h, Py, Px, dy, dx, lam, z, st, te.hq));
+  } else {
+    TOP_CUDA(launch_transfer_table(te.hq, Py, Px, dy, dx, lam, z, method, st), "transfer table");
+  }
   TOP_CUDA(cudaStreamSynchronize(st), "cudaStreamSynchronize(transfer table)");
   h->transfer[key] = te;
   *out = te;
   return TOP_OK;
+}
+
+// The method of one field: TOP_AUTO picks AS below z_critical (Eq. 6, the smaller of the two
+// axes' n d^2 / lambda) and DI above it.
+int resolve_method(const top_grid* g, int ny, int nx, double lam, double z) {
+  if (g->method != TOP_AUTO) return g->method;
+  const double zc = std::min(double(nx) * g->dx * g->dx / lam, double(ny) * g->dy * g->dy / lam);
+  return z < zc ? TOP_AS : TOP_DI;
+}
+
+// Transfer table of one field with its method resolved and the DI conditions checked.
+top_status field_transfer(top_handle h, const top_grid* g, int ny, int nx, int Py, int Px, double lam, double z,
+                          cudaStream_t st, TransferEntry* te) {
+  const int m = resolve_method(g, ny, nx, lam, z);
+  if (m == TOP_DI) {
+    if (Py < 2 * ny - 1 || Px < 2 * nx - 1)
+      return fail(TOP_ERR_INVALID_ARG, "DI needs padded sizes >= 2 n - 1 (got %dx%d for %dx%d; pad >= 2)", Py, Px, ny, nx);
+    if (!(z > 0)) return fail(TOP_ERR_INVALID_ARG, "DI needs z > 0 (got %g)", z);
+  }
+  return transfer_tables(h, Py, Px, g->dy, g->dx, lam, z, m, st, te);
 }
 
 // Thin-lens factor table exp(-i pi s^2 / (lambda f)) along one axis (s = (i - (n-1)/2) d).
@@ -337,7 +412,8 @@ top_status check_grid(const top_grid* g, Geometry* geo) {
   if (!(std::isfinite(g->dy) && g->dy > 0) || !(std::isfinite(g->dx) && g->dx > 0))
     return fail(TOP_ERR_INVALID_ARG, "spacing must be finite and > 0");
   if (!(std::isfinite(g->pad) && g->pad >= 1.0)) return fail(TOP_ERR_INVALID_ARG, "pad must be finite and >= 1");
-  if (g->method != TOP_AS && g->method != TOP_FRESNEL_TF) return fail(TOP_ERR_INVALID_ARG, "unknown method %d", g->method);
+  if (g->method != TOP_AS && g->method != TOP_FRESNEL_TF && g->method != TOP_DI && g->method != TOP_AUTO)
+    return fail(TOP_ERR_INVALID_ARG, "unknown method %d", g->method);
   if (g->input_repeat < 0 || (g->input_repeat > 1 && g->batch % g->input_repeat != 0))
     return fail(TOP_ERR_INVALID_ARG, "input_repeat (%d) must be 0, 1 or a divisor of batch", g->input_repeat);
   geo->ny = g->ny;
@@ -495,7 +571,7 @@ top_status run_propagation(top_handle h, const Request& q, cudaStream_t st) {
   for (int64_t b = 0; b < B; ++b) {
     const int64_t i = q.n_lz == 1 ? 0 : b;
     TransferEntry te;
-    TOP_TRY(transfer_tables(h, geo.Py, geo.Px, g->dy, g->dx, q.lam[i], q.z[i], g->method, st, &te));
+    TOP_TRY(field_transfer(h, g, geo.ny, geo.nx, geo.Py, geo.Px, q.lam[i], q.z[i], st, &te));
     FieldSet fs{};
     fs.hq = te.hq;
     if (q.msrc && (q.msrc->flags & TOP_MOD_LENS)) {
@@ -725,7 +801,7 @@ top_status run_chain(top_handle h, const top_grid* g, const void* in, void* out,
     for (int64_t b = 0; b < B; ++b) {
       const int64_t i = n_lz == 1 ? 0 : b;
       TransferEntry te;
-      TOP_TRY(transfer_tables(h, geo.Py, geo.Px, g->dy, g->dx, lam[i], stages[k].z, g->method, st, &te));
+      TOP_TRY(field_transfer(h, g, geo.ny, geo.nx, geo.Py, geo.Px, lam[i], stages[k].z, st, &te));
       FieldSet fs{};
       fs.hq = te.hq;
       if (m && (m->flags & TOP_MOD_LENS)) {
@@ -923,7 +999,7 @@ top_status run_ragged(top_handle h, int count, const top_grid* grids, const void
     for (int64_t j = 0; j < nf; ++j) {
       const int i = grp[j];
       TransferEntry te;
-      TOP_TRY(transfer_tables(h, geo.Py, geo.Px, grids[i].dy, grids[i].dx, lam[i], z[i], method, st, &te));
+      TOP_TRY(field_transfer(h, &grids[i], geo.ny, geo.nx, geo.Py, geo.Px, lam[i], z[i], st, &te));
       fsets[j] = FieldSet{};
       fsets[j].hq = te.hq;
     }
@@ -1553,6 +1629,8 @@ top_status propagate_noalloc(const top_grid* g, const void* in, void* out, const
   TOP_TRY(check_engines(geo));
   TOP_TRY(check_lz(g, lam, z, n_lz, true));
   if (g->input_repeat > 1) return fail(TOP_ERR_UNSUPPORTED, "top_propagate_noalloc takes input_repeat 0 or 1");
+  if (g->method != TOP_AS && g->method != TOP_FRESNEL_TF)
+    return fail(TOP_ERR_UNSUPPORTED, "top_propagate_noalloc takes the AS and Fresnel methods");
   TOP_TRY(check_ptr(in, "input field"));
   TOP_TRY(check_ptr(out, "output field"));
   const int64_t B = g->batch;

@@ -174,6 +174,33 @@ __global__ void __launch_bounds__(256) k_transfer_table(float2* hq, int Py, int 
   *out = make_float2(float(cs * norm), float(sn * norm));
 }
 
+// h_z(x, y) dx dy of Eq. 3 at x = sx dx, y = sy dy with (sx, sy) the signed lags of the grid:
+// h = z / (i lambda d) (1 + i / (k d)) exp(i k d) / d = (z / (lambda d^2)) (1/(k d) - i) exp(i k d),
+// the phase k d reduced in cycles (d / lambda - rint) before the sine and cosine.
+__global__ void __launch_bounds__(256) k_di_samples(float2* out, int Py, int Px, double dy, double dx, double lam,
+                                                    double z) {
+  const int ix = blockIdx.x * blockDim.x + threadIdx.x;
+  const int iy = blockIdx.y;
+  if (ix >= Px) return;
+  const int sx = ix < (Px + 1) / 2 ? ix : ix - Px;
+  const int sy = iy < (Py + 1) / 2 ? iy : iy - Py;
+  const double x = sx * dx, y = sy * dy;
+  const double r2 = x * x + y * y + z * z;
+  const double d = sqrt(r2);
+  const double amp = z / (lam * r2) * (dx * dy);
+  const double a = lam / (2.0 * 3.14159265358979323846 * d);  // 1 / (k d)
+  const double c = d / lam;
+  double sn, cs;
+  sincospi(2.0 * (c - rint(c)), &sn, &cs);
+  out[(long long)iy * Px + ix] = make_float2(float(amp * (a * cs + sn)), float(amp * (a * sn - cs)));
+}
+
+cudaError_t launch_di_samples(float2* out, int Py, int Px, double dy, double dx, double lam, double z, cudaStream_t s) {
+  dim3 grid((Px + 255) / 256, Py);
+  TOP_LAUNCH(k_di_samples, grid, 256, 0, s, out, Py, Px, dy, dx, lam, z);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_transfer_table(float2* hq, int Py, int Px, double dy, double dx, double lam, double z, int method,
                                   cudaStream_t s) {
   const int my = Py / 2;

@@ -18,6 +18,9 @@ cudaError_t launch_reduce_partials(const float* part_phase, const float* part_am
                                    cudaStream_t s);
 cudaError_t launch_mse(long long n, const float* I, const float* T, float* grad, double* partial, double* loss,
                        cudaStream_t s);
+// Samples of h_z (Eq. 3) times dx dy at the signed lags of a Py x Px grid, row-major (float64
+// arithmetic, rounded once), the kernel of the Direct Integration method.
+cudaError_t launch_di_samples(float2* out, int Py, int Px, double dy, double dx, double lam, double z, cudaStream_t s);
 // Quadrant table of H / (Py Px) for one (lambda, z) in the FieldSet::hq layout (float64 arithmetic).
 cudaError_t launch_transfer_table(float2* hq, int Py, int Px, double dy, double dx, double lam, double z, int method,
                                   cudaStream_t s);

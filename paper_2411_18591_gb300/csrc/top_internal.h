@@ -89,6 +89,11 @@ struct PassParams {
   const float2* wpx;  // exp(-2 pi i p / Px), p < Mx
   const float2* wpy;
 
+  // column pass as the second half of a forward 2-D transform: bins of columns kx <= Px/2 go to
+  // this quadrant table (FieldSet::hq layout) times hq_scale, nothing else is written
+  float2* hq_out;
+  float hq_scale;
+
   ModDev msrc;  // modulation applied to the R1 source
   ModDev mepi;  // modulation applied in the R2 epilogue
 

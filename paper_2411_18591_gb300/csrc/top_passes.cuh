@@ -478,6 +478,31 @@ __global__ void __launch_bounds__(ColShape<EY>::THREADS, ColShape<EY>::MINB) k_c
   fold<EY, X2, 1>(v, line, ny, p.oy, r, p.wpy, t);
   __syncthreads();  // the lines become the even halves' exchange buffers
   EY::fwd(v, xbuf, t, p.twy);
+  if (p.hq_out) {
+    // forward transform only (a transfer-function table from sampled kernels): half r holds
+    // ky = 2k + r, kept where |ky| <= Py/2, i.e. k <= M/2 (even) and k < M/2 (odd), plus the
+    // zero that pads each row
+    if (kpos0 + cl < p.Px) {
+      const int kp = kpos0 + cl;
+      const int rx = kp >= p.Mx ? 1 : 0;
+      const int kx = 2 * (kp - rx * p.Mx) + rx;
+      if (kx <= p.Px / 2) {
+        float2* row = p.hq_out + (long long)kx * (M + 2);
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int k = EY::bin(t, e);
+          if (r == 0) {
+            if (k <= M / 2) row[k] = c_scale(v[e], p.hq_scale);
+          } else if (k < M / 2) {
+            row[M / 2 + 1 + k] = c_scale(v[e], p.hq_scale);
+          } else if (k == M / 2) {
+            row[M + 1] = make_float2(0.f, 0.f);
+          }
+        }
+      }
+    }
+    return;
+  }
   if constexpr (SH::template stage_h<X2>()) {
     apply_transfer<EY, true>(v, hrows + cl * SH::HS, r, p.adjoint, t);
   } else {
