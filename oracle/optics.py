@@ -22,7 +22,8 @@ paper (TorchOptics, arXiv 2411.18591):
   above it (§3);
 * mutual coherence is modulated by M(r1) M*(r2) (Eq. 12) and propagated with
   h_z on r1 and h_z* on r2 (Eq. 13);
-* polychromatic intensity is the incoherent sum over wavelengths (Eq. 14).
+* polychromatic intensity is the incoherent sum over wavelengths (Eq. 14);
+* the overlap loss is Eq. 7 with the integral as a sum times dx dy, averaged over a batch.
 
 Readings of points the paper leaves open (each listed in the design doc):
 
@@ -285,6 +286,27 @@ def intensity_sum(field: np.ndarray, group: int, weights=None) -> np.ndarray:
 def power(field: np.ndarray, dy: float, dx: float) -> np.ndarray:
     """Total power sum |psi|^2 dx dy per field."""
     return intensity(_as_batch(field)).sum(axis=(-2, -1)) * dx * dy
+
+
+def overlap(field: np.ndarray, target: np.ndarray, dy: float, dx: float) -> np.ndarray:
+    """The integral of Eq. 7 per field: O_b = sum_{x,y} psi_b conj(phi) dx dy (phi [ny, nx] shared
+    or [B, ny, nx] per field)."""
+    f = _as_batch(field)
+    t = np.asarray(target, dtype=np.complex128)
+    return (f * np.conj(t)).sum(axis=(-2, -1)) * dx * dy
+
+
+def overlap_loss(field: np.ndarray, target: np.ndarray, dy: float, dx: float):
+    """Eq. 7 averaged over the batch, L = mean_b (1 - |O_b|^2), and dL/dpsi in the real-loss
+    convention: d|O|^2 = 2 Re(conj(O) dO) with dO = conj(phi) dpsi dx dy gives
+    g_b = -(2 / B) O_b phi dx dy."""
+    f = _as_batch(field)
+    o = overlap(f, target, dy, dx)
+    b = f.shape[0]
+    t = np.broadcast_to(np.asarray(target, dtype=np.complex128), f.shape)
+    loss = float(np.mean(1.0 - np.abs(o) ** 2))
+    grad = -(2.0 / b) * o[:, None, None] * t * (dx * dy)
+    return loss, grad
 
 
 # ----------------------------------------------------------------------------- coherence

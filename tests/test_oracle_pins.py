@@ -289,6 +289,47 @@ def test_direct_integration_adjoint_identity():
     assert abs(np.vdot(y, px) - np.vdot(phy, x)) < 1e-12 * abs(np.vdot(y, px))
 
 
+def test_overlap_of_two_gaussians_closed_form():
+    """Eq. 7's integral of exp(-|r - a|^2 / w1^2) exp(-|r - b|^2 / w2^2) is
+    pi / (1/w1^2 + 1/w2^2) exp(-|a - b|^2 / (w1^2 + w2^2)); well-sampled Gaussians inside the
+    grid reproduce it to rounding. The power of a Gaussian is the same integral with itself."""
+    ny, nx, dy, dx = 96, 128, 2e-6, 1.5e-6
+    w1, w2 = 20e-6, 14e-6
+    a, b = (6e-6, -4e-6), (-3e-6, 5e-6)
+    x = O.coords(nx, dx)[None, :]
+    y = O.coords(ny, dy)[:, None]
+    g1 = np.exp(-((x - a[0]) ** 2 + (y - a[1]) ** 2) / w1 ** 2)
+    g2 = np.exp(-((x - b[0]) ** 2 + (y - b[1]) ** 2) / w2 ** 2) * np.exp(0.7j)
+    ref = math.pi / (1 / w1 ** 2 + 1 / w2 ** 2) * math.exp(-((a[0] - b[0]) ** 2 + (a[1] - b[1]) ** 2) / (w1 ** 2 + w2 ** 2))
+    o = O.overlap(g1, g2, dy, dx)[0]
+    assert abs(o - ref * np.exp(-0.7j)) < 1e-10 * ref
+    assert O.power(g1, dy, dx)[0] == pytest.approx(math.pi * w1 * w1 / 2, rel=1e-10)
+
+
+def test_overlap_loss_gradient_by_finite_differences():
+    """dL/dphi of Eq. 7 (batch mean) through a phase mask and an AS propagation: the analytic chain
+    (overlap-loss gradient, adjoint propagation, phase gradient) against central differences."""
+    n, d, lam, z = 16, 8e-6, 0.6e-6, 2e-3
+    s = 0.4 / (n * d)  # unit-order powers
+    x = to_c64(normal(51, (2, n, n)) + 1j * normal(52, (2, n, n))).astype(np.complex128) * s
+    phi = uniform(55, (n, n), -math.pi, math.pi)
+    # a target close to the first output, so |O| is of order 1 and the differences resolve
+    tgt = 1.5 * O.propagate(x[:1] * np.exp(1j * uniform(56, (n, n), -0.3, 0.3) + 1j * phi), d, d, lam, z, 2.0)[0]
+
+    def loss(p):
+        out = O.propagate(x * np.exp(1j * p), d, d, lam, z, 2.0)
+        return O.overlap_loss(out, tgt, d, d)[0]
+
+    m = np.exp(1j * phi)
+    out = O.propagate(x * m, d, d, lam, z, 2.0)
+    _, g = O.overlap_loss(out, tgt, d, d)
+    gy = O.propagate_adjoint(g, d, d, lam, z, 2.0)
+    g_phi = O.grad_modulation(x, m, gy)[2]
+    idx = np.arange(0, n * n, 7)
+    fd = O.finite_difference(loss, phi, idx)
+    assert np.max(np.abs(fd - g_phi.reshape(-1)[idx])) < 1e-6 * np.max(np.abs(fd))
+
+
 # ----------------------------------------------------------------------------- coherence
 
 def test_gsm_spreading_mandel_wolf():
