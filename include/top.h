@@ -254,6 +254,25 @@ top_status top_modulate_backward(top_handle h, const top_grid* g, const top_mod*
 
 /* ---------------------------------------------------------------- losses */
 
+/* The overlap integral of Eq. 7 at the output of a propagation, fused into its last pass: for
+ * every field O_b = sum_{x,y} psi_b conj(phi_b) dx dy and its power sum |psi_b|^2 dx dy, with
+ * psi_b = post * P_z(pre * in_b) (Eq. 1, Eq. 4). target phi: complex64 device, [ny][nx]
+ * (target_stride 0, shared) or [batch][ny][nx] (target_stride ny nx). overlap: device
+ * double[2 batch] (re, im per field); power: device double[batch] or NULL; field_out: psi
+ * (complex64 [batch][ny][nx]) or NULL, in which case psi is never written. The sums are
+ * float64 in a fixed order (deterministic). */
+top_status top_propagate_overlap(top_handle h, const top_grid* g, const void* in, void* field_out,
+                                 const void* target, int64_t target_stride, double* overlap, double* power,
+                                 const double* lambda, const double* z, int64_t n_lz, const top_mod* pre,
+                                 const top_mod* post, void* stream);
+
+/* Loss of Eq. 7 averaged over the batch, L = mean_b (1 - |O_b|^2), from the overlaps of
+ * top_propagate_overlap (device double[2 batch]) into loss (device double[1]); when grad is
+ * non-NULL also dL/dpsi_b = -(2 / batch) O_b phi_b dx dy (complex64 [batch][ny][nx], the
+ * real-loss convention), ready for top_propagate_backward. g gives batch, ny, nx, dy, dx. */
+top_status top_overlap_loss(top_handle h, const top_grid* g, const double* overlap, const void* target,
+                            int64_t target_stride, double* loss, void* grad, void* stream);
+
 /* L = mean((I - T)^2) over n elements and grad = 2 (I - T) / n (float32, device; grad may be
  * NULL). loss: device double[1]. Deterministic two-stage reduction. */
 top_status top_mse_loss(top_handle h, int64_t n, const float* intensity, const float* target, double* loss,

@@ -75,6 +75,8 @@ SIGNATURES = {
     "top_modulate": (C.c_int, [_P, _GRID, _MOD, _P, _P, _D, _I64, _P]),
     "top_modulate_backward": (C.c_int, [_P, _GRID, _MOD, _P, _P, _GRADS, _D, _I64, _P]),
     "top_mse_loss": (C.c_int, [_P, _I64, _P, _P, _P, _P, _P]),
+    "top_propagate_overlap": (C.c_int, [_P, _GRID, _P, _P, _P, _I64, _P, _P, _D, _D, _I64, _MOD, _MOD, _P]),
+    "top_overlap_loss": (C.c_int, [_P, _GRID, _P, _P, _I64, _P, _P, _P]),
     "top_propagate_coherence": (C.c_int, [_P, _GRID, _P, _P, _D, _D, _MOD, _P]),
     "top_propagate_coherence_backward": (C.c_int, [_P, _GRID, _P, _P, _D, _D, _MOD, _GRADS, _P]),
     "top_coherence_intensity": (C.c_int, [_P, _GRID, _P, _P, _P]),

@@ -159,6 +159,41 @@ def top_propagate(field: torch.Tensor, dy: float, dx: float, lam, z, pad: float 
     return out
 
 
+def top_propagate_overlap(field: torch.Tensor, target: torch.Tensor, dy: float, dx: float, lam, z, pad: float = 2.0,
+                          method="as", pre: Optional[Modulation] = None, post: Optional[Modulation] = None,
+                          keep_field: bool = False):
+    """Overlaps O_b = sum psi_b conj(phi) dx dy of Eq. 7 and powers sum |psi_b|^2 dx dy of
+    psi_b = post * P_z(pre * field_b); returns (overlap complex128 [batch], power float64 [batch],
+    psi or None). ``target`` is [ny, nx] (shared) or [batch, ny, nx]."""
+    _field(field, "field")
+    _field(target, "target")
+    b, ny, nx = _shape3(field)
+    stride = ny * nx if target.dim() == 3 else 0
+    ov = torch.empty((b, 2), dtype=torch.float64, device=field.device)
+    pw = torch.empty((b,), dtype=torch.float64, device=field.device)
+    psi = torch.empty_like(field) if keep_field else None
+    lams, zs, n = _lz(lam, z, b)
+    g = make_grid(b, ny, nx, dy, dx, pad, method)
+    check(_lib.load().top_propagate_overlap(handle(field.device), C.byref(g), field.data_ptr(), _ptr(psi),
+                                            target.data_ptr(), stride, ov.data_ptr(), pw.data_ptr(), lams, zs, n,
+                                            _mod(pre), _mod(post), _stream(field)))
+    return torch.view_as_complex(ov), pw, psi
+
+
+def top_overlap_loss(overlap: torch.Tensor, target: torch.Tensor, batch: int, ny: int, nx: int, dy: float, dx: float,
+                     want_grad: bool = True):
+    """Eq. 7 loss mean_b (1 - |O_b|^2) (device float64 scalar) and dL/dpsi (complex64 [batch, ny, nx])."""
+    _field(target, "target")
+    ov = torch.view_as_real(overlap.to(torch.complex128)).contiguous()
+    stride = ny * nx if target.dim() == 3 else 0
+    loss = torch.empty((1,), dtype=torch.float64, device=target.device)
+    grad = torch.empty((batch, ny, nx), dtype=torch.complex64, device=target.device) if want_grad else None
+    g = make_grid(batch, ny, nx, dy, dx)
+    check(_lib.load().top_overlap_loss(handle(target.device), C.byref(g), ov.data_ptr(), target.data_ptr(), stride,
+                                       loss.data_ptr(), _ptr(grad), _stream(target)))
+    return loss[0], grad
+
+
 def top_propagate_ragged(fields: Sequence[torch.Tensor], spacings, lams, zs, pad: float = 2.0, method="as",
                          backward: bool = False, out: Optional[Sequence[torch.Tensor]] = None):
     """Propagate (or back-propagate) fields of different sizes in one call: field i ([ny, nx]

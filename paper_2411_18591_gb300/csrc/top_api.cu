@@ -511,6 +511,10 @@ struct Request {
   const top_mod* mepi;
   int mepi_conj;
   const top_mod_grads* grads;  // EPI_MODGRAD
+  const void* target;          // EPI_OVERLAP: phi, shared (target_stride 0) or per field
+  int64_t target_stride;
+  double* ov_out;              // EPI_OVERLAP: [2 batch] overlaps, [batch] powers (may be null)
+  double* pw_out;
 };
 
 top_status run_propagation(top_handle h, const Request& q, cudaStream_t st) {
@@ -537,6 +541,14 @@ top_status run_propagation(top_handle h, const Request& q, cudaStream_t st) {
   if (q.epi_kind == EPI_FIELD) TOP_TRY(check_ptr(q.out, "output field"));
   if (q.epi_kind == EPI_INTENSITY) {
     TOP_TRY(check_ptr(q.outf, "intensity"));
+    if (q.out) TOP_TRY(check_ptr(q.out, "field output"));
+  }
+  if (q.epi_kind == EPI_OVERLAP) {
+    TOP_TRY(check_ptr(q.target, "target"));
+    if (q.target_stride != 0 && q.target_stride != (int64_t)geo.ny * geo.nx)
+      return fail(TOP_ERR_INVALID_ARG, "target_stride must be 0 (shared) or ny * nx (per field)");
+    if (!q.ov_out || (reinterpret_cast<uintptr_t>(q.ov_out) & 7u) || (reinterpret_cast<uintptr_t>(q.pw_out) & 7u))
+      return fail(TOP_ERR_INVALID_ARG, "overlap must be a non-NULL, 8-byte aligned device array (power too when given)");
     if (q.out) TOP_TRY(check_ptr(q.out, "field output"));
   }
   const top_mod_grads* gr = q.grads;
@@ -599,7 +611,11 @@ top_status run_propagation(top_handle h, const Request& q, cudaStream_t st) {
     group = std::max<int64_t>(1, (B + want_groups - 1) / want_groups);
   }
   const size_t ws_field = size_t(geo.Px) * size_t(geo.ny) * sizeof(float2);
+  EngineInfo ex_info;
+  find_engine(geo.Px / 2, &ex_info);
+  const int ntiles = (geo.ny + ex_info.rows - 1) / ex_info.rows;  // R2 row tiles (overlap partial sums)
   size_t part_bytes_per_group = 0;
+  if (q.epi_kind == EPI_OVERLAP) part_bytes_per_group = size_t(ntiles) * 3 * sizeof(double);
   if (partials) {
     if (gr->grad_phase) part_bytes_per_group += plane * sizeof(float);
     if (gr->grad_amplitude) part_bytes_per_group += plane * sizeof(float);
@@ -737,7 +753,18 @@ top_status run_propagation(top_handle h, const Request& q, cudaStream_t st) {
     }
     TOP_TRY(timed(h, KK_ROWS_FWD, st, "rows forward pass", [&] { return launch_pass(PASS_ROWS_FWD, p.Mx, p, st); }));
     TOP_TRY(timed(h, KK_COLS, st, "column pass", [&] { return launch_pass(PASS_COLS, p.My, p, st); }));
+    if (q.epi_kind == EPI_OVERLAP) {
+      p.target = static_cast<const float2*>(q.target) + pos * q.target_stride;
+      p.target_stride = q.target_stride;
+      p.ov_part = reinterpret_cast<double*>(part_base);
+    }
     TOP_TRY(timed(h, KK_ROWS_INV, st, "rows inverse pass", [&] { return launch_pass(PASS_ROWS_INV, p.Mx, p, st); }));
+    if (q.epi_kind == EPI_OVERLAP) {
+      TOP_TRY(timed(h, KK_AUX, st, "overlap sums", [&] {
+        return launch_overlap_finish(p.ov_part, ntiles, int(n), g->dy * g->dx, q.ov_out + 2 * pos,
+                                     q.pw_out ? q.pw_out + pos : nullptr, st);
+      }));
+    }
     pos += n;
   }
   if (partials) {
@@ -1160,6 +1187,44 @@ top_status top_propagate(top_handle h, const top_grid* g, const void* in, void* 
   q.msrc = pre; q.msrc_conj = 0;
   q.epi_kind = EPI_FIELD; q.out = out; q.mepi = post; q.mepi_conj = 0;
   return run_propagation(h, q, static_cast<cudaStream_t>(stream));
+}
+
+top_status top_propagate_overlap(top_handle h, const top_grid* g, const void* in, void* field_out,
+                                 const void* target, int64_t target_stride, double* overlap, double* power,
+                                 const double* lambda, const double* z, int64_t n_lz, const top_mod* pre,
+                                 const top_mod* post, void* stream) {
+  if (!h) return fail(TOP_ERR_INVALID_ARG, "handle is NULL");
+  Request q{};
+  q.g = g; q.lam = lambda; q.z = z; q.n_lz = n_lz; q.adjoint = 0;
+  q.src_kind = SRC_FIELD; q.in = in; q.group = 1;
+  q.msrc = pre; q.msrc_conj = 0;
+  q.epi_kind = EPI_OVERLAP; q.out = field_out; q.mepi = post; q.mepi_conj = 0;
+  q.target = target; q.target_stride = target_stride; q.ov_out = overlap; q.pw_out = power;
+  return run_propagation(h, q, static_cast<cudaStream_t>(stream));
+}
+
+top_status top_overlap_loss(top_handle h, const top_grid* g, const double* overlap, const void* target,
+                            int64_t target_stride, double* loss, void* grad, void* stream) {
+  if (!h) return fail(TOP_ERR_INVALID_ARG, "handle is NULL");
+  if (!g) return fail(TOP_ERR_INVALID_ARG, "grid is NULL");
+  if (g->batch < 1 || g->ny < 1 || g->nx < 1) return fail(TOP_ERR_INVALID_ARG, "batch, ny and nx must be >= 1");
+  if (!(std::isfinite(g->dy) && g->dy > 0) || !(std::isfinite(g->dx) && g->dx > 0))
+    return fail(TOP_ERR_INVALID_ARG, "spacing must be finite and > 0");
+  const long long plane = (long long)g->ny * g->nx;
+  if (!overlap || (reinterpret_cast<uintptr_t>(overlap) & 7u) || !loss || (reinterpret_cast<uintptr_t>(loss) & 7u))
+    return fail(TOP_ERR_INVALID_ARG, "overlap and loss must be non-NULL, 8-byte aligned device arrays");
+  if (grad) {
+    TOP_TRY(check_ptr(grad, "grad"));
+    TOP_TRY(check_ptr(target, "target"));
+    if (target_stride != 0 && target_stride != plane)
+      return fail(TOP_ERR_INVALID_ARG, "target_stride must be 0 (shared) or ny * nx (per field)");
+  }
+  TOP_TRY(bind(h));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  return timed(h, KK_AUX, st, "overlap loss", [&] {
+    return launch_overlap_loss(overlap, g->batch, static_cast<const float2*>(target), target_stride, plane,
+                               g->dy * g->dx, loss, static_cast<float2*>(grad), st);
+  });
 }
 
 top_status top_propagate_ragged(top_handle h, int count, const top_grid* grids, const void* const* in,

@@ -201,6 +201,69 @@ cudaError_t launch_di_samples(float2* out, int Py, int Px, double dy, double dx,
   return cudaGetLastError();
 }
 
+// One warp per field: lanes take tiles lane, lane + 32, ... in order, then a fixed butterfly.
+__global__ void __launch_bounds__(32) k_overlap_finish(const double* part, int ntiles, double area, double* overlap,
+                                                       double* power) {
+  const int f = blockIdx.x;
+  const int lane = threadIdx.x;
+  double sr = 0.0, si = 0.0, sp = 0.0;
+  const double* pf = part + (long long)f * ntiles * 3;
+  for (int i = lane; i < ntiles; i += 32) {
+    sr += pf[3 * i];
+    si += pf[3 * i + 1];
+    sp += pf[3 * i + 2];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    sr += __shfl_xor_sync(0xffffffffu, sr, o);
+    si += __shfl_xor_sync(0xffffffffu, si, o);
+    sp += __shfl_xor_sync(0xffffffffu, sp, o);
+  }
+  if (lane == 0) {
+    overlap[2 * f] = sr * area;
+    overlap[2 * f + 1] = si * area;
+    if (power) power[f] = sp * area;
+  }
+}
+
+cudaError_t launch_overlap_finish(const double* part, int ntiles, int nfields, double area, double* overlap,
+                                  double* power, cudaStream_t s) {
+  if (nfields < 1) return cudaSuccess;
+  TOP_LAUNCH(k_overlap_finish, nfields, 32, 0, s, part, ntiles, area, overlap, power);
+  return cudaGetLastError();
+}
+
+__global__ void k_overlap_loss_value(const double* overlap, long long batch, double* loss) {
+  double l = 0.0;
+  for (long long b = 0; b < batch; ++b) {
+    const double re = overlap[2 * b], im = overlap[2 * b + 1];
+    l += 1.0 - (re * re + im * im);
+  }
+  loss[0] = l / double(batch);
+}
+
+__global__ void __launch_bounds__(256) k_overlap_grad(const double* overlap, long long batch, const float2* target,
+                                                      long long target_stride, long long plane, double area,
+                                                      float2* grad) {
+  const double s = -2.0 * area / double(batch);
+  const long long total = batch * plane;
+  for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < total; j += (long long)gridDim.x * blockDim.x) {
+    const long long b = j / plane, i = j - b * plane;
+    const float2 c = make_float2(float(s * overlap[2 * b]), float(s * overlap[2 * b + 1]));
+    grad[j] = c_mul(c, ldg2(target + b * target_stride + i));
+  }
+}
+
+cudaError_t launch_overlap_loss(const double* overlap, long long batch, const float2* target, long long target_stride,
+                                long long plane, double area, double* loss, float2* grad, cudaStream_t s) {
+  TOP_LAUNCH(k_overlap_loss_value, 1, 1, 0, s, overlap, batch, loss);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || !grad) return e;
+  const long long blocks = (batch * plane + 255) / 256;
+  TOP_LAUNCH(k_overlap_grad, unsigned(blocks < 152 * 64 ? blocks : 152 * 64), 256, 0, s, overlap, batch, target,
+             target_stride, plane, area, grad);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_transfer_table(float2* hq, int Py, int Px, double dy, double dx, double lam, double z, int method,
                                   cudaStream_t s) {
   const int my = Py / 2;

@@ -21,6 +21,13 @@ cudaError_t launch_mse(long long n, const float* I, const float* T, float* grad,
 // Samples of h_z (Eq. 3) times dx dy at the signed lags of a Py x Px grid, row-major (float64
 // arithmetic, rounded once), the kernel of the Direct Integration method.
 cudaError_t launch_di_samples(float2* out, int Py, int Px, double dy, double dx, double lam, double z, cudaStream_t s);
+// Overlaps of Eq. 7 and powers per field from the row-tile partial sums of an EPI_OVERLAP pass:
+// overlap[2 f] + i overlap[2 f + 1] = area sum_tiles, power[f] = area sum_tiles (fixed order).
+cudaError_t launch_overlap_finish(const double* part, int ntiles, int nfields, double area, double* overlap,
+                                  double* power, cudaStream_t s);
+// L = mean_b (1 - |O_b|^2) into loss[0] and, when grad is non-null, grad_b = -(2/B) O_b phi_b area.
+cudaError_t launch_overlap_loss(const double* overlap, long long batch, const float2* target, long long target_stride,
+                                long long plane, double area, double* loss, float2* grad, cudaStream_t s);
 // Quadrant table of H / (Py Px) for one (lambda, z) in the FieldSet::hq layout (float64 arithmetic).
 cudaError_t launch_transfer_table(float2* hq, int Py, int Px, double dy, double dx, double lam, double z, int method,
                                   cudaStream_t s);

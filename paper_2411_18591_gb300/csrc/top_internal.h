@@ -49,6 +49,7 @@ enum EpiKind : int {
   EPI_FIELD = 0,      // out[f] = modepi * v
   EPI_INTENSITY = 1,  // I[g] += w_f |modepi * v|^2 over the group; optional out[f] = modepi * v
   EPI_MODGRAD = 2,    // gradient of a modulation y = M x: grad_in = conj(M) v, grads of M (partials)
+  EPI_OVERLAP = 3,    // per row tile: sums of psi conj(phi) and |psi|^2, psi = modepi * v (Eq. 7); optional out[f]
 };
 
 struct PassParams {
@@ -89,6 +90,10 @@ struct PassParams {
   const float2* wpx;  // exp(-2 pi i p / Px), p < Mx
   const float2* wpy;
 
+  // EPI_OVERLAP: target phi (+ f * target_stride) and float64 partial sums [field][row tile][3]
+  // (re and im of sum psi conj(phi), sum |psi|^2)
+  const float2* target; long long target_stride;
+  double* ov_part;
   // column pass as the second half of a forward 2-D transform: bins of columns kx <= Px/2 go to
   // this quadrant table (FieldSet::hq layout) times hq_scale, nothing else is written
   float2* hq_out;

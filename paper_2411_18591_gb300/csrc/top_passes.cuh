@@ -69,6 +69,7 @@ struct RowShape {
                                              ? SMEM + sizeof(float) * 10 * ROWS * 2 * EN::M
                                              : 227 * 1024;
   static_assert(SMEM % 16 == 0, "staged planes start on a 16-byte boundary");
+  static_assert(SMEM >= 3 * sizeof(double) * THREADS, "room for the overlap reduction");
   static_assert(THREADS <= 1024, "row block too large");
   static_assert(EN::M % 2 == 0, "the four-line workspace blocks need P = 2M to be a multiple of 4");
 };
@@ -553,6 +554,18 @@ __global__ void __launch_bounds__(ColShape<EY>::THREADS, ColShape<EY>::MINB) k_c
 
 // ----------------------------------------------------------------------------- R2
 
+// Per-thread float64 sums of the overlap epilogue: psi conj(phi) and |psi|^2.
+struct OvAcc {
+  double re, im, pw;
+};
+
+__device__ __forceinline__ void overlap_add(OvAcc& acc, float2 val, float2 phi) {
+  const double vx = val.x, vy = val.y, px = phi.x, py = phi.y;
+  acc.re = fma(vx, px, fma(vy, py, acc.re));
+  acc.im = fma(vy, px, fma(-vx, py, acc.im));
+  acc.pw = fma(vx, vx, fma(vy, vy, acc.pw));
+}
+
 // Rows of the R2 epilogue held in shared memory ([ROWS][nx] each, sample i = rr nx + x): the
 // accumulators of a group (intensity, modulation-gradient partials), written back once after the
 // group's last field, and the planes the epilogue reads (mask factors, the saved modulation input).
@@ -608,10 +621,15 @@ __device__ __forceinline__ float2 mod_value_planes(const EpiPlanes& e, uint32_t 
 // Epilogue of one output sample val = psi(y, x) of field f in group g, from staged planes.
 template <int KIND>
 __device__ __forceinline__ void epilogue_planes(const PassParams& p, const FieldSet& fs, const EpiPlanes& e, int f,
-                                                bool first, int y, int x, int i, float2 ly, int2 rg, float2 val) {
+                                                bool first, int y, int x, int i, float2 ly, int2 rg, float2 val,
+                                                OvAcc& acc) {
   const long long idx = (long long)y * p.nx + x;
   const ModDev& m = p.mepi;
-  if constexpr (KIND == EPI_FIELD) {
+  if constexpr (KIND == EPI_OVERLAP) {
+    if (m.flags) val = c_mul(val, mod_value_planes(e, m.flags, m.conj, fs.epi_lx, ly, rg, i, x));
+    if (p.out) p.out[(long long)f * p.out_stride + idx] = val;
+    overlap_add(acc, val, ldg2(p.target + (long long)f * p.target_stride + idx));
+  } else if constexpr (KIND == EPI_FIELD) {
     if (m.flags) val = c_mul(val, mod_value_planes(e, m.flags, m.conj, fs.epi_lx, ly, rg, i, x));
     field_out(p, f)[idx] = val;
   } else if constexpr (KIND == EPI_INTENSITY) {
@@ -645,9 +663,13 @@ __device__ __forceinline__ void epilogue_planes(const PassParams& p, const Field
 // Epilogue of one output sample val = psi(y, x) of field f in group g.
 template <int KIND>
 __device__ __forceinline__ void epilogue(const PassParams& p, const FieldSet& fs, int f, int g, bool first, int y,
-                                         int x, float2 val) {
+                                         int x, float2 val, OvAcc& acc) {
   const long long idx = (long long)y * p.nx + x;
-  if constexpr (KIND == EPI_FIELD) {
+  if constexpr (KIND == EPI_OVERLAP) {
+    if (p.mepi.flags) val = c_mul(val, mod_value(p.mepi, p.mepi.flags, p.mepi.conj, fs.epi_lx, fs.epi_ly, f, y, x, p.nx));
+    if (p.out) p.out[(long long)f * p.out_stride + idx] = val;
+    overlap_add(acc, val, ldg2(p.target + (long long)f * p.target_stride + idx));
+  } else if constexpr (KIND == EPI_FIELD) {
     if (p.mepi.flags) val = c_mul(val, mod_value(p.mepi, p.mepi.flags, p.mepi.conj, fs.epi_lx, fs.epi_ly, f, y, x, p.nx));
     field_out(p, f)[idx] = val;
   } else if constexpr (KIND == EPI_INTENSITY) {
@@ -691,7 +713,7 @@ __device__ __forceinline__ void epilogue(const PassParams& p, const FieldSet& fs
 // sample to the epilogue (one cooperative loop; with padding exactly 2 its trip count is fixed).
 template <class EX, bool X2, int KIND>
 __device__ __forceinline__ void combine_rows(const PassParams& p, const FieldSet& fs, const float2* smem, int f, int g,
-                                             bool first, int y0, int nrows, const EpiPlanes* ep) {
+                                             bool first, int y0, int nrows, const EpiPlanes* ep, OvAcc& acc) {
   using SH = RowShape<EX>;
   constexpr int M = EX::M, ROWS = SH::ROWS, NT = SH::THREADS;
   if (ep) {
@@ -713,7 +735,8 @@ __device__ __forceinline__ void combine_rows(const PassParams& p, const FieldSet
         }
         const float2 o = smem[(ROWS + rr) * M + pos];
         const float2 ev = smem[rr * M + pos];
-        epilogue_planes<KIND>(p, fs, *ep, f, first, y, x, rr * p.nx + x, ly, rg, upper ? c_sub(ev, o) : c_add(ev, o));
+        epilogue_planes<KIND>(p, fs, *ep, f, first, y, x, rr * p.nx + x, ly, rg, upper ? c_sub(ev, o) : c_add(ev, o),
+                              acc);
       }
     }
     return;
@@ -731,7 +754,7 @@ __device__ __forceinline__ void combine_rows(const PassParams& p, const FieldSet
     }
     const float2 o = smem[(ROWS + rr) * M + pos];
     const float2 ev = smem[rr * M + pos];
-    epilogue<KIND>(p, fs, f, g, first, y0 + rr, x, upper ? c_sub(ev, o) : c_add(ev, o));
+    epilogue<KIND>(p, fs, f, g, first, y0 + rr, x, upper ? c_sub(ev, o) : c_add(ev, o), acc);
   };
   if constexpr (X2 && M % NT == 0) {
     for (int rr = 0; rr < nrows; ++rr) {
@@ -892,12 +915,34 @@ __global__ void __launch_bounds__(RowShape<EX>::THREADS, RowShape<EX>::MINB_INV)
     __syncthreads();
     // combine the halves over the cropped window, epilogue, coalesced store
     const EpiPlanes* epp = staged ? &ep : nullptr;
+    OvAcc acc{0.0, 0.0, 0.0};
     if (p.epi_kind == EPI_FIELD) {
-      combine_rows<EX, X2, EPI_FIELD>(p, fs, smem, f, g, f == f0, y0, nrows, epp);
+      combine_rows<EX, X2, EPI_FIELD>(p, fs, smem, f, g, f == f0, y0, nrows, epp, acc);
     } else if (p.epi_kind == EPI_INTENSITY) {
-      combine_rows<EX, X2, EPI_INTENSITY>(p, fs, smem, f, g, f == f0, y0, nrows, epp);
+      combine_rows<EX, X2, EPI_INTENSITY>(p, fs, smem, f, g, f == f0, y0, nrows, epp, acc);
+    } else if (p.epi_kind == EPI_MODGRAD) {
+      combine_rows<EX, X2, EPI_MODGRAD>(p, fs, smem, f, g, f == f0, y0, nrows, epp, acc);
     } else {
-      combine_rows<EX, X2, EPI_MODGRAD>(p, fs, smem, f, g, f == f0, y0, nrows, epp);
+      combine_rows<EX, X2, EPI_OVERLAP>(p, fs, smem, f, g, f == f0, y0, nrows, epp, acc);
+      // the block's sums in a fixed order: every thread's three values, added by thread 0
+      __syncthreads();
+      double* red = reinterpret_cast<double*>(smem);
+      red[3 * threadIdx.x] = acc.re;
+      red[3 * threadIdx.x + 1] = acc.im;
+      red[3 * threadIdx.x + 2] = acc.pw;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double sr = 0.0, si = 0.0, sp = 0.0;
+        for (int i = 0; i < NT; ++i) {
+          sr += red[3 * i];
+          si += red[3 * i + 1];
+          sp += red[3 * i + 2];
+        }
+        double* out = p.ov_part + ((long long)f * gridDim.x + blockIdx.x) * 3;
+        out[0] = sr;
+        out[1] = si;
+        out[2] = sp;
+      }
     }
     __syncthreads();
   }
