@@ -23,7 +23,9 @@ paper (TorchOptics, arXiv 2411.18591):
 * mutual coherence is modulated by M(r1) M*(r2) (Eq. 12) and propagated with
   h_z on r1 and h_z* on r2 (Eq. 13);
 * polychromatic intensity is the incoherent sum over wavelengths (Eq. 14);
-* the overlap loss is Eq. 7 with the integral as a sum times dx dy, averaged over a batch.
+* the overlap loss is Eq. 7 with the integral as a sum times dx dy, averaged over a batch;
+* polarisation elements act as Jones matrices on (psi_x, psi_y) per pixel (§5.1), the z
+  component of a three-component field passing unchanged.
 
 Readings of points the paper leaves open (each listed in the design doc):
 
@@ -307,6 +309,63 @@ def overlap_loss(field: np.ndarray, target: np.ndarray, dy: float, dx: float):
     loss = float(np.mean(1.0 - np.abs(o) ** 2))
     grad = -(2.0 / b) * o[:, None, None] * t * (dx * dy)
     return loss, grad
+
+
+# ----------------------------------------------------------------------------- polarisation (§5.1)
+
+def jones_matrix_3x3(j2) -> np.ndarray:
+    """A 2 x 2 Jones matrix acting on (psi_x, psi_y), extended to the three field components
+    (x, y, z) with the z component passed unchanged."""
+    m = np.zeros((3, 3), dtype=np.complex128)
+    m[:2, :2] = np.asarray(j2, dtype=np.complex128)
+    m[2, 2] = 1.0
+    return m
+
+
+def linear_polarizer(theta: float) -> np.ndarray:
+    """Transmission axis at angle theta to x: J = u u^T with u = (cos theta, sin theta)."""
+    c, s = math.cos(theta), math.sin(theta)
+    return jones_matrix_3x3([[c * c, c * s], [c * s, s * s]])
+
+
+def circular_polarizer(handedness: int) -> np.ndarray:
+    """Projector on (1, i handedness) / sqrt 2: J = v v^H (handedness +1 or -1)."""
+    v = np.array([1.0, 1j * handedness]) / math.sqrt(2.0)
+    return jones_matrix_3x3(np.outer(v, np.conj(v)))
+
+
+def waveplate(retardance: float, theta: float) -> np.ndarray:
+    """Retarder with its fast axis at theta: J = R(-theta) diag(1, exp(i retardance)) R(theta),
+    R the rotation of the coordinates by theta."""
+    c, s = math.cos(theta), math.sin(theta)
+    r = np.array([[c, s], [-s, c]])
+    return jones_matrix_3x3(r.T @ np.diag([1.0, np.exp(1j * retardance)]) @ r)
+
+
+def jones_modulate(field: np.ndarray, jones: np.ndarray) -> np.ndarray:
+    """|psi_out(r)> = J(r) |psi_in(r)> (§5.1) on fields [..., 3, ny, nx]; J is [3, 3] (uniform) or
+    [3, 3, ny, nx] (spatially varying)."""
+    f = np.asarray(field, dtype=np.complex128)
+    j = np.asarray(jones, dtype=np.complex128)
+    if j.ndim == 2:
+        return np.einsum("ij,...jyx->...iyx", j, f)
+    return np.einsum("ijyx,...jyx->...iyx", j, f)
+
+
+def grad_jones(field: np.ndarray, jones: np.ndarray, g_out: np.ndarray):
+    """Backward of jones_modulate: g_in = J^H g_out per pixel, and g_J = sum over the leading
+    axes of g_out conj(psi_in)^T (per pixel), in the real-loss convention."""
+    f = np.asarray(field, dtype=np.complex128)
+    g = np.asarray(g_out, dtype=np.complex128)
+    j = np.asarray(jones, dtype=np.complex128)
+    if j.ndim == 2:
+        g_in = np.einsum("ji,...jyx->...iyx", np.conj(j), g)
+    else:
+        g_in = np.einsum("jiyx,...jyx->...iyx", np.conj(j), g)
+    gb = g.reshape((-1,) + g.shape[-3:])
+    fb = f.reshape((-1,) + f.shape[-3:])
+    g_j = np.einsum("biyx,bjyx->ijyx", gb, np.conj(fb))
+    return g_in, g_j
 
 
 # ----------------------------------------------------------------------------- coherence

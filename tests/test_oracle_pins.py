@@ -330,6 +330,80 @@ def test_overlap_loss_gradient_by_finite_differences():
     assert np.max(np.abs(fd - g_phi.reshape(-1)[idx])) < 1e-6 * np.max(np.abs(fd))
 
 
+def _golden(name):
+    import os
+    rows = []
+    with open(os.path.join(os.path.dirname(__file__), "golden", name)) as fh:
+        for line in fh:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append(line.split())
+    return rows
+
+
+def test_polarizer_powers_printed_in_the_paper():
+    """Listing 6: a normalised x-polarised field through linear polarisers at 45 and 90 degrees."""
+    n, d = 64, 10e-6
+    f = np.zeros((3, n, n), dtype=np.complex128)
+    f[0] = 1.0
+    f /= math.sqrt(O.power(f, d, d).sum())
+    elems = {"polarizer_45": O.linear_polarizer(math.pi / 4), "polarizer_90": O.linear_polarizer(math.pi / 2)}
+    for seq, val in _golden("polarizer_powers.txt"):
+        g = f
+        if seq != "none":
+            for e in seq.split(","):
+                g = O.jones_modulate(g, elems[e])
+        assert O.power(g, d, d).sum() == pytest.approx(float(val), abs=1e-12)
+
+
+def test_malus_law_and_waveplates():
+    """Malus's law cos^2; a quarter-wave plate at 45 degrees turns x into circular light (equal
+    powers, phase +-pi/2 between y and x); a half-wave plate at theta rotates x to 2 theta; a
+    circular polariser passes half of linear light."""
+    f = np.zeros((3, 1, 1), dtype=np.complex128)
+    f[0] = 1.0
+    for th in (0.1, 0.7, 1.3):
+        assert np.sum(np.abs(O.jones_modulate(f, O.linear_polarizer(th))) ** 2) == pytest.approx(math.cos(th) ** 2, abs=1e-14)
+    q = O.jones_modulate(f, O.waveplate(math.pi / 2, math.pi / 4))[:, 0, 0]
+    assert abs(abs(q[0]) - abs(q[1])) < 1e-14 and abs(abs(np.angle(q[1] / q[0])) - math.pi / 2) < 1e-14
+    th = 0.3
+    h = O.jones_modulate(f, O.waveplate(math.pi, th))[:, 0, 0]
+    assert abs(abs(h[0]) - abs(math.cos(2 * th))) < 1e-14 and abs(abs(h[1]) - abs(math.sin(2 * th))) < 1e-14
+    for hand in (1, -1):
+        assert np.sum(np.abs(O.jones_modulate(f, O.circular_polarizer(hand))) ** 2) == pytest.approx(0.5, abs=1e-14)
+        v = O.jones_modulate(O.jones_modulate(f, O.circular_polarizer(hand)), O.circular_polarizer(-hand))
+        assert np.sum(np.abs(v) ** 2) < 1e-28
+
+
+def test_jones_backward_by_finite_differences():
+    rng_f = to_c64(normal(61, (2, 3, 4, 5)) + 1j * normal(62, (2, 3, 4, 5))).astype(np.complex128)
+    jm = to_c64(normal(63, (3, 3, 4, 5)) + 1j * normal(64, (3, 3, 4, 5))).astype(np.complex128)
+    w = to_c64(normal(65, (2, 3, 4, 5)) + 1j * normal(66, (2, 3, 4, 5))).astype(np.complex128)
+
+    def loss(jr, ji, fr, fi):
+        out = O.jones_modulate(fr + 1j * fi, jr + 1j * ji)
+        return float(np.real(np.sum(np.conj(w) * out)))  # L = Re <w, out>, so dL/dout = w
+
+    g_in, g_j = O.grad_jones(rng_f, jm, w)
+    h = 1e-6
+    for idx in [(0, 1, 2, 3), (2, 2, 0, 0), (1, 0, 3, 4)]:
+        for part, g in ((0, g_j.real), (1, g_j.imag)):
+            a = [jm.real.copy(), jm.imag.copy()]
+            a[part][idx] += h
+            lp = loss(a[0], a[1], rng_f.real, rng_f.imag)
+            a[part][idx] -= 2 * h
+            lm = loss(a[0], a[1], rng_f.real, rng_f.imag)
+            assert (lp - lm) / (2 * h) == pytest.approx(g[idx], rel=1e-6, abs=1e-9)
+    for idx in [(0, 1, 2, 3), (1, 2, 0, 4)]:
+        for part, g in ((0, g_in.real), (1, g_in.imag)):
+            a = [rng_f.real.copy(), rng_f.imag.copy()]
+            a[part][idx] += h
+            lp = loss(jm.real, jm.imag, a[0], a[1])
+            a[part][idx] -= 2 * h
+            lm = loss(jm.real, jm.imag, a[0], a[1])
+            assert (lp - lm) / (2 * h) == pytest.approx(g[idx], rel=1e-6, abs=1e-9)
+
+
 # ----------------------------------------------------------------------------- coherence
 
 def test_gsm_spreading_mandel_wolf():
