@@ -278,6 +278,29 @@ top_status top_overlap_loss(top_handle h, const top_grid* g, const double* overl
 top_status top_mse_loss(top_handle h, int64_t n, const float* intensity, const float* target, double* loss,
                         float* grad, void* stream);
 
+/* ---------------------------------------------------------------- polarisation (§5.1) */
+
+/* Jones-matrix modulation |psi_out(r)> = J(r) |psi_in(r)> of polarised fields with three
+ * components (x, y, z). Field index b = (o * 3 + c) * inner + i holds component c of polarised
+ * field (o, i): g->batch = 3 * inner * (number of polarised fields); inner = 1 is the
+ * [fields][3][ny][nx] layout, inner = W the (object, component, wavelength) order of a
+ * polychromatic batch. J: device complex64 [3][3][ny][nx] (spatially varying, row-major
+ * matrix index) or NULL, then j_uniform: host double[18], one 3x3 matrix row-major as
+ * (re, im) pairs. A 2x2 Jones matrix acts on (x, y) with J_zz = 1 and zero z couplings.
+ * in == out allowed. */
+top_status top_jones(top_handle h, const top_grid* g, int64_t inner, const void* J, const double* j_uniform,
+                     const void* in, void* out, void* stream);
+
+/* Backward of top_jones: grad_in = J^H grad_out per pixel (grad_in may be NULL, must not
+ * alias grad_out) and, for spatially varying J only, grad_J = sum over the polarised fields of
+ * grad_out conj(saved_in)^T per pixel (device complex64 [3][3][ny][nx], or NULL), summed in
+ * field order. */
+top_status top_jones_backward(top_handle h, const top_grid* g, int64_t inner, const void* J, const double* j_uniform,
+                              const void* saved_in, const void* grad_out, void* grad_in, void* grad_J, void* stream);
+
+/* Power of every field, sum |psi_b|^2 dx dy (device double[batch]; float64, fixed order). */
+top_status top_field_power(top_handle h, const top_grid* g, const void* field, double* power, void* stream);
+
 /* ---------------------------------------------------------------- mutual coherence (§5.2) */
 
 /* Gamma_out = P_z (M(r1) M*(r2) Gamma_in) P_z^H  (Eq. 12 then Eq. 13): h_z acts on

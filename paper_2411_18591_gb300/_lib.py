@@ -75,6 +75,9 @@ SIGNATURES = {
     "top_modulate": (C.c_int, [_P, _GRID, _MOD, _P, _P, _D, _I64, _P]),
     "top_modulate_backward": (C.c_int, [_P, _GRID, _MOD, _P, _P, _GRADS, _D, _I64, _P]),
     "top_mse_loss": (C.c_int, [_P, _I64, _P, _P, _P, _P, _P]),
+    "top_jones": (C.c_int, [_P, _GRID, _I64, _P, _D, _P, _P, _P]),
+    "top_jones_backward": (C.c_int, [_P, _GRID, _I64, _P, _D, _P, _P, _P, _P, _P]),
+    "top_field_power": (C.c_int, [_P, _GRID, _P, _P, _P]),
     "top_propagate_overlap": (C.c_int, [_P, _GRID, _P, _P, _P, _I64, _P, _P, _D, _D, _I64, _MOD, _MOD, _P]),
     "top_overlap_loss": (C.c_int, [_P, _GRID, _P, _P, _I64, _P, _P, _P]),
     "top_propagate_coherence": (C.c_int, [_P, _GRID, _P, _P, _D, _D, _MOD, _P]),

@@ -194,6 +194,93 @@ def top_overlap_loss(overlap: torch.Tensor, target: torch.Tensor, batch: int, ny
     return loss[0], grad
 
 
+# ----------------------------------------------------------------------------- polarisation
+
+
+def jones_3x3(j2) -> "np.ndarray":
+    """A 2x2 Jones matrix on (x, y) extended to (x, y, z) with the z component unchanged."""
+    import numpy as np
+    m = np.zeros((3, 3), dtype=np.complex128)
+    m[:2, :2] = np.asarray(j2, dtype=np.complex128)
+    m[2, 2] = 1.0
+    return m
+
+
+def linear_polarizer(theta: float):
+    """Linear polariser with its transmission axis at theta to x (§5.1)."""
+    import math
+    c, s = math.cos(theta), math.sin(theta)
+    return jones_3x3([[c * c, c * s], [c * s, s * s]])
+
+
+def circular_polarizer(handedness: int = 1):
+    """Circular polariser passing (1, i handedness) / sqrt 2."""
+    import math
+    import numpy as np
+    v = np.array([1.0, 1j * handedness]) / math.sqrt(2.0)
+    return jones_3x3(np.outer(v, np.conj(v)))
+
+
+def waveplate(retardance: float, theta: float = 0.0):
+    """Waveplate of the given retardance with its fast axis at theta (quarter-wave: pi/2, half-wave: pi)."""
+    import math
+    import numpy as np
+    c, s = math.cos(theta), math.sin(theta)
+    r = np.array([[c, s], [-s, c]])
+    return jones_3x3(r.T @ np.diag([1.0, np.exp(1j * retardance)]) @ r)
+
+
+def _jones_args(jones):
+    if isinstance(jones, torch.Tensor):
+        _field(jones, "jones")
+        return jones.data_ptr(), None
+    import numpy as np
+    j = np.asarray(jones, dtype=np.complex128).reshape(9)
+    return None, doubles([v for z in j for v in (z.real, z.imag)])
+
+
+def top_jones(field: torch.Tensor, jones, inner: int = 1, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """J |psi> per pixel on three-component fields. ``field``: complex64 [..., ny, nx] with
+    3 * inner * K leading entries (component c of polarised field (o, i) at (o 3 + c) inner + i).
+    ``jones``: a 3x3 matrix (uniform) or a complex64 [3, 3, ny, nx] tensor (spatially varying)."""
+    _field(field, "field")
+    ny, nx = field.shape[-2:]
+    b = field.numel() // (ny * nx)
+    out = torch.empty_like(field) if out is None else _field(out, "out")
+    jp, ju = _jones_args(jones)
+    g = make_grid(b, ny, nx, 1.0, 1.0)
+    check(_lib.load().top_jones(handle(field.device), C.byref(g), inner, jp, ju, field.data_ptr(), out.data_ptr(),
+                                _stream(field)))
+    return out
+
+
+def top_jones_backward(saved_in: torch.Tensor, grad_out: torch.Tensor, jones, inner: int = 1, want_grad_in: bool = True,
+                       want_grad_jones: bool = False):
+    """(grad_in, grad_jones) of top_jones; grad_jones only for a spatially varying [3, 3, ny, nx] tensor."""
+    _field(grad_out, "grad_out")
+    ny, nx = grad_out.shape[-2:]
+    b = grad_out.numel() // (ny * nx)
+    gin = torch.empty_like(grad_out) if want_grad_in else None
+    gj = torch.empty((3, 3, ny, nx), dtype=torch.complex64, device=grad_out.device) if want_grad_jones else None
+    jp, ju = _jones_args(jones)
+    g = make_grid(b, ny, nx, 1.0, 1.0)
+    check(_lib.load().top_jones_backward(handle(grad_out.device), C.byref(g), inner, jp, ju, _ptr(saved_in),
+                                         grad_out.data_ptr(), _ptr(gin), _ptr(gj), _stream(grad_out)))
+    return gin, gj
+
+
+def top_field_power(field: torch.Tensor, dy: float, dx: float) -> torch.Tensor:
+    """sum |psi_b|^2 dx dy for every [ny, nx] plane of ``field`` (float64 device tensor)."""
+    _field(field, "field")
+    ny, nx = field.shape[-2:]
+    b = field.numel() // (ny * nx)
+    power = torch.empty((b,), dtype=torch.float64, device=field.device)
+    g = make_grid(b, ny, nx, dy, dx)
+    check(_lib.load().top_field_power(handle(field.device), C.byref(g), field.data_ptr(), power.data_ptr(),
+                                      _stream(field)))
+    return power
+
+
 def top_propagate_ragged(fields: Sequence[torch.Tensor], spacings, lams, zs, pad: float = 2.0, method="as",
                          backward: bool = False, out: Optional[Sequence[torch.Tensor]] = None):
     """Propagate (or back-propagate) fields of different sizes in one call: field i ([ny, nx]

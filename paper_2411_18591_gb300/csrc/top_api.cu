@@ -1227,6 +1227,85 @@ top_status top_overlap_loss(top_handle h, const top_grid* g, const double* overl
   });
 }
 
+static top_status jones_common(const top_grid* g, int64_t inner, const void* J, const double* ju, Jones3* m,
+                               int64_t* groups) {
+  if (!g) return fail(TOP_ERR_INVALID_ARG, "grid is NULL");
+  if (g->batch < 1 || g->ny < 1 || g->nx < 1) return fail(TOP_ERR_INVALID_ARG, "batch, ny and nx must be >= 1");
+  if (inner < 1 || g->batch % (3 * inner) != 0)
+    return fail(TOP_ERR_INVALID_ARG, "batch (%lld) must be 3 * inner (%lld) * the number of polarised fields",
+                (long long)g->batch, (long long)inner);
+  *groups = g->batch / (3 * inner);
+  if (J) {
+    TOP_TRY(check_ptr(J, "Jones planes"));
+  } else {
+    if (!ju) return fail(TOP_ERR_INVALID_ARG, "give either Jones planes or a uniform Jones matrix");
+    for (int k = 0; k < 9; ++k) {
+      if (!std::isfinite(ju[2 * k]) || !std::isfinite(ju[2 * k + 1])) return fail(TOP_ERR_INVALID_ARG, "Jones matrix entries must be finite");
+      m->m[k] = make_float2(float(ju[2 * k]), float(ju[2 * k + 1]));
+    }
+  }
+  return TOP_OK;
+}
+
+top_status top_jones(top_handle h, const top_grid* g, int64_t inner, const void* J, const double* j_uniform,
+                     const void* in, void* out, void* stream) {
+  if (!h) return fail(TOP_ERR_INVALID_ARG, "handle is NULL");
+  Jones3 m{};
+  int64_t groups = 0;
+  TOP_TRY(jones_common(g, inner, J, j_uniform, &m, &groups));
+  TOP_TRY(check_ptr(in, "input field"));
+  TOP_TRY(check_ptr(out, "output field"));
+  TOP_TRY(bind(h));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  return timed(h, KK_AUX, st, "Jones modulation", [&] {
+    return launch_jones(static_cast<const float2*>(in), static_cast<float2*>(out), groups, inner,
+                        (long long)g->ny * g->nx, static_cast<const float2*>(J), m, st);
+  });
+}
+
+top_status top_jones_backward(top_handle h, const top_grid* g, int64_t inner, const void* J, const double* j_uniform,
+                              const void* saved_in, const void* grad_out, void* grad_in, void* grad_J, void* stream) {
+  if (!h) return fail(TOP_ERR_INVALID_ARG, "handle is NULL");
+  Jones3 m{};
+  int64_t groups = 0;
+  TOP_TRY(jones_common(g, inner, J, j_uniform, &m, &groups));
+  TOP_TRY(check_ptr(grad_out, "grad_out"));
+  if (grad_in) TOP_TRY(check_ptr(grad_in, "grad_in"));
+  if (grad_J) {
+    if (!J) return fail(TOP_ERR_INVALID_ARG, "grad_J needs spatially varying Jones planes");
+    TOP_TRY(check_ptr(grad_J, "grad_J"));
+    TOP_TRY(check_ptr(saved_in, "saved_in"));
+  }
+  if (grad_in && grad_in == grad_out) return fail(TOP_ERR_INVALID_ARG, "grad_in must not alias grad_out");
+  TOP_TRY(bind(h));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  return timed(h, KK_AUX, st, "Jones backward", [&] {
+    return launch_jones_backward(static_cast<const float2*>(saved_in), static_cast<const float2*>(grad_out),
+                                 static_cast<float2*>(grad_in), static_cast<float2*>(grad_J), groups, inner,
+                                 (long long)g->ny * g->nx, static_cast<const float2*>(J), m, st);
+  });
+}
+
+top_status top_field_power(top_handle h, const top_grid* g, const void* field, double* power, void* stream) {
+  if (!h) return fail(TOP_ERR_INVALID_ARG, "handle is NULL");
+  if (!g) return fail(TOP_ERR_INVALID_ARG, "grid is NULL");
+  if (g->batch < 1 || g->ny < 1 || g->nx < 1) return fail(TOP_ERR_INVALID_ARG, "batch, ny and nx must be >= 1");
+  if (!(std::isfinite(g->dy) && g->dy > 0) || !(std::isfinite(g->dx) && g->dx > 0))
+    return fail(TOP_ERR_INVALID_ARG, "spacing must be finite and > 0");
+  TOP_TRY(check_ptr(field, "field"));
+  if (!power || (reinterpret_cast<uintptr_t>(power) & 7u)) return fail(TOP_ERR_INVALID_ARG, "power must be a non-NULL, 8-byte aligned device array");
+  TOP_TRY(bind(h));
+  // partial sums in a small region at the end of the workspace
+  const size_t bytes = size_t(g->batch) * kPowerBlocks * sizeof(double) + 256;
+  if (h->ws_bytes < bytes) TOP_TRY(ensure_workspace(h, bytes));
+  double* partial = reinterpret_cast<double*>(static_cast<char*>(h->ws) + h->ws_bytes - size_t(g->batch) * kPowerBlocks * sizeof(double));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  return timed(h, KK_AUX, st, "field power", [&] {
+    return launch_field_power(static_cast<const float2*>(field), g->batch, (long long)g->ny * g->nx, g->dy * g->dx,
+                              partial, power, st);
+  });
+}
+
 top_status top_propagate_ragged(top_handle h, int count, const top_grid* grids, const void* const* in,
                                 void* const* out, const double* lambda, const double* z, int backward, void* stream) {
   if (!h) return fail(TOP_ERR_INVALID_ARG, "handle is NULL");

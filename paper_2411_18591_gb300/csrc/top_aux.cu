@@ -264,6 +264,133 @@ cudaError_t launch_overlap_loss(const double* overlap, long long batch, const fl
   return cudaGetLastError();
 }
 
+// ----------------------------------------------------------------------------- Jones matrices
+
+__device__ __forceinline__ float2 jones_at(const float2* J, const Jones3& ju, int k, long long px, long long plane) {
+  return J ? ldg2(J + k * plane + px) : ju.m[k];
+}
+
+__global__ void __launch_bounds__(256) k_jones(const float2* in, float2* out, long long groups, long long inner,
+                                               long long plane, const float2* J, const Jones3 ju) {
+  const long long total = groups * inner * plane;
+  for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < total; j += (long long)gridDim.x * blockDim.x) {
+    const long long px = j % plane, q = j / plane;
+    const long long o = q / inner, i = q - o * inner;
+    const long long base = (o * 3 * inner + i) * plane + px, cs = inner * plane;
+    const float2 a0 = ldg2(in + base), a1 = ldg2(in + base + cs), a2 = ldg2(in + base + 2 * cs);
+    float2 r[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      r[c] = c_add(c_add(c_mul(jones_at(J, ju, 3 * c, px, plane), a0), c_mul(jones_at(J, ju, 3 * c + 1, px, plane), a1)),
+                   c_mul(jones_at(J, ju, 3 * c + 2, px, plane), a2));
+    }
+    out[base] = r[0];
+    out[base + cs] = r[1];
+    out[base + 2 * cs] = r[2];
+  }
+}
+
+cudaError_t launch_jones(const float2* in, float2* out, long long groups, long long inner, long long plane,
+                         const float2* J, Jones3 ju, cudaStream_t s) {
+  const long long n = groups * inner * plane;
+  if (n == 0) return cudaSuccess;
+  const long long blocks = (n + 255) / 256;
+  TOP_LAUNCH(k_jones, unsigned(blocks < 152 * 32 ? blocks : 152 * 32), 256, 0, s, in, out, groups, inner, plane, J, ju);
+  return cudaGetLastError();
+}
+
+// one thread per pixel: grad_in for every polarised field, grad_J summed over them in order
+__global__ void __launch_bounds__(256) k_jones_backward(const float2* in, const float2* gout, float2* gin, float2* gJ,
+                                                        long long groups, long long inner, long long plane,
+                                                        const float2* J, const Jones3 ju) {
+  const long long px = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (px >= plane) return;
+  float2 acc[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) acc[k] = make_float2(0.f, 0.f);
+  const long long cs = inner * plane;
+  for (long long o = 0; o < groups; ++o) {
+    for (long long i = 0; i < inner; ++i) {
+      const long long base = (o * 3 * inner + i) * plane + px;
+      const float2 g0 = ldg2(gout + base), g1 = ldg2(gout + base + cs), g2 = ldg2(gout + base + 2 * cs);
+      if (gJ) {
+        const float2 x[3] = {ldg2(in + base), ldg2(in + base + cs), ldg2(in + base + 2 * cs)};
+        const float2 g[3] = {g0, g1, g2};
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+          for (int b = 0; b < 3; ++b) acc[3 * a + b] = c_add(acc[3 * a + b], c_mulc(g[a], x[b]));
+      }
+      if (gin) {
+        float2 r[3];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+          // (J^H g)_b = sum_a conj(J_ab) g_a
+          r[b] = c_add(c_add(c_mul(c_conj(jones_at(J, ju, b, px, plane)), g0),
+                             c_mul(c_conj(jones_at(J, ju, 3 + b, px, plane)), g1)),
+                       c_mul(c_conj(jones_at(J, ju, 6 + b, px, plane)), g2));
+        }
+        gin[base] = r[0];
+        gin[base + cs] = r[1];
+        gin[base + 2 * cs] = r[2];
+      }
+    }
+  }
+  if (gJ) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) gJ[k * plane + px] = acc[k];
+  }
+}
+
+cudaError_t launch_jones_backward(const float2* in, const float2* gout, float2* gin, float2* gJ, long long groups,
+                                  long long inner, long long plane, const float2* J, Jones3 ju, cudaStream_t s) {
+  if (plane == 0) return cudaSuccess;
+  TOP_LAUNCH(k_jones_backward, unsigned((plane + 255) / 256), 256, 0, s, in, gout, gin, gJ, groups, inner, plane, J, ju);
+  return cudaGetLastError();
+}
+
+// power: kPowerBlocks blocks per field, each a float64 grid-stride sum and a fixed-order tree
+__global__ void __launch_bounds__(256) k_power_partial(const float2* field, long long plane, double* partial) {
+  __shared__ double red[256];
+  const long long b = blockIdx.y;
+  const float2* f = field + b * plane;
+  double acc = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < plane; i += (long long)gridDim.x * blockDim.x) {
+    const float2 v = ldg2(f + i);
+    acc = fma(double(v.x), double(v.x), fma(double(v.y), double(v.y), acc));
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[b * gridDim.x + blockIdx.x] = red[0];
+}
+
+__global__ void k_power_finish(const double* partial, long long batch, int nblk, double area, double* power) {
+  const long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= batch) return;
+  double s = 0.0;
+  for (int k = 0; k < nblk; ++k) s += partial[b * nblk + k];
+  power[b] = s * area;
+}
+
+cudaError_t launch_field_power(const float2* field, long long batch, long long plane, double area, double* partial,
+                               double* power, cudaStream_t s) {
+  if (batch == 0) return cudaSuccess;
+  cudaError_t e = cudaSuccess;
+  for (long long b0 = 0; b0 < batch && e == cudaSuccess; b0 += 65535) {
+    const long long nb = batch - b0 < 65535 ? batch - b0 : 65535;
+    dim3 grid(kPowerBlocks, unsigned(nb));
+    TOP_LAUNCH(k_power_partial, grid, 256, 0, s, field + b0 * plane, plane, partial + b0 * kPowerBlocks);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) return e;
+  TOP_LAUNCH(k_power_finish, unsigned((batch + 255) / 256), 256, 0, s, partial, batch, kPowerBlocks, area, power);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_transfer_table(float2* hq, int Py, int Px, double dy, double dx, double lam, double z, int method,
                                   cudaStream_t s) {
   const int my = Py / 2;

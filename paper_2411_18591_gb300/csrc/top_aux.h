@@ -28,6 +28,21 @@ cudaError_t launch_overlap_finish(const double* part, int ntiles, int nfields, d
 // L = mean_b (1 - |O_b|^2) into loss[0] and, when grad is non-null, grad_b = -(2/B) O_b phi_b area.
 cudaError_t launch_overlap_loss(const double* overlap, long long batch, const float2* target, long long target_stride,
                                 long long plane, double area, double* loss, float2* grad, cudaStream_t s);
+// Jones matrices (§5.1) on three-component fields: field (o 3 + c) inner + i holds component c of
+// polarised field (o, i). J: per-pixel planes [3][3][plane] or, when null, the uniform matrix ju.
+struct Jones3 {
+  float2 m[9];
+};
+cudaError_t launch_jones(const float2* in, float2* out, long long groups, long long inner, long long plane,
+                         const float2* J, Jones3 ju, cudaStream_t s);
+// grad_in = J^H grad_out (optional) and grad_J = sum over the polarised fields of grad_out conj(in)^T
+// per pixel (optional, per-pixel J only), the sum in field order.
+cudaError_t launch_jones_backward(const float2* in, const float2* gout, float2* gin, float2* gJ, long long groups,
+                                  long long inner, long long plane, const float2* J, Jones3 ju, cudaStream_t s);
+// power[b] = area sum |field_b|^2 (float64, fixed order); partial: batch * kPowerBlocks doubles.
+constexpr int kPowerBlocks = 64;
+cudaError_t launch_field_power(const float2* field, long long batch, long long plane, double area, double* partial,
+                               double* power, cudaStream_t s);
 // Quadrant table of H / (Py Px) for one (lambda, z) in the FieldSet::hq layout (float64 arithmetic).
 cudaError_t launch_transfer_table(float2* hq, int Py, int Px, double dy, double dx, double lam, double z, int method,
                                   cudaStream_t s);
