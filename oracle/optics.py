@@ -25,7 +25,9 @@ paper (TorchOptics, arXiv 2411.18591):
 * polychromatic intensity is the incoherent sum over wavelengths (Eq. 14);
 * the overlap loss is Eq. 7 with the integral as a sum times dx dy, averaged over a batch;
 * polarisation elements act as Jones matrices on (psi_x, psi_y) per pixel (§5.1), the z
-  component of a three-component field passing unchanged.
+  component of a three-component field passing unchanged;
+* a field moves between grids of different spacing by nearest or bilinear interpolation of
+  the centred sample positions (§3), samples outside the input grid counting as zero.
 
 Readings of points the paper leaves open (each listed in the design doc):
 
@@ -309,6 +311,53 @@ def overlap_loss(field: np.ndarray, target: np.ndarray, dy: float, dx: float):
     loss = float(np.mean(1.0 - np.abs(o) ** 2))
     grad = -(2.0 / b) * o[:, None, None] * t * (dx * dy)
     return loss, grad
+
+
+# ----------------------------------------------------------------------------- unequal spacings (§3)
+
+NEAREST = 0
+BILINEAR = 1
+
+
+def resample_weights(n_in: int, d_in: float, n_out: int, d_out: float, mode: int) -> np.ndarray:
+    """Interpolation matrix [n_out, n_in] along one axis between centred grids (sample i at
+    (i - (n-1)/2) d): output sample j sits at fractional input index
+    u = (j - (n_out-1)/2) d_out / d_in + (n_in-1)/2. NEAREST takes sample floor(u + 1/2); BILINEAR
+    weighs floor(u) by 1 - (u - floor(u)) and floor(u) + 1 by u - floor(u). Samples outside the
+    input grid count as zero."""
+    w = np.zeros((n_out, n_in))
+    for j in range(n_out):
+        u = (j - (n_out - 1) / 2.0) * d_out / d_in + (n_in - 1) / 2.0
+        if mode == NEAREST:
+            i = math.floor(u + 0.5)
+            if 0 <= i < n_in:
+                w[j, i] = 1.0
+        else:
+            i0 = math.floor(u)
+            t = u - i0
+            for i, c in ((i0, 1.0 - t), (i0 + 1, t)):
+                if 0 <= i < n_in and c != 0.0:
+                    w[j, i] += c
+    return w
+
+
+def resample(field: np.ndarray, dy: float, dx: float, ny_out: int, nx_out: int, dy_out: float, dx_out: float,
+             mode: int = BILINEAR) -> np.ndarray:
+    """A field on one centred grid interpolated onto another (§3: propagation keeps the input
+    spacing, then the result is interpolated onto the output grid), separably along y and x."""
+    f = _as_batch(field)
+    wy = resample_weights(f.shape[-2], dy, ny_out, dy_out, mode)
+    wx = resample_weights(f.shape[-1], dx, nx_out, dx_out, mode)
+    return np.einsum("ay,byx,cx->bac", wy, f, wx)
+
+
+def resample_adjoint(g: np.ndarray, ny_in: int, nx_in: int, dy: float, dx: float, dy_out: float, dx_out: float,
+                     mode: int = BILINEAR) -> np.ndarray:
+    """Backward of ``resample``: the transposed interpolation."""
+    gb = _as_batch(g)
+    wy = resample_weights(ny_in, dy, gb.shape[-2], dy_out, mode)
+    wx = resample_weights(nx_in, dx, gb.shape[-1], dx_out, mode)
+    return np.einsum("ay,bac,cx->byx", wy, gb, wx)
 
 
 # ----------------------------------------------------------------------------- polarisation (§5.1)

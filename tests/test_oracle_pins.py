@@ -404,6 +404,31 @@ def test_jones_backward_by_finite_differences():
             assert (lp - lm) / (2 * h) == pytest.approx(g[idx], rel=1e-6, abs=1e-9)
 
 
+def test_bilinear_resampling_reproduces_bilinear_functions():
+    """Bilinear interpolation is exact for a + b x + c y + e x y inside the input grid; nearest
+    picks the closest sample; equal grids give the identity; the adjoint identity holds."""
+    ny, nx, dy, dx = 20, 30, 3e-6, 2e-6
+    ny2, nx2, dy2, dx2 = 17, 23, 2.5e-6, 1.7e-6
+    x = O.coords(nx, dx)[None, :]
+    y = O.coords(ny, dy)[:, None]
+    fn = lambda xx, yy: (0.3 + 2e5 * xx - 1e5 * yy + 4e9 * xx * yy) * (1 + 0.5j)
+    out = O.resample(fn(x, y), dy, dx, ny2, nx2, dy2, dx2, O.BILINEAR)[0]
+    x2 = O.coords(nx2, dx2)[None, :]
+    y2 = O.coords(ny2, dy2)[:, None]
+    assert np.max(np.abs(out - fn(x2, y2))) < 1e-12
+    near = O.resample(fn(x, y), dy, dx, ny2, nx2, dy2, dx2, O.NEAREST)[0]
+    jx = np.floor(x2[0] / dx + (nx - 1) / 2 + 0.5).astype(int)
+    jy = np.floor(y2[:, 0] / dy + (ny - 1) / 2 + 0.5).astype(int)
+    assert np.array_equal(near, fn(x, y)[np.ix_(jy, jx)])
+    f = to_c64(normal(71, (2, ny, nx)) + 1j * normal(72, (2, ny, nx))).astype(np.complex128)
+    assert np.array_equal(O.resample(f, dy, dx, ny, nx, dy, dx), f)
+    g = to_c64(normal(73, (2, ny2, nx2)) + 1j * normal(74, (2, ny2, nx2))).astype(np.complex128)
+    for mode in (O.NEAREST, O.BILINEAR):
+        a = np.vdot(g, O.resample(f, dy, dx, ny2, nx2, dy2, dx2, mode))
+        b = np.vdot(O.resample_adjoint(g, ny, nx, dy, dx, dy2, dx2, mode), f)
+        assert abs(a - b) < 1e-12 * abs(a)
+
+
 # ----------------------------------------------------------------------------- coherence
 
 def test_gsm_spreading_mandel_wolf():
