@@ -278,6 +278,21 @@ top_status top_overlap_loss(top_handle h, const top_grid* g, const double* overl
 top_status top_mse_loss(top_handle h, int64_t n, const float* intensity, const float* target, double* loss,
                         float* grad, void* stream);
 
+/* ---------------------------------------------------------------- unequal spacings (§3) */
+
+typedef enum top_interp { TOP_NEAREST = 0, TOP_BILINEAR = 1 } top_interp;
+
+/* A field on g's centred grid (sample i at (i - (n-1)/2) d) interpolated onto the centred grid
+ * (ny_out, nx_out, dy_out, dx_out), as the paper does after propagating on the input spacing:
+ * output sample j sits at fractional input index u = (j - (n_out-1)/2) d_out / d + (n-1)/2
+ * (float64), TOP_NEAREST takes sample floor(u + 1/2), TOP_BILINEAR weighs floor(u) and
+ * floor(u) + 1 by 1 - t and t (t = u - floor(u)); samples outside the input grid count as zero.
+ * in: complex64 [batch][g->ny][g->nx], out: [batch][ny_out][nx_out] (distinct buffers).
+ * backward != 0 applies the transpose (the gradient): in is then [batch][ny_out][nx_out] and
+ * out [batch][g->ny][g->nx], each input sample gathering its terms in a fixed order. */
+top_status top_resample(top_handle h, const top_grid* g, int ny_out, int nx_out, double dy_out, double dx_out,
+                        int mode, int backward, const void* in, void* out, void* stream);
+
 /* ---------------------------------------------------------------- polarisation (§5.1) */
 
 /* Jones-matrix modulation |psi_out(r)> = J(r) |psi_in(r)> of polarised fields with three

@@ -348,7 +348,7 @@ def resample(field: np.ndarray, dy: float, dx: float, ny_out: int, nx_out: int, 
     f = _as_batch(field)
     wy = resample_weights(f.shape[-2], dy, ny_out, dy_out, mode)
     wx = resample_weights(f.shape[-1], dx, nx_out, dx_out, mode)
-    return np.einsum("ay,byx,cx->bac", wy, f, wx)
+    return wy @ f @ wx.T
 
 
 def resample_adjoint(g: np.ndarray, ny_in: int, nx_in: int, dy: float, dx: float, dy_out: float, dx_out: float,
@@ -357,7 +357,7 @@ def resample_adjoint(g: np.ndarray, ny_in: int, nx_in: int, dy: float, dx: float
     gb = _as_batch(g)
     wy = resample_weights(ny_in, dy, gb.shape[-2], dy_out, mode)
     wx = resample_weights(nx_in, dx, gb.shape[-1], dx_out, mode)
-    return np.einsum("ay,bac,cx->byx", wy, gb, wx)
+    return wy.T @ gb @ wx
 
 
 # ----------------------------------------------------------------------------- polarisation (§5.1)

@@ -14,6 +14,8 @@ TOP_AS = 0
 TOP_FRESNEL_TF = 1
 TOP_DI = 2
 TOP_AUTO = 3
+TOP_NEAREST = 0
+TOP_BILINEAR = 1
 TOP_MOD_COMPLEX = 0x1
 TOP_MOD_AMPLITUDE = 0x2
 TOP_MOD_PHASE = 0x4
@@ -75,6 +77,7 @@ SIGNATURES = {
     "top_modulate": (C.c_int, [_P, _GRID, _MOD, _P, _P, _D, _I64, _P]),
     "top_modulate_backward": (C.c_int, [_P, _GRID, _MOD, _P, _P, _GRADS, _D, _I64, _P]),
     "top_mse_loss": (C.c_int, [_P, _I64, _P, _P, _P, _P, _P]),
+    "top_resample": (C.c_int, [_P, _GRID, C.c_int, C.c_int, C.c_double, C.c_double, C.c_int, C.c_int, _P, _P, _P]),
     "top_jones": (C.c_int, [_P, _GRID, _I64, _P, _D, _P, _P, _P]),
     "top_jones_backward": (C.c_int, [_P, _GRID, _I64, _P, _D, _P, _P, _P, _P, _P]),
     "top_field_power": (C.c_int, [_P, _GRID, _P, _P, _P]),

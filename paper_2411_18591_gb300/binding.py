@@ -194,6 +194,37 @@ def top_overlap_loss(overlap: torch.Tensor, target: torch.Tensor, batch: int, ny
     return loss[0], grad
 
 
+def top_resample(field: torch.Tensor, dy: float, dx: float, ny_out: int, nx_out: int, dy_out: float, dx_out: float,
+                 mode: str = "bilinear") -> torch.Tensor:
+    """Interpolate [..., ny, nx] fields on spacing (dy, dx) onto the centred grid (ny_out, nx_out,
+    dy_out, dx_out) (§3), nearest or bilinear."""
+    _field(field, "field")
+    ny, nx = field.shape[-2:]
+    b = field.numel() // (ny * nx)
+    out = torch.empty(field.shape[:-2] + (ny_out, nx_out), dtype=field.dtype, device=field.device)
+    g = make_grid(b, ny, nx, dy, dx)
+    check(_lib.load().top_resample(handle(field.device), C.byref(g), ny_out, nx_out, dy_out, dx_out, _interp(mode), 0,
+                                   field.data_ptr(), out.data_ptr(), _stream(field)))
+    return out
+
+
+def top_resample_backward(grad_out: torch.Tensor, ny: int, nx: int, dy: float, dx: float, dy_out: float, dx_out: float,
+                          mode: str = "bilinear") -> torch.Tensor:
+    """Gradient of top_resample: from [..., ny_out, nx_out] on (dy_out, dx_out) back to [..., ny, nx] on (dy, dx)."""
+    _field(grad_out, "grad_out")
+    ny_out, nx_out = grad_out.shape[-2:]
+    b = grad_out.numel() // (ny_out * nx_out)
+    out = torch.empty(grad_out.shape[:-2] + (ny, nx), dtype=grad_out.dtype, device=grad_out.device)
+    g = make_grid(b, ny, nx, dy, dx)
+    check(_lib.load().top_resample(handle(grad_out.device), C.byref(g), ny_out, nx_out, dy_out, dx_out, _interp(mode), 1,
+                                   grad_out.data_ptr(), out.data_ptr(), _stream(grad_out)))
+    return out
+
+
+def _interp(mode: str) -> int:
+    return {"nearest": _lib.TOP_NEAREST, "bilinear": _lib.TOP_BILINEAR}[mode]
+
+
 # ----------------------------------------------------------------------------- polarisation
 
 

@@ -1306,6 +1306,26 @@ top_status top_field_power(top_handle h, const top_grid* g, const void* field, d
   });
 }
 
+top_status top_resample(top_handle h, const top_grid* g, int ny_out, int nx_out, double dy_out, double dx_out, int mode,
+                        int backward, const void* in, void* out, void* stream) {
+  if (!h) return fail(TOP_ERR_INVALID_ARG, "handle is NULL");
+  if (!g) return fail(TOP_ERR_INVALID_ARG, "grid is NULL");
+  if (g->batch < 1 || g->ny < 1 || g->nx < 1 || ny_out < 1 || nx_out < 1)
+    return fail(TOP_ERR_INVALID_ARG, "batch and all grid sizes must be >= 1");
+  for (double d : {g->dy, g->dx, dy_out, dx_out})
+    if (!(std::isfinite(d) && d > 0)) return fail(TOP_ERR_INVALID_ARG, "spacings must be finite and > 0");
+  if (mode != TOP_NEAREST && mode != TOP_BILINEAR) return fail(TOP_ERR_INVALID_ARG, "unknown interpolation mode %d", mode);
+  TOP_TRY(check_ptr(in, "input"));
+  TOP_TRY(check_ptr(out, "output"));
+  if (in == out) return fail(TOP_ERR_INVALID_ARG, "input and output must be distinct");
+  TOP_TRY(bind(h));
+  ResampleGeom rg{g->ny, g->nx, ny_out, nx_out, g->dy, g->dx, dy_out, dx_out, mode};
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  return timed(h, KK_AUX, st, "resample", [&] {
+    return launch_resample(static_cast<const float2*>(in), static_cast<float2*>(out), g->batch, rg, backward ? 1 : 0, st);
+  });
+}
+
 top_status top_propagate_ragged(top_handle h, int count, const top_grid* grids, const void* const* in,
                                 void* const* out, const double* lambda, const double* z, int backward, void* stream) {
   if (!h) return fail(TOP_ERR_INVALID_ARG, "handle is NULL");

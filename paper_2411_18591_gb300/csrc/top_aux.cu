@@ -391,6 +391,105 @@ cudaError_t launch_field_power(const float2* field, long long batch, long long p
   return cudaGetLastError();
 }
 
+// ----------------------------------------------------------------------------- resampling
+
+// Output sample j of an axis at fractional input index u = (j - (n_out-1)/2) d_out / d_in +
+// (n_in-1)/2 (float64, each operation rounded on its own): nearest takes floor(u + 1/2) with weight
+// 1, bilinear floor(u) with 1 - t and floor(u) + 1 with t = u - floor(u).
+__device__ __forceinline__ void axis_weights(int j, int n_in, double d_in, int n_out, double d_out, int mode, int& i0,
+                                             float& w0, float& w1) {
+  const double u = __dadd_rn(__ddiv_rn(__dmul_rn(__dsub_rn(double(j), (n_out - 1) / 2.0), d_out), d_in), (n_in - 1) / 2.0);
+  if (mode == 0) {
+    i0 = int(floor(__dadd_rn(u, 0.5)));
+    w0 = 1.f;
+    w1 = 0.f;
+  } else {
+    const double f = floor(u);
+    i0 = int(f);
+    const double t = __dsub_rn(u, f);
+    w0 = float(1.0 - t);
+    w1 = float(t);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_resample(const float2* in, float2* out, ResampleGeom g) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int a = blockIdx.y;
+  const long long b = blockIdx.z;
+  if (c >= g.nx2) return;
+  int iy, ix;
+  float wy0, wy1, wx0, wx1;
+  axis_weights(a, g.ny, g.dy, g.ny2, g.dy2, g.mode, iy, wy0, wy1);
+  axis_weights(c, g.nx, g.dx, g.nx2, g.dx2, g.mode, ix, wx0, wx1);
+  const float2* f = in + b * (long long)g.ny * g.nx;
+  float2 acc = make_float2(0.f, 0.f);
+  const float wy[2] = {wy0, wy1}, wx[2] = {wx0, wx1};
+#pragma unroll
+  for (int p = 0; p < 2; ++p) {
+    const int y = iy + p;
+    if (wy[p] == 0.f || y < 0 || y >= g.ny) continue;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int x = ix + q;
+      if (wx[q] == 0.f || x < 0 || x >= g.nx) continue;
+      acc = c_add(acc, c_scale(ldg2(f + (long long)y * g.nx + x), wy[p] * wx[q]));
+    }
+  }
+  out[(b * g.ny2 + a) * (long long)g.nx2 + c] = acc;
+}
+
+// first output index j whose sample can reach input index i (a safe lower bound, refined by the
+// exact weights in the caller's loop)
+__device__ __forceinline__ int first_reach(int i, int n_in, double d_in, int n_out, double d_out) {
+  const double j = (double(i) - 1.0 - (n_in - 1) / 2.0) * d_in / d_out + (n_out - 1) / 2.0;
+  return max(0, int(floor(j)) - 1);
+}
+
+// transpose: every input sample gathers the output samples that weigh it, in a fixed order
+__global__ void __launch_bounds__(256) k_resample_t(const float2* gout, float2* gin, ResampleGeom g) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y;
+  const long long b = blockIdx.z;
+  if (x >= g.nx) return;
+  const float2* go = gout + b * (long long)g.ny2 * g.nx2;
+  float2 acc = make_float2(0.f, 0.f);
+  for (int a = first_reach(y, g.ny, g.dy, g.ny2, g.dy2); a < g.ny2; ++a) {
+    int iy;
+    float wy0, wy1;
+    axis_weights(a, g.ny, g.dy, g.ny2, g.dy2, g.mode, iy, wy0, wy1);
+    if (iy > y) break;
+    const float wy = iy == y ? wy0 : (iy + 1 == y ? wy1 : 0.f);
+    if (wy == 0.f) continue;
+    for (int c = first_reach(x, g.nx, g.dx, g.nx2, g.dx2); c < g.nx2; ++c) {
+      int ix;
+      float wx0, wx1;
+      axis_weights(c, g.nx, g.dx, g.nx2, g.dx2, g.mode, ix, wx0, wx1);
+      if (ix > x) break;
+      const float wx = ix == x ? wx0 : (ix + 1 == x ? wx1 : 0.f);
+      if (wx == 0.f) continue;
+      acc = c_add(acc, c_scale(ldg2(go + (long long)a * g.nx2 + c), wy * wx));
+    }
+  }
+  gin[(b * g.ny + y) * (long long)g.nx + x] = acc;
+}
+
+cudaError_t launch_resample(const float2* in, float2* out, long long batch, ResampleGeom rg, int transpose,
+                            cudaStream_t s) {
+  for (long long b0 = 0; b0 < batch; b0 += 65535) {
+    const unsigned nb = unsigned(batch - b0 < 65535 ? batch - b0 : 65535);
+    if (!transpose) {
+      dim3 grid(unsigned((rg.nx2 + 255) / 256), unsigned(rg.ny2), nb);
+      TOP_LAUNCH(k_resample, grid, 256, 0, s, in + b0 * (long long)rg.ny * rg.nx, out + b0 * (long long)rg.ny2 * rg.nx2, rg);
+    } else {
+      dim3 grid(unsigned((rg.nx + 255) / 256), unsigned(rg.ny), nb);
+      TOP_LAUNCH(k_resample_t, grid, 256, 0, s, in + b0 * (long long)rg.ny2 * rg.nx2, out + b0 * (long long)rg.ny * rg.nx, rg);
+    }
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 cudaError_t launch_transfer_table(float2* hq, int Py, int Px, double dy, double dx, double lam, double z, int method,
                                   cudaStream_t s) {
   const int my = Py / 2;

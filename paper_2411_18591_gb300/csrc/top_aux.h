@@ -43,6 +43,14 @@ cudaError_t launch_jones_backward(const float2* in, const float2* gout, float2* 
 constexpr int kPowerBlocks = 64;
 cudaError_t launch_field_power(const float2* field, long long batch, long long plane, double area, double* partial,
                                double* power, cudaStream_t s);
+// Interpolation between centred grids (nearest: mode 0, bilinear: 1) and its transpose.
+struct ResampleGeom {
+  int ny, nx, ny2, nx2;
+  double dy, dx, dy2, dx2;
+  int mode;
+};
+cudaError_t launch_resample(const float2* in, float2* out, long long batch, ResampleGeom rg, int transpose,
+                            cudaStream_t s);
 // Quadrant table of H / (Py Px) for one (lambda, z) in the FieldSet::hq layout (float64 arithmetic).
 cudaError_t launch_transfer_table(float2* hq, int Py, int Px, double dy, double dx, double lam, double z, int method,
                                   cudaStream_t s);
