@@ -25,3 +25,11 @@ __device__ __forceinline__ void top_cp_async8(void* smem_dst, const void* gsrc) 
 }
 __device__ __forceinline__ void top_cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 #endif
+
+#ifndef TOP_NAMED_BARRIER
+#define TOP_NAMED_BARRIER
+// Barrier `id` (1..15) among `count` threads (a multiple of 32, whole warps) of the block.
+__device__ __forceinline__ void top_named_barrier(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+#endif

@@ -433,6 +433,21 @@ __device__ __forceinline__ long long col_src(int j, int kpos0, int ny) {
   }
 }
 
+// Barrier of the two thread groups of column cl only (the steps between the column loads and the
+// final stores touch the column's own line and exchange buffers): one warp, a named barrier of
+// the column's warps, or the whole block where neither fits.
+template <class EY, int COLS>
+__device__ __forceinline__ void column_sync(int cl) {
+  constexpr int T2 = 2 * EY::G;
+  if constexpr (T2 == 32) {
+    __syncwarp();
+  } else if constexpr (T2 % 32 == 0 && COLS < 16) {
+    top_named_barrier(1 + cl, T2);
+  } else {
+    __syncthreads();
+  }
+}
+
 template <class EY, bool X2>
 __global__ void __launch_bounds__(ColShape<EY>::THREADS, ColShape<EY>::MINB) k_cols(const __grid_constant__ PassParams p) {
   using SH = ColShape<EY>;
@@ -477,7 +492,7 @@ __global__ void __launch_bounds__(ColShape<EY>::THREADS, ColShape<EY>::MINB) k_c
 
   float2 v[E];
   fold<EY, X2, 1>(v, line, ny, p.oy, r, p.wpy, t);
-  __syncthreads();  // the lines become the even halves' exchange buffers
+  column_sync<EY, COLS>(cl);  // the column's line becomes its even half's exchange buffer
   EY::fwd(v, xbuf, t, p.twy);
   if (p.hq_out) {
     // forward transform only (a transfer-function table from sampled kernels): half r holds
@@ -528,7 +543,7 @@ __global__ void __launch_bounds__(ColShape<EY>::THREADS, ColShape<EY>::MINB) k_c
       }
     }
   }
-  __syncthreads();
+  column_sync<EY, COLS>(cl);  // the odd half's output is in its buffer
   if (!r) {
     // combine the halves into the column's line
 #pragma unroll
