@@ -193,6 +193,56 @@ def workload_config(sample=False, objects=None):
 
 # ----------------------------------------------------------------------------- our arm
 
+def context_paths(dev, c):
+    """Per-field forward time of one 1024^2 AS propagation at 2x padding, three ways (context for
+    the batched number, not part of it): the library batched (16 fields per call), the library
+    unbatched (one field per call), and torch.fft (cuFFT) pad -> fft2 -> x H -> ifft2 -> crop as a
+    reference path. Each is event-timed on the launching stream after warm-up; the 16 fields
+    (128 MB, padded 512 MB) exceed L2."""
+    import torch
+    from paper_2411_18591_gb300 import binding as Bd
+    n, d, lam, z, B = c["n"], c["d"], 532e-9, c["f"], 16
+    g = torch.Generator(device="cpu").manual_seed(7)
+    x = torch.complex(torch.randn(B, n, n, generator=g), torch.randn(B, n, n, generator=g)).to(dev)
+    y = torch.empty_like(x)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn, reps):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    batched = timed(lambda: Bd.top_propagate(x, d, d, lam, z, 2.0, out=y), 5) / B
+    unbatched = timed(lambda: [Bd.top_propagate(x[i], d, d, lam, z, 2.0, out=y[i]) for i in range(B)], 3) / B
+    # cuFFT reference: H on the padded grid in float64, rounded to complex64 once
+    P = 2 * n
+    f = torch.fft.fftfreq(P, d=d, dtype=torch.float64, device=dev)
+    rad = 1.0 / (lam * lam) - f[None, :] ** 2 - f[:, None] ** 2
+    H = torch.where(rad >= 0, torch.exp(2j * math.pi * z * torch.sqrt(rad.clamp(min=0))),
+                    torch.zeros((), dtype=torch.complex128, device=dev)).to(torch.complex64)
+    buf = torch.zeros(B, P, P, dtype=torch.complex64, device=dev)
+    o = n // 2
+
+    def cufft():
+        buf.zero_()
+        buf[:, o:o + n, o:o + n] = x
+        out = torch.fft.ifft2(torch.fft.fft2(buf) * H)
+        y.copy_(out[:, o:o + n, o:o + n])
+
+    ref = timed(cufft, 3) / B
+    return {"fwd_ms_per_field_batched": batched, "fwd_ms_per_field_unbatched": unbatched,
+            "fwd_ms_per_field_torch_fft": ref, "unbatched_over_batched": unbatched / batched,
+            "torch_fft_over_batched": ref / batched,
+            "note": "one 1024^2 AS forward propagation at 2x padding, 16 fields, event-timed; context only"}
+
+
 def run_ours(args, rank, world):
     import torch
     import __graft_entry__ as ge
@@ -284,21 +334,31 @@ def run_ours(args, rank, world):
     e2e = {"value": units_per_step * world / (ms_e2e / 1000.0), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
            "d2h_bytes_per_step": int(host_g.numel() * 4 + 8)}
 
-    # roofline of the dominant kernel (the column pass): algorithmic bytes = the workspace lines
-    # read and written once, 2 x Px x ny x 8 B per field per launch
+    # roofline of the dominant kernel (the column pass), averaged over its launches in a step:
+    # algorithmic bytes per step / column time per step. With u = Px ny 8 B (one field's
+    # workspace): a column pass that starts from the workspace reads and writes it (2u per field);
+    # the first forward propagation starts from the object broadcast over the wavelengths, so its
+    # sources' spectra are made once (read u, write 2u per source) and every field's pass reads
+    # its source's spectrum (2u once per source) and writes its workspace (u per field).
     peaks, peak_kind = measured_peaks()
     kinds = {k: v for k, v in prof.items() if v[1] > 0}
     dominant = max(kinds, key=lambda k: kinds[k][0])
     cols_ms, cols_n = prof["cols"]
-    bytes_per_field = 2 * (2 * c["n"]) * c["n"] * 8
-    cols_bytes = sysm.batch * bytes_per_field
-    cols_avg_s = cols_ms / cols_n / 1000.0
-    achieved = cols_bytes / cols_avg_s / 1e9
+    u = (2 * c["n"]) * c["n"] * 8
+    nsrc = sysm.batch // sysm.repeat
+    full_passes = FourF.FWD_PROPS + FourF.BWD_PROPS - 1
+    bytes_step = full_passes * sysm.batch * 2 * u + nsrc * 3 * u + nsrc * 2 * u + sysm.batch * u
+    launches_step = cols_n / args.steps
+    cols_s_step = cols_ms / args.steps / 1000.0
+    achieved = bytes_step / cols_s_step / 1e9
     traffic = profiled_traffic("cols")
     roofline = {"kernel": "cols (column pass: y-FFT x H x inverse y-FFT)", "bound": "hbm", "achieved": achieved,
                 "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
                 "traffic": None if traffic is None else traffic * sysm.batch, "peak_source": peak_kind,
-                "algorithmic_bytes_per_launch": cols_bytes, "avg_launch_ms": cols_avg_s * 1000.0,
+                "algorithmic_bytes_per_launch": bytes_step / launches_step,
+                "avg_launch_ms": cols_s_step / launches_step * 1000.0,
+                "algorithmic_bytes_per_step": bytes_step, "launches_per_step": launches_step,
+                "traffic_note": "ncu dram bytes of one full column launch (workspace in, workspace out)",
                 "dominant_by_time": dominant,
                 "kernel_ms_per_step": {k: v[0] / args.steps for k, v in kinds.items()}}
     launches = int(sum(v[1] for v in prof.values()))
@@ -308,6 +368,8 @@ def run_ours(args, rank, world):
             "vs_baseline": None, "dtype": "c64/f32 (FP64 phase tables)", "data": "synthetic",
             "config": workload_config(objects=objects), "roofline": roofline, "clocks": clocks, "e2e": e2e,
             "gpu_launches": launches}
+    if rank == 0 and world == 1 and not args.no_context:
+        line["context"] = context_paths(dev, c)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(2, 0)
     if rank == 0:
@@ -321,6 +383,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-context", action="store_true", help="skip the unbatched and torch.fft context timings")
     ap.add_argument("--objects", type=int, default=S.CFG4["objects"],
                     help="objects per GPU (a smaller batch for profiler captures; the workload has 16)")
     args = ap.parse_args()

@@ -174,6 +174,25 @@ cudaError_t launch_pass(int kind, int M, const PassParams& p, cudaStream_t s, co
   return cudaErrorInvalidValue;
 }
 
+// Fields of a repeat group (input_repeat) share one source when the source modulation does not
+// depend on the wavelength: no lens, and masks shared by the batch.
+bool shared_source(const top_mod* m) {
+  return !m || m->flags == 0 || (!(m->flags & TOP_MOD_LENS) && m->batch_stride == 0);
+}
+
+// The forward half of a propagation whose fields come in repeat groups with one source each: R1
+// and the forward column transforms run once per source (these parameters) into `spec`, then every
+// field's column pass starts from its source's spectrum (H of its own wavelength, inverse, crop),
+// with the same results as R1 and the column pass per field.
+PassParams source_params(const PassParams& p, int repeat, float2* spec) {
+  PassParams ps = p;
+  ps.nfields = p.nfields / repeat;
+  ps.in_repeat = 1;
+  for (int s = 0; s < ps.nfields; ++s) ps.set_of[s] = p.set_of[s * repeat];
+  ps.spec_out = spec;
+  return ps;
+}
+
 // (cos, sin) of pi * x for a float64 x, with x reduced modulo 2 exactly (fmod is exact).
 void cis_pi(double x, double* c, double* s) {
   double r = std::fmod(x, 2.0);
@@ -630,9 +649,12 @@ top_status run_propagation(top_handle h, const Request& q, cudaStream_t st) {
   if (align > kMaxFields) return fail(TOP_ERR_UNSUPPORTED, "intensity group larger than %d fields", kMaxFields);
   int64_t chunk = std::min<int64_t>(B, kMaxFields);
   chunk = std::max<int64_t>(align, chunk - chunk % align);
+  // broadcast sources: one forward spectrum per source (Px x Py samples) after the partials
+  const bool share = q.src_kind == SRC_FIELD && in_repeat > 1 && shared_source(q.msrc);
+  const size_t spec_src = share ? size_t(geo.Px) * size_t(geo.Py) * sizeof(float2) : 0;
   auto need = [&](int64_t c) {
     const int64_t ng = (c + group - 1) / group;
-    return size_t(c) * ws_field + size_t(ng) * part_bytes_per_group + 256;
+    return size_t(c) * ws_field + size_t(ng) * part_bytes_per_group + 256 + size_t(c / in_repeat) * spec_src + 256;
   };
   while (chunk > align && need(chunk) > h->ws_limit) chunk = std::max<int64_t>(align, (chunk / 2) - (chunk / 2) % align);
   if (need(chunk) > h->ws_limit)
@@ -643,6 +665,11 @@ top_status run_propagation(top_handle h, const Request& q, cudaStream_t st) {
   char* part_base = reinterpret_cast<char*>(h->ws) + size_t(chunk) * ws_field;
   part_base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(part_base) + 255) & ~uintptr_t(255));
   const int64_t ngroups_chunk = (chunk + group - 1) / group;
+  float2* spec = nullptr;
+  if (share) {
+    char* sb = part_base + size_t(ngroups_chunk) * part_bytes_per_group;
+    spec = reinterpret_cast<float2*>((reinterpret_cast<uintptr_t>(sb) + 255) & ~uintptr_t(255));
+  }
   float* part_phase = nullptr;
   float* part_amp = nullptr;
   float2* part_mask = nullptr;
@@ -751,8 +778,17 @@ top_status run_propagation(top_handle h, const Request& q, cudaStream_t st) {
       // per-field gradients use groups of one field
       p.group = partials ? int(group) : 1;
     }
-    TOP_TRY(timed(h, KK_ROWS_FWD, st, "rows forward pass", [&] { return launch_pass(PASS_ROWS_FWD, p.Mx, p, st); }));
-    TOP_TRY(timed(h, KK_COLS, st, "column pass", [&] { return launch_pass(PASS_COLS, p.My, p, st); }));
+    if (share) {
+      const PassParams ps = source_params(p, int(in_repeat), spec);
+      PassParams pc = p;
+      pc.spec_in = spec;
+      TOP_TRY(timed(h, KK_ROWS_FWD, st, "rows forward pass (sources)", [&] { return launch_pass(PASS_ROWS_FWD, p.Mx, ps, st); }));
+      TOP_TRY(timed(h, KK_COLS, st, "column spectra (sources)", [&] { return launch_pass(PASS_COLS, p.My, ps, st); }));
+      TOP_TRY(timed(h, KK_COLS, st, "column pass from spectra", [&] { return launch_pass(PASS_COLS, p.My, pc, st); }));
+    } else {
+      TOP_TRY(timed(h, KK_ROWS_FWD, st, "rows forward pass", [&] { return launch_pass(PASS_ROWS_FWD, p.Mx, p, st); }));
+      TOP_TRY(timed(h, KK_COLS, st, "column pass", [&] { return launch_pass(PASS_COLS, p.My, p, st); }));
+    }
     if (q.epi_kind == EPI_OVERLAP) {
       p.target = static_cast<const float2*>(q.target) + pos * q.target_stride;
       p.target_stride = q.target_stride;
@@ -863,9 +899,11 @@ top_status run_chain(top_handle h, const top_grid* g, const void* in, void* out,
   if (align > kMaxFields) return fail(TOP_ERR_UNSUPPORTED, "intensity group larger than %d fields", kMaxFields);
   const size_t ws_field = size_t(geo.Px) * size_t(geo.ny) * sizeof(float2);
   const size_t scr_field = scratch ? size_t(plane) * sizeof(float2) : 0;
+  const bool share = in_repeat > 1 && shared_source(stages[0].pre);
+  const size_t spec_src = share ? size_t(geo.Px) * size_t(geo.Py) * sizeof(float2) : 0;
   int64_t chunk = std::min<int64_t>(B, kMaxFields);
   chunk = std::max<int64_t>(align, chunk - chunk % align);
-  auto need = [&](int64_t c) { return size_t(c) * (ws_field + scr_field) + 256; };
+  auto need = [&](int64_t c) { return size_t(c) * (ws_field + scr_field) + 256 + size_t(c / in_repeat) * spec_src + 256; };
   while (chunk > align && need(chunk) > h->ws_limit) chunk = std::max<int64_t>(align, (chunk / 2) - (chunk / 2) % align);
   if (need(chunk) > h->ws_limit)
     return fail(TOP_ERR_OOM, "one group of fields needs %zu bytes of workspace, above the limit %llu", need(chunk),
@@ -873,6 +911,11 @@ top_status run_chain(top_handle h, const top_grid* g, const void* in, void* out,
   TOP_TRY(ensure_workspace(h, need(chunk)));
   float2* ws = static_cast<float2*>(h->ws);
   float2* scr = scratch ? ws + size_t(chunk) * size_t(geo.Px) * size_t(geo.ny) : nullptr;
+  float2* spec = nullptr;
+  if (share) {
+    char* sb = reinterpret_cast<char*>(h->ws) + size_t(chunk) * (ws_field + scr_field);
+    spec = reinterpret_cast<float2*>((reinterpret_cast<uintptr_t>(sb) + 255) & ~uintptr_t(255));
+  }
 
   PassParams base{};
   base.ny = geo.ny;
@@ -953,8 +996,17 @@ top_status run_chain(top_handle h, const top_grid* g, const void* in, void* out,
       last.group = int(group);
       last.outf = inten + (pos / group) * plane;
     }
-    TOP_TRY(timed(h, KK_ROWS_FWD, st, "rows forward pass", [&] { return launch_pass(PASS_ROWS_FWD, geo.Px / 2, ps[0], st); }));
-    TOP_TRY(timed(h, KK_COLS, st, "column pass", [&] { return launch_pass(PASS_COLS, geo.Py / 2, ps[0], st); }));
+    if (share) {
+      const PassParams psrc = source_params(ps[0], int(in_repeat), spec);
+      PassParams pc = ps[0];
+      pc.spec_in = spec;
+      TOP_TRY(timed(h, KK_ROWS_FWD, st, "rows forward pass (sources)", [&] { return launch_pass(PASS_ROWS_FWD, geo.Px / 2, psrc, st); }));
+      TOP_TRY(timed(h, KK_COLS, st, "column spectra (sources)", [&] { return launch_pass(PASS_COLS, geo.Py / 2, psrc, st); }));
+      TOP_TRY(timed(h, KK_COLS, st, "column pass from spectra", [&] { return launch_pass(PASS_COLS, geo.Py / 2, pc, st); }));
+    } else {
+      TOP_TRY(timed(h, KK_ROWS_FWD, st, "rows forward pass", [&] { return launch_pass(PASS_ROWS_FWD, geo.Px / 2, ps[0], st); }));
+      TOP_TRY(timed(h, KK_COLS, st, "column pass", [&] { return launch_pass(PASS_COLS, geo.Py / 2, ps[0], st); }));
+    }
     for (int k = 1; k < K; ++k) {
       if (fused[k]) {
         TOP_TRY(timed(h, KK_ROWS_INV, st, "fused row pass",

@@ -94,6 +94,12 @@ struct PassParams {
   // (re and im of sum psi conj(phi), sum |psi|^2)
   const float2* target; long long target_stride;
   double* ov_part;
+  // shared sources (input_repeat): the column pass stores the forward spectrum of every column in
+  // its register order (spec_out, one spectrum per launch field), or starts from the spectrum of
+  // field f / in_repeat (spec_in) instead of loading, folding and transforming its columns.
+  // Spectrum of field s, column kpos, half r, slot e, lane t at ((s Px + kpos) 2 + r) M + e G + t.
+  float2* spec_out;
+  const float2* spec_in;
   // column pass as the second half of a forward 2-D transform: bins of columns kx <= Px/2 go to
   // this quadrant table (FieldSet::hq layout) times hq_scale, nothing else is written
   float2* hq_out;

@@ -475,10 +475,12 @@ __global__ void __launch_bounds__(ColShape<EY>::THREADS, ColShape<EY>::MINB) k_c
   };
 
   // (A) de-interleave each unit of CB columns into contiguous lines: copy j of a unit holds
-  // sample j / CB of its line j % CB
-  for (int u = 0; u < ncols; u += CB) {
-    for (int j = threadIdx.x; j < CB * ny; j += NT)
-      top_cp_async8(smem + (u + j % CB) * LS + j / CB, ws + col_src<CB>(j, kpos0 + u, ny));
+  // sample j / CB of its line j % CB (not needed when the column starts from a stored spectrum)
+  if (!p.spec_in) {
+    for (int u = 0; u < ncols; u += CB) {
+      for (int j = threadIdx.x; j < CB * ny; j += NT)
+        top_cp_async8(smem + (u + j % CB) * LS + j / CB, ws + col_src<CB>(j, kpos0 + u, ny));
+    }
   }
   if constexpr (SH::template stage_h<X2>()) {
     constexpr int H4 = SH::HS / 2;  // 16-byte units per row
@@ -491,9 +493,26 @@ __global__ void __launch_bounds__(ColShape<EY>::THREADS, ColShape<EY>::MINB) k_c
   __syncthreads();
 
   float2 v[E];
-  fold<EY, X2, 1>(v, line, ny, p.oy, r, p.wpy, t);
-  column_sync<EY, COLS>(cl);  // the column's line becomes its even half's exchange buffer
-  EY::fwd(v, xbuf, t, p.twy);
+  // spectrum slot of this thread's column and half (spec_in / spec_out)
+  const long long spec_at = ((long long)min(kpos0 + cl, p.Px - 1) * 2 + r) * M + t;
+  if (p.spec_in) {
+    const float2* sp = p.spec_in + (long long)(f / p.in_repeat) * p.Px * (2 * M) + spec_at;
+#pragma unroll
+    for (int e = 0; e < E; ++e) v[e] = ldg2(sp + e * G);
+  } else {
+    fold<EY, X2, 1>(v, line, ny, p.oy, r, p.wpy, t);
+    column_sync<EY, COLS>(cl);  // the column's line becomes its even half's exchange buffer
+    EY::fwd(v, xbuf, t, p.twy);
+  }
+  if (p.spec_out) {
+    // forward transform only: the spectrum, for the fields that share this source
+    if (kpos0 + cl < p.Px) {
+      float2* sp = p.spec_out + (long long)f * p.Px * (2 * M) + spec_at;
+#pragma unroll
+      for (int e = 0; e < E; ++e) sp[e * G] = v[e];
+    }
+    return;
+  }
   if (p.hq_out) {
     // forward transform only (a transfer-function table from sampled kernels): half r holds
     // ky = 2k + r, kept where |ky| <= Py/2, i.e. k <= M/2 (even) and k < M/2 (odd), plus the

@@ -128,6 +128,23 @@ def test_in_place_and_input_repeat(T):
     assert rel_l2(out, ref2) < TOL
 
 
+@pytest.mark.parametrize("ny,nx,pad", [(64, 64, 2.0), (48, 96, 2.667), (250, 250, 2.0)])
+def test_shared_source_equals_repeated_inputs(T, ny, nx, pad):
+    """With input_repeat the forward transform of each source runs once and the fields start from
+    its spectrum; that must equal repeating the inputs bit for bit (plain, with a shared phase and
+    aperture, and with a lens, which depends on the wavelength and so is not shared)."""
+    d, rep = 5e-6, 3
+    x = cfield(8, (2, ny, nx))
+    lams = [450e-9, 560e-9, 690e-9] * 2
+    xr = dev(np.repeat(x, rep, axis=0))
+    phi = uniform(9, (ny, nx), -math.pi, math.pi).astype(np.float32)
+    for pre in (None, T.Modulation(phase=dev(phi), radius=0.4 * nx * d), T.Modulation(focal_length=0.05)):
+        a = T.top_propagate(dev(x), d, d, lams, 2e-3, pad, pre=pre, input_repeat=rep)
+        b = T.top_propagate(xr, d, d, lams, 2e-3, pad, pre=pre)
+        torch.cuda.synchronize()
+        assert torch.equal(a, b)
+
+
 # ----------------------------------------------------------------------------- modulation
 
 def _mods(T, ny, nx, per_field=False, B=3):
