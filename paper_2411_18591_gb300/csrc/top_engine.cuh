@@ -24,6 +24,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "top_launch.h"
+
 #include <utility>
 
 namespace top {
@@ -289,10 +291,14 @@ struct Engine : Radices<R0, R1, R2, R3> {
 
   __device__ __forceinline__ static int padi(int p) { return p + p / PADW; }
 
-  // a group that tiles a warp synchronises with __syncwarp, otherwise the whole block syncs
+  // a group that tiles a warp synchronises with __syncwarp, a group of whole warps with its own
+  // named barrier (ids from 15 down, one per group of the block; blocks hold at most four such
+  // groups), anything else with the whole block
   __device__ __forceinline__ static void sync_group() {
     if constexpr (G <= 32 && 32 % G == 0) {
       __syncwarp();
+    } else if constexpr (G % 32 == 0) {
+      top_named_barrier(15 - int(threadIdx.x) / G, G);
     } else {
       __syncthreads();
     }
