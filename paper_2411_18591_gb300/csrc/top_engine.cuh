@@ -292,8 +292,8 @@ struct Engine : Radices<R0, R1, R2, R3> {
   __device__ __forceinline__ static int padi(int p) { return p + p / PADW; }
 
   // a group that tiles a warp synchronises with __syncwarp, a group of whole warps with its own
-  // named barrier (ids from 15 down, one per group of the block; blocks hold at most four such
-  // groups), anything else with the whole block
+  // named barrier (ids from 15 down, one per group of the block; the pass shapes assert that they
+  // stay clear of the column barriers' ids from 1 up), anything else with the whole block
   __device__ __forceinline__ static void sync_group() {
     if constexpr (G <= 32 && 32 % G == 0) {
       __syncwarp();

@@ -71,7 +71,7 @@ struct RowShape {
   static_assert(SMEM % 16 == 0, "staged planes start on a 16-byte boundary");
   static_assert(SMEM >= 3 * sizeof(double) * THREADS, "room for the overlap reduction");
   static_assert(THREADS <= 1024, "row block too large");
-  static_assert(EN::G <= 32 || EN::G % 32 != 0 || THREADS / EN::G <= 4, "group barrier ids 12..15");
+  static_assert(EN::G <= 32 || EN::G % 32 != 0 || THREADS / EN::G <= 15, "one named barrier id per group");
   static_assert(EN::M % 2 == 0, "the four-line workspace blocks need P = 2M to be a multiple of 4");
 };
 
@@ -117,8 +117,8 @@ struct ColShape {
                                    ? (2 * EN::M > EN::BUF ? 2 * EN::M : EN::BUF) + 16 + EN::BUF
                                    : line_stride(EN::M) + EN::BUF + HS);
   static_assert(COLS % CB == 0, "columns come in whole copy units");
-  static_assert(EN::G <= 32 || EN::G % 32 != 0 || (THREADS / EN::G <= 4 && COLS < 12),
-                "group barrier ids 12..15 clear of the column barriers");
+  static_assert(EN::G <= 32 || EN::G % 32 != 0 || THREADS / EN::G + COLS <= 15,
+                "group barrier ids (15 down) clear of the column barrier ids (1 up)");
   static_assert(SMEM_MAX <= 227 * 1024, "column block above the shared-memory limit");
 };
 
