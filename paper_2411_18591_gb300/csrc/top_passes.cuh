@@ -57,8 +57,8 @@ struct RowShape {
   static constexpr int ROWBUF = ROWS * 2 * EN::M;  // input rows (n <= P = 2M) or E/O halves of the inverse
   static constexpr int MAX2 = TILE > XCH ? TILE : XCH;
   static constexpr size_t SMEM = sizeof(float2) * (MAX2 > ROWBUF ? MAX2 : ROWBUF);
-  // the inverse pass keeps four 128-thread blocks per SM (128 registers)
-  static constexpr int MINB_INV = THREADS == 128 ? 4 : 1;
+  // the inverse pass keeps 128 registers a thread (four 128-thread blocks per SM, two of 256)
+  static constexpr int MINB_INV = THREADS % 128 == 0 ? 512 / THREADS : 1;
   // R1 stages the planes its source needs besides the field rows after SMEM (at most five floats
   // per sample: intensity gradient, phase, amplitude, complex mask)
   static constexpr size_t SMEM_SRC_MAX = SMEM + sizeof(float) * 5 * ROWS * 2 * EN::M < 227 * 1024
@@ -91,9 +91,10 @@ struct ColShape {
   static constexpr int CB = COLS >= 4 ? 4 : 2;  // lines moved together: one block of four, or a pair
   static constexpr int GROUPS = 2 * COLS;
   static constexpr int THREADS = GROUPS * EN::G;
-  // two-stage power-of-two plans fit five blocks per SM (96 registers) without real spills
+  // two-stage power-of-two plans fit five blocks per SM (96 registers) without real spills; other
+  // blocks of whole 128-thread multiples keep 128 registers a thread (at least two blocks of 256)
   static constexpr int MINB = (EN::NS == 2 && (EN::G & (EN::G - 1)) == 0 && THREADS <= 128) ? 5
-                              : (EN::NS == 2 && THREADS == 256) ? 2 : 1;
+                              : (THREADS % 128 == 0 && THREADS <= 256) ? 512 / THREADS : 1;
   // line stride: room for the column and an exchange buffer, and LS = 16 / CB (mod 16) so that the
   // CB lines of a copy instruction fall on distinct banks
   __host__ __device__ static constexpr int line_stride(int ny) {
