@@ -320,7 +320,7 @@ struct Engine : Radices<R0, R1, R2, R3> {
   }
 
   // Frequency layout (last stage): slot e = q RL + j holds the bin kbase(t + G q) + j M / RL.
-  __device__ __forceinline__ static int kbase(int b) {
+  __host__ __device__ __forceinline__ static constexpr int kbase(int b) {
     // b = position / RL; digits of stages 0 .. NS-2 of the position b * RL
     int k = 0;
 #pragma unroll
@@ -334,6 +334,11 @@ struct Engine : Radices<R0, R1, R2, R3> {
     const int q = e / RL, j = e - (e / RL) * RL;
     return kbase(t + G * q) + j * (M / RL);
   }
+  // Arrays indexed by bin that lanes read or write in the frequency layout: where consecutive
+  // lanes hold bins a multiple of 16 apart (sixteen 8-byte entries span the banks once), one
+  // spare entry after every 16 spreads a warp's accesses over all banks.
+  static constexpr bool BIN_PAD = (kbase(1) - kbase(0)) % 16 == 0;
+  __host__ __device__ __forceinline__ static constexpr int bin_slot(int k) { return BIN_PAD ? k + k / 16 : k; }
 
   template <int S, int DIR>
   __device__ __forceinline__ static void stage(float2 (&v)[E], int t, const float2* __restrict__ tw) {

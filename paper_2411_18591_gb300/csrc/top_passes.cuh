@@ -51,14 +51,19 @@ struct RowShape {
   static constexpr int GROUPS = 2 * ROWS;
   static constexpr int THREADS = GROUPS * EN::G;
   static constexpr bool DIRECT = EN::NS == 2;
-  static constexpr int LD = ROWS + 1;  // odd tile stride: conflict-free column writes
-  static constexpr int TILE = DIRECT ? 0 : 2 * EN::M * LD;
+  // tile [2M][LD], bin k of a row at tslot(k) * LD + row: an odd stride keeps the column writes
+  // free of bank conflicts; plans whose lanes hold bins 16 apart pad the bin index instead
+  static constexpr int LD = EN::BIN_PAD ? (ROWS % 2 ? ROWS : ROWS + 1) : ROWS + 1;
+  __host__ __device__ __forceinline__ static constexpr int tslot(int k) { return EN::bin_slot(k); }
+  static constexpr int TILE = DIRECT ? 0 : tslot(2 * EN::M) * LD;
   static constexpr int XCH = GROUPS * EN::BUF;
   static constexpr int ROWBUF = ROWS * 2 * EN::M;  // input rows (n <= P = 2M) or E/O halves of the inverse
   static constexpr int MAX2 = TILE > XCH ? TILE : XCH;
   static constexpr size_t SMEM = sizeof(float2) * (MAX2 > ROWBUF ? MAX2 : ROWBUF);
-  // the inverse pass keeps 128 registers a thread (four 128-thread blocks per SM, two of 256)
+  // the inverse pass keeps 128 registers a thread (four 128-thread blocks per SM, two of 256);
+  // the forward pass of 256-thread blocks too (smaller blocks stay below 128 unbounded)
   static constexpr int MINB_INV = THREADS % 128 == 0 ? 512 / THREADS : 1;
+  static constexpr bool FWD_B2 = THREADS == 256;
   // R1 stages the planes its source needs besides the field rows after SMEM (at most five floats
   // per sample: intensity gradient, phase, amplitude, complex mask)
   static constexpr size_t SMEM_SRC_MAX = SMEM + sizeof(float) * 5 * ROWS * 2 * EN::M < 227 * 1024
@@ -103,20 +108,21 @@ struct ColShape {
   }
   // With padding exactly 2 (ny = M) the transfer-function rows of the block's columns (HS entries
   // each) are staged in shared memory too, where that keeps two blocks per SM; otherwise the
-  // rows are read from global memory.
+  // rows are read from global memory. Entry i of a staged row sits at bin_slot(i) (rows HSS apart).
   static constexpr int HS = EN::M + 2;
+  static constexpr int HSS = (EN::bin_slot(HS - 1) + 2) & ~1;
   template <bool X2>
   static constexpr bool stage_h() {
-    return X2 && sizeof(float2) * COLS * (line_stride(EN::M) + EN::BUF + HS) <= 110 * 1024;
+    return X2 && sizeof(float2) * COLS * (line_stride(EN::M) + EN::BUF + HSS) <= 110 * 1024;
   }
   template <bool X2>
   static size_t smem(int ny) {
-    return sizeof(float2) * (size_t(COLS) * (line_stride(ny) + EN::BUF) + (stage_h<X2>() ? COLS * HS : 0));
+    return sizeof(float2) * (size_t(COLS) * (line_stride(ny) + EN::BUF) + (stage_h<X2>() ? COLS * HSS : 0));
   }
   static constexpr size_t SMEM_MAX =
-      sizeof(float2) * COLS * ((2 * EN::M > EN::BUF ? 2 * EN::M : EN::BUF) + 16 + EN::BUF > line_stride(EN::M) + EN::BUF + HS
+      sizeof(float2) * COLS * ((2 * EN::M > EN::BUF ? 2 * EN::M : EN::BUF) + 16 + EN::BUF > line_stride(EN::M) + EN::BUF + HSS
                                    ? (2 * EN::M > EN::BUF ? 2 * EN::M : EN::BUF) + 16 + EN::BUF
-                                   : line_stride(EN::M) + EN::BUF + HS);
+                                   : line_stride(EN::M) + EN::BUF + HSS);
   static_assert(COLS % CB == 0, "columns come in whole copy units");
   static_assert(EN::G <= 32 || EN::G % 32 != 0 || THREADS / EN::G + COLS <= 15,
                 "group barrier ids (15 down) clear of the column barrier ids (1 up)");
@@ -342,19 +348,19 @@ __device__ __forceinline__ void forward_rows(const PassParams& p, int f, int y0,
   } else {
     __syncthreads();  // the exchange buffers alias the tile
 #pragma unroll
-    for (int e = 0; e < E; ++e) smem[(r * M + EX::bin(t, e)) * LD + row] = v[e];
+    for (int e = 0; e < E; ++e) smem[SH::tslot(r * M + EX::bin(t, e)) * LD + row] = v[e];
     __syncthreads();
     // the tile, ROWS rows x 4 lines per block, to the workspace in address order
     for (int i = threadIdx.x; i < 2 * M * ROWS; i += NT) {
       const int c = i & 3, q = i >> 2;
       const int yo = q % ROWS, blk = q / ROWS;
-      if (yo < nrows) ws[((long long)blk * ny + y0 + yo) * 4 + c] = smem[(4 * blk + c) * LD + yo];
+      if (yo < nrows) ws[((long long)blk * ny + y0 + yo) * 4 + c] = smem[SH::tslot(4 * blk + c) * LD + yo];
     }
   }
 }
 
 template <class EX, bool X2>
-__global__ void __launch_bounds__(RowShape<EX>::THREADS) k_rows_fwd(const __grid_constant__ PassParams p) {
+__device__ __forceinline__ void rows_fwd(const PassParams& p) {
   using SH = RowShape<EX>;
   constexpr int ROWS = SH::ROWS, NT = SH::THREADS;
   TOP_DYN_SMEM(float2, smem);
@@ -398,17 +404,29 @@ __global__ void __launch_bounds__(RowShape<EX>::THREADS) k_rows_fwd(const __grid
   forward_rows<EX, X2>(p, f, y0, nrows, smem, smem, grp, t);
 }
 
+// R1. Blocks of 128 threads or fewer take the compiler's own register choice (below 128); an
+// explicit bound of two 256-thread blocks per SM is a separate kernel.
+template <class EX, bool X2>
+__global__ void __launch_bounds__(RowShape<EX>::THREADS) k_rows_fwd(const __grid_constant__ PassParams p) {
+  rows_fwd<EX, X2>(p);
+}
+template <class EX, bool X2>
+__global__ void __launch_bounds__(RowShape<EX>::THREADS, 2) k_rows_fwd_b2(const __grid_constant__ PassParams p) {
+  rows_fwd<EX, X2>(p);
+}
+
 // ----------------------------------------------------------------------------- C
 
 // Multiply the bins of half r of column kx by H(kx, ky) / (Py Px), conjugated for the adjoint,
 // from the quadrant row of |kx| (shared or global memory): bin k of the half holds ky = 2k + r,
 // whose |signed ky| is 2k + r below the middle and Py - 2k - r above it, so the even half reads
 // entries k or M - k of the row's even part and the odd half entries k or M - 1 - k of its odd part.
+// A row in shared memory holds entry i at bin_slot(i).
 template <class EY, bool SHARED>
 __device__ __forceinline__ void apply_transfer(float2 (&v)[EY::E], const float2* row, int r, bool adjoint, int t) {
   constexpr int M = EY::M;
   const float sg = adjoint ? -1.f : 1.f;
-  const float2* part = row + r * (M / 2 + 1);
+  const int part = r * (M / 2 + 1);
   const int mirror = M - r;
   // eight loads at a time: the compiler barrier keeps it from hoisting all E loads at once
   constexpr int CH = EY::E % 8 == 0 ? 8 : EY::E;
@@ -418,7 +436,7 @@ __device__ __forceinline__ void apply_transfer(float2 (&v)[EY::E], const float2*
     for (int e = e0; e < e0 + CH; ++e) {
       const int k = EY::bin(t, e);
       const int j = k < M / 2 ? k : mirror - k;
-      float2 h = SHARED ? part[j] : ldg2(part + j);
+      float2 h = SHARED ? row[EY::bin_slot(part + j)] : ldg2(row + part + j);
       h.y *= sg;
       v[e] = c_mul(v[e], h);
     }
@@ -469,7 +487,7 @@ __global__ void __launch_bounds__(ColShape<EY>::THREADS, ColShape<EY>::MINB) k_c
   float2* line = smem + cl * LS;                            // [COLS][LS]
   float2* obuf = smem + COLS * LS + cl * EY::BUF;           // the odd half's exchange buffer and output
   float2* xbuf = r ? obuf : line;
-  float2* hrows = smem + COLS * (LS + EY::BUF);             // [COLS][HS] transfer-function rows
+  float2* hrows = smem + COLS * (LS + EY::BUF);             // [COLS][HSS] transfer-function rows
   float2* ws = p.ws + (long long)f * p.ws_stride;
   auto abs_kx = [&](int c) {  // |signed kx| of the block's column c (the last column repeats past the end)
     const int kp = min(kpos0 + c, p.Px - 1);
@@ -487,10 +505,17 @@ __global__ void __launch_bounds__(ColShape<EY>::THREADS, ColShape<EY>::MINB) k_c
     }
   }
   if constexpr (SH::template stage_h<X2>()) {
-    constexpr int H4 = SH::HS / 2;  // 16-byte units per row
-    for (int i = threadIdx.x; i < COLS * H4; i += NT) {
-      const int c = i / H4, q = i - c * H4;
-      top_cp_async16(hrows + c * SH::HS + 2 * q, fs.hq + (long long)abs_kx(c) * SH::HS + 2 * q);
+    if constexpr (EY::BIN_PAD) {
+      for (int i = threadIdx.x; i < COLS * SH::HS; i += NT) {
+        const int c = i / SH::HS, q = i - c * SH::HS;
+        top_cp_async8(hrows + c * SH::HSS + EY::bin_slot(q), fs.hq + (long long)abs_kx(c) * SH::HS + q);
+      }
+    } else {
+      constexpr int H4 = SH::HS / 2;  // 16-byte units per row
+      for (int i = threadIdx.x; i < COLS * H4; i += NT) {
+        const int c = i / H4, q = i - c * H4;
+        top_cp_async16(hrows + c * SH::HSS + 2 * q, fs.hq + (long long)abs_kx(c) * SH::HS + 2 * q);
+      }
     }
   }
   top_cp_async_wait_all();
@@ -543,7 +568,7 @@ __global__ void __launch_bounds__(ColShape<EY>::THREADS, ColShape<EY>::MINB) k_c
     return;
   }
   if constexpr (SH::template stage_h<X2>()) {
-    apply_transfer<EY, true>(v, hrows + cl * SH::HS, r, p.adjoint, t);
+    apply_transfer<EY, true>(v, hrows + cl * SH::HSS, r, p.adjoint, t);
   } else {
     apply_transfer<EY, false>(v, fs.hq + (long long)abs_kx(cl) * SH::HS, r, p.adjoint, t);
   }
@@ -828,11 +853,12 @@ __device__ __forceinline__ void inverse_rows(const PassParams& p, int f, int y0,
     for (int i = threadIdx.x; i < 2 * M * ROWS; i += NT) {
       const int c = i & 3, q = i >> 2;
       const int yo = q % ROWS, blk = q / ROWS;
-      smem[(4 * blk + c) * LD + yo] = yo < nrows ? ws[((long long)blk * ny + y0 + yo) * 4 + c] : make_float2(0.f, 0.f);
+      smem[SH::tslot(4 * blk + c) * LD + yo] =
+          yo < nrows ? ws[((long long)blk * ny + y0 + yo) * 4 + c] : make_float2(0.f, 0.f);
     }
     __syncthreads();
 #pragma unroll
-    for (int e = 0; e < E; ++e) v[e] = smem[(r * M + EX::bin(t, e)) * LD + row];
+    for (int e = 0; e < E; ++e) v[e] = smem[SH::tslot(r * M + EX::bin(t, e)) * LD + row];
     __syncthreads();  // the tile aliases the exchange buffers
   }
   EX::inv(v, smem + grp * EX::BUF, t, p.twx);
@@ -1084,12 +1110,19 @@ inline cudaError_t set_smem(K kernel, size_t bytes) {
 template <class EX, bool X2>
 cudaError_t launch_rows_fwd_t(const PassParams& p, cudaStream_t s) {
   using SH = RowShape<EX>;
-  static const cudaError_t attr = set_smem(k_rows_fwd<EX, X2>, SH::SMEM_SRC_MAX);
-  if (attr != cudaSuccess) return attr;
-  dim3 grid((p.ny + SH::ROWS - 1) / SH::ROWS, p.nfields);
-  const size_t bytes = SH::SMEM + (src_staged<EX>(p) ? sizeof(float) * src_plane_floats(p, SH::ROWS) : 0);
-  TOP_LAUNCH((k_rows_fwd<EX, X2>), grid, SH::THREADS, bytes, s, p);
-  return cudaGetLastError();
+  const auto launch = [&](auto kernel) {
+    static const cudaError_t attr = set_smem(kernel, SH::SMEM_SRC_MAX);
+    if (attr != cudaSuccess) return attr;
+    dim3 grid((p.ny + SH::ROWS - 1) / SH::ROWS, p.nfields);
+    const size_t bytes = SH::SMEM + (src_staged<EX>(p) ? sizeof(float) * src_plane_floats(p, SH::ROWS) : 0);
+    TOP_LAUNCH(kernel, grid, SH::THREADS, bytes, s, p);
+    return cudaGetLastError();
+  };
+  if constexpr (SH::FWD_B2) {
+    return launch(k_rows_fwd_b2<EX, X2>);
+  } else {
+    return launch(k_rows_fwd<EX, X2>);
+  }
 }
 
 template <class EY, bool X2>
