@@ -107,13 +107,15 @@ struct ColShape {
     return l + ((16 / CB - l) % 16 + 16) % 16;
   }
   // With padding exactly 2 (ny = M) the transfer-function rows of the block's columns (HS entries
-  // each) are staged in shared memory too, where that keeps two blocks per SM; otherwise the
-  // rows are read from global memory. Entry i of a staged row sits at bin_slot(i) (rows HSS apart).
+  // each) are staged in shared memory too, where that keeps two blocks per SM (or where the
+  // registers hold one block per SM anyway); otherwise the rows are read from global memory.
+  // Entry i of a staged row sits at bin_slot(i) (rows HSS apart).
   static constexpr int HS = EN::M + 2;
   static constexpr int HSS = (EN::bin_slot(HS - 1) + 2) & ~1;
+  static constexpr size_t H_BUDGET = 65536 / (THREADS * 128) >= 2 ? 110 * 1024 : 220 * 1024;
   template <bool X2>
   static constexpr bool stage_h() {
-    return X2 && sizeof(float2) * COLS * (line_stride(EN::M) + EN::BUF + HSS) <= 110 * 1024;
+    return X2 && sizeof(float2) * COLS * (line_stride(EN::M) + EN::BUF + HSS) <= H_BUDGET;
   }
   template <bool X2>
   static size_t smem(int ny) {
@@ -124,6 +126,7 @@ struct ColShape {
                                    ? (2 * EN::M > EN::BUF ? 2 * EN::M : EN::BUF) + 16 + EN::BUF
                                    : line_stride(EN::M) + EN::BUF + HSS);
   static_assert(COLS % CB == 0, "columns come in whole copy units");
+  static_assert(!EN::BIN_PAD || EN::bin_slot(EN::M / 2) < EN::BUF, "a half's row part fits its exchange buffer");
   static_assert(EN::G <= 32 || EN::G % 32 != 0 || THREADS / EN::G + COLS <= 15,
                 "group barrier ids (15 down) clear of the column barrier ids (1 up)");
   static_assert(SMEM_MAX <= 227 * 1024, "column block above the shared-memory limit");
@@ -422,11 +425,12 @@ __global__ void __launch_bounds__(RowShape<EX>::THREADS, 2) k_rows_fwd_b2(const 
 // whose |signed ky| is 2k + r below the middle and Py - 2k - r above it, so the even half reads
 // entries k or M - k of the row's even part and the odd half entries k or M - 1 - k of its odd part.
 // A row in shared memory holds entry i at bin_slot(i).
-template <class EY, bool SHARED>
+// With HALF the shared row holds only this half's part (entry j at bin_slot(j)).
+template <class EY, bool SHARED, bool HALF = false>
 __device__ __forceinline__ void apply_transfer(float2 (&v)[EY::E], const float2* row, int r, bool adjoint, int t) {
   constexpr int M = EY::M;
   const float sg = adjoint ? -1.f : 1.f;
-  const int part = r * (M / 2 + 1);
+  const int part = HALF ? 0 : r * (M / 2 + 1);
   const int mirror = M - r;
   // eight loads at a time: the compiler barrier keeps it from hoisting all E loads at once
   constexpr int CH = EY::E % 8 == 0 ? 8 : EY::E;
@@ -569,6 +573,14 @@ __global__ void __launch_bounds__(ColShape<EY>::THREADS, ColShape<EY>::MINB) k_c
   }
   if constexpr (SH::template stage_h<X2>()) {
     apply_transfer<EY, true>(v, hrows + cl * SH::HSS, r, p.adjoint, t);
+  } else if constexpr (EY::BIN_PAD) {
+    // lanes hold bins 16 apart: the half's part of the row goes, read in order, into the half's
+    // own exchange buffer (free between the transforms) and is applied from there
+    const float2* part = fs.hq + (long long)abs_kx(cl) * SH::HS + r * (M / 2 + 1);
+    EY::sync_group();  // every lane is past its last read of the forward transform's exchanges
+    for (int i = t; i < M / 2 + 1; i += G) xbuf[EY::bin_slot(i)] = ldg2(part + i);
+    EY::sync_group();
+    apply_transfer<EY, true, true>(v, xbuf, r, p.adjoint, t);
   } else {
     apply_transfer<EY, false>(v, fs.hq + (long long)abs_kx(cl) * SH::HS, r, p.adjoint, t);
   }

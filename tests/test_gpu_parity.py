@@ -52,6 +52,8 @@ ENGINE_CASES = [
     (24, 48, 1.34), (12, 24, 2.667), (300, 600, 1.7067), (16, 1024, 2.0), (1024, 16, 2.0),
     (16, 2048, 2.0), (2048, 16, 2.0), (16, 4096, 2.0), (4096, 16, 2.0),
     (250, 16, 2.0), (16, 500, 2.0), (768, 16, 2.0), (16, 1000, 2.0), (256, 250, 2.0), (200, 200, 2.5),
+    # the 2048- and 4096-point plans with a padding other than 2 (transfer function not staged)
+    (2000, 125, 2.048), (125, 2000, 2.048), (4000, 125, 2.048), (8192, 32, 1.0),
 ]
 
 
