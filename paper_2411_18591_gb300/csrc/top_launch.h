@@ -24,6 +24,13 @@ __device__ __forceinline__ void top_cp_async8(void* smem_dst, const void* gsrc) 
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gsrc) : "memory");
 }
 __device__ __forceinline__ void top_cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+// Close this thread's current group of copies; top_cp_async_wait_group<N>() waits until at most
+// the N most recent groups are still in flight.
+__device__ __forceinline__ void top_cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void top_cp_async_wait_group() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
 #endif
 
 #ifndef TOP_NAMED_BARRIER

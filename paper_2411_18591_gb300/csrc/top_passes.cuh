@@ -508,21 +508,23 @@ __global__ void __launch_bounds__(ColShape<EY>::THREADS, ColShape<EY>::MINB) k_c
         top_cp_async8(smem + (u + j % CB) * LS + j / CB, ws + col_src<CB>(j, kpos0 + u, ny));
     }
   }
+  top_cp_async_commit();
   if constexpr (SH::template stage_h<X2>()) {
-    if constexpr (EY::BIN_PAD) {
-      for (int i = threadIdx.x; i < COLS * SH::HS; i += NT) {
-        const int c = i / SH::HS, q = i - c * SH::HS;
-        top_cp_async8(hrows + c * SH::HSS + EY::bin_slot(q), fs.hq + (long long)abs_kx(c) * SH::HS + q);
-      }
-    } else {
-      constexpr int H4 = SH::HS / 2;  // 16-byte units per row
-      for (int i = threadIdx.x; i < COLS * H4; i += NT) {
-        const int c = i / H4, q = i - c * H4;
-        top_cp_async16(hrows + c * SH::HSS + 2 * q, fs.hq + (long long)abs_kx(c) * SH::HS + 2 * q);
+    // the column's own two groups copy its transfer-function row as a second group of copies,
+    // waited for only where it is applied: the copy overlaps the forward transform
+    if (!p.spec_out && !p.hq_out) {
+      const int ct = threadIdx.x - cl * 2 * G;  // thread of the column's 2G
+      const float2* hsrc = fs.hq + (long long)abs_kx(cl) * SH::HS;
+      float2* hdst = hrows + cl * SH::HSS;
+      if constexpr (EY::BIN_PAD) {
+        for (int q = ct; q < SH::HS; q += 2 * G) top_cp_async8(hdst + EY::bin_slot(q), hsrc + q);
+      } else {
+        for (int q = ct; q < SH::HS / 2; q += 2 * G) top_cp_async16(hdst + 2 * q, hsrc + 2 * q);  // 16-byte units
       }
     }
   }
-  top_cp_async_wait_all();
+  top_cp_async_commit();
+  top_cp_async_wait_group<1>();  // this thread's column copies
   __syncthreads();
 
   float2 v[E];
@@ -572,6 +574,8 @@ __global__ void __launch_bounds__(ColShape<EY>::THREADS, ColShape<EY>::MINB) k_c
     return;
   }
   if constexpr (SH::template stage_h<X2>()) {
+    top_cp_async_wait_all();
+    column_sync<EY, COLS>(cl);  // the column's transfer-function row is in place
     apply_transfer<EY, true>(v, hrows + cl * SH::HSS, r, p.adjoint, t);
   } else if constexpr (EY::BIN_PAD) {
     // lanes hold bins 16 apart: the half's part of the row goes, read in order, into the half's
