@@ -32,8 +32,24 @@ namespace top {
 
 // ----------------------------------------------------------------------------- complex helpers
 
-__device__ __forceinline__ float2 c_add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 c_sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// Sums and differences of complex samples are single packed-pair instructions (two FP32 lanes
+// in one 64-bit register pair, round to nearest like the scalar forms).
+__device__ __forceinline__ float2 c_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 c_sub(float2 a, float2 b) {
+  float2 r;
+  asm("{.reg .b64 pa, pb, pr;\n\t"
+      "mov.b64 pa, {%2, %3};\n\t"
+      "mov.b64 pb, {%4, %5};\n\t"
+      "sub.rn.f32x2 pr, pa, pb;\n\t"
+      "mov.b64 {%0, %1}, pr;}"
+      : "=f"(r.x), "=f"(r.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return r;
+}
+// Scalar forms, where an operand is a quarter-turn rotation that the scalar instructions absorb
+// (a packed pair would need the swapped components moved into a register pair first).
+__device__ __forceinline__ float2 s_add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 s_sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ float2 c_mul(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
@@ -154,8 +170,8 @@ __device__ __forceinline__ void dft3(float2* v) {
   const float2 m = make_float2(fmaf(c, t.x, x0.x), fmaf(c, t.y, x0.y));
   const float2 id = make_float2(-s * d.y, s * d.x);  // i s d
   v[0] = c_add(x0, t);
-  v[S] = c_add(m, id);
-  v[2 * S] = c_sub(m, id);
+  v[S] = s_add(m, id);
+  v[2 * S] = s_sub(m, id);
 }
 
 template <int S, int DIR>
@@ -166,8 +182,8 @@ __device__ __forceinline__ void dft4(float2* v) {
   const float2 wd = DIR > 0 ? c_mul_i(d) : c_mul_mi(d);  // exp(DIR i pi/2) d
   v[0] = c_add(a, c);
   v[2 * S] = c_sub(a, c);
-  v[S] = c_add(b, wd);
-  v[3 * S] = c_sub(b, wd);
+  v[S] = s_add(b, wd);
+  v[3 * S] = s_sub(b, wd);
 }
 
 template <int S, int DIR>
@@ -185,10 +201,10 @@ __device__ __forceinline__ void dft5(float2* v) {
   const float2 n1 = make_float2(fmaf(s1, b1.x, s2 * b2.x), fmaf(s1, b1.y, s2 * b2.y));
   const float2 n2 = make_float2(fmaf(s2, b1.x, -s1 * b2.x), fmaf(s2, b1.y, -s1 * b2.y));
   v[0] = c_add(x0, c_add(a1, a2));
-  v[S] = c_add(m1, c_mul_i(n1));
-  v[4 * S] = c_sub(m1, c_mul_i(n1));
-  v[2 * S] = c_add(m2, c_mul_i(n2));
-  v[3 * S] = c_sub(m2, c_mul_i(n2));
+  v[S] = s_add(m1, c_mul_i(n1));
+  v[4 * S] = s_sub(m1, c_mul_i(n1));
+  v[2 * S] = s_add(m2, c_mul_i(n2));
+  v[3 * S] = s_sub(m2, c_mul_i(n2));
 }
 
 // element I of an A x B block (index I = B k1 + n2) gets w_N^{n2 k1}
