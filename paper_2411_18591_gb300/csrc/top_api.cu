@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <complex>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -67,6 +68,15 @@ struct TransferEntry {
   float2* hq = nullptr;
 };
 
+// Bluestein tables of one line length P (CztParams): L-point engine, chirp, chirp transforms.
+struct CztPlan {
+  int L = 0;
+  const float2* chirp = nullptr;
+  const float2* bh_fwd = nullptr;
+  const float2* bh_inv = nullptr;
+  const float2* tw = nullptr;
+};
+
 struct top_ctx {
   int device = 0;
   uint64_t ws_limit = 8ull << 30;
@@ -80,6 +90,8 @@ struct top_ctx {
   std::map<std::array<uint64_t, 7>, TransferEntry> transfer;
   std::map<std::array<uint64_t, 4>, float2*> lens;
   std::map<std::array<uint64_t, 5>, int2*> circ;
+  std::map<int, CztPlan> czt;                               // Bluestein tables per line length
+  std::map<std::array<uint64_t, 7>, float2*> transfer_full;  // natural-order H for Bluestein columns
   // instrumentation
   bool prof = false;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
@@ -170,6 +182,19 @@ cudaError_t launch_pass(int kind, int M, const PassParams& p, cudaStream_t s, co
   e = launch_pass_large(kind, M, p, next, s, &found);
   if (found) return e;
   e = launch_pass_mixed(kind, M, p, next, s, &found);
+  if (found) return e;
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_czt_pass(int L, const CztParams& p, cudaStream_t s) {
+  bool found = false;
+  cudaError_t e = launch_czt_small(L, p, s, &found);
+  if (found) return e;
+  e = launch_czt_mid(L, p, s, &found);
+  if (found) return e;
+  e = launch_czt_m1024(L, p, s, &found);
+  if (found) return e;
+  e = launch_czt_large(L, p, s, &found);
   if (found) return e;
   return cudaErrorInvalidValue;
 }
@@ -444,12 +469,19 @@ top_status check_grid(const top_grid* g, Geometry* geo) {
   return TOP_OK;
 }
 
-top_status check_engines(const Geometry& geo) {
+bool has_engines(const Geometry& geo) {
   EngineInfo info;
-  for (int P : {geo.Py, geo.Px}) {
-    if (P % 2 != 0 || !find_engine(P / 2, &info))
-      return fail(TOP_ERR_UNSUPPORTED, "padded size %d has no FFT engine (supported: 2 x {16 .. 4096 powers of two, 250, 500, 768, 1000})", P);
-  }
+  for (int P : {geo.Py, geo.Px})
+    if (P % 2 != 0 || !find_engine(P / 2, &info)) return false;
+  return true;
+}
+
+top_status check_engines(const Geometry& geo) {
+  if (!has_engines(geo))
+    return fail(TOP_ERR_UNSUPPORTED,
+                "padded size %d x %d has no FFT plan of its own (planned: 2 x {16 .. 4096 powers of two, 250, 500, 768, "
+                "1000}); other sizes up to 2048 go through Bluestein transforms in top_propagate and "
+                "top_propagate_backward only", geo.Py, geo.Px);
   return TOP_OK;
 }
 
@@ -536,11 +568,283 @@ struct Request {
   double* pw_out;
 };
 
+// ============================================================================= Bluestein path
+
+// In-place radix-2 FFT in float64, X[k] = sum_n x[n] exp(-2 pi i n k / L), L a power of two.
+void host_fft(std::vector<std::complex<double>>& a) {
+  const size_t L = a.size();
+  for (size_t i = 1, j = 0; i < L; ++i) {
+    size_t bit = L >> 1;
+    for (; j & bit; bit >>= 1) j ^= bit;
+    j ^= bit;
+    if (i < j) std::swap(a[i], a[j]);
+  }
+  for (size_t len = 2; len <= L; len <<= 1) {
+    for (size_t k = 0; k < len / 2; ++k) {
+      double c, sn;
+      cis_pi(-2.0 * double(k) / double(len), &c, &sn);
+      const std::complex<double> w(c, sn);
+      for (size_t i = 0; i < L; i += len) {
+        const std::complex<double> u = a[i + k], v = a[i + k + len / 2] * w;
+        a[i + k] = u + v;
+        a[i + k + len / 2] = u - v;
+      }
+    }
+  }
+}
+
+// Tables of the Bluestein transforms of length P: c[n] = exp(-i pi n^2 / P) with n^2 reduced
+// modulo 2 P in integers (exact), and the L-point transforms of conj(c) and c on the lags
+// (-P, P) wrapped modulo L, in float64, rounded once.
+top_status czt_plan(top_handle h, int P, CztPlan* out) {
+  auto it = h->czt.find(P);
+  if (it != h->czt.end()) {
+    *out = it->second;
+    return TOP_OK;
+  }
+  int L = 16;
+  while (L < 2 * P - 1) L *= 2;
+  if (L > 4096)
+    return fail(TOP_ERR_UNSUPPORTED, "padded size %d has no FFT plan and is above the 2048 points of the Bluestein "
+                "transforms", P);
+  std::vector<float2> chirp(P);
+  std::vector<std::complex<double>> bf(L), bi(L);
+  for (int n = 0; n < P; ++n) {
+    const unsigned long long r = ((unsigned long long)n * (unsigned long long)n) % (2ull * (unsigned long long)P);
+    double c, sn;
+    cis_pi(-double(r) / double(P), &c, &sn);
+    chirp[n] = make_float2(float(c), float(sn));
+    bf[n] = std::complex<double>(c, -sn);
+    bi[n] = std::complex<double>(c, sn);
+    if (n > 0) {
+      bf[L - n] = bf[n];
+      bi[L - n] = bi[n];
+    }
+  }
+  host_fft(bf);
+  host_fft(bi);
+  std::vector<float2> hf(L), hi(L);
+  for (int k = 0; k < L; ++k) {
+    hf[k] = make_float2(float(bf[k].real()), float(bf[k].imag()));
+    hi[k] = make_float2(float(bi[k].real()), float(bi[k].imag()));
+  }
+  CztPlan plan;
+  plan.L = L;
+  float2 *dc = nullptr, *df = nullptr, *di = nullptr;
+  TOP_TRY(upload(h, chirp, &dc));
+  TOP_TRY(upload(h, hf, &df));
+  TOP_TRY(upload(h, hi, &di));
+  plan.chirp = dc;
+  plan.bh_fwd = df;
+  plan.bh_inv = di;
+  TOP_TRY(engine_twiddles(h, L, &plan.tw));
+  h->czt[P] = plan;
+  *out = plan;
+  return TOP_OK;
+}
+
+// H / (Py Px) on the whole grid in natural order, one row per kx (cached per parameter set).
+top_status transfer_full_table(top_handle h, int Py, int Px, double dy, double dx, double lam, double z, int method,
+                               cudaStream_t st, const float2** out) {
+  const std::array<uint64_t, 7> key = {uint64_t(Py), uint64_t(Px), bits(dy), bits(dx), bits(lam), bits(z),
+                                       uint64_t(method)};
+  auto it = h->transfer_full.find(key);
+  if (it != h->transfer_full.end()) {
+    *out = it->second;
+    return TOP_OK;
+  }
+  void* p = nullptr;
+  TOP_CUDA(cudaMalloc(&p, size_t(Px) * size_t(Py) * sizeof(float2)), "cudaMalloc(transfer table)");
+  h->allocs.push_back(p);
+  TOP_CUDA(launch_transfer_full(static_cast<float2*>(p), Py, Px, dy, dx, lam, z, method, st), "transfer table");
+  TOP_CUDA(cudaStreamSynchronize(st), "cudaStreamSynchronize(transfer table)");
+  h->transfer_full[key] = static_cast<float2*>(p);
+  *out = static_cast<float2*>(p);
+  return TOP_OK;
+}
+
+// Lens tables of fields [pos, pos + n) as the parameter sets of one modulation launch.
+top_status fill_lens_sets(top_handle h, const top_grid* g, const top_mod* mod, const double* lambda,
+                                 int64_t n_lz, int64_t pos, int64_t n, PassParams* p) {
+  p->nsets = 0;
+  for (int64_t b = pos; b < pos + n; ++b) {
+    FieldSet fs{};
+    if (mod->flags & TOP_MOD_LENS) {
+      const double lam = lambda[n_lz == 1 ? 0 : b];
+      TOP_TRY(lens_table(h, g->nx, g->dx, lam, mod->focal_length, &fs.src_lx));
+      TOP_TRY(lens_table(h, g->ny, g->dy, lam, mod->focal_length, &fs.src_ly));
+    }
+    fs.epi_lx = fs.src_lx;
+    fs.epi_ly = fs.src_ly;
+    int k = 0;
+    while (k < p->nsets && std::memcmp(&p->sets[k], &fs, sizeof fs) != 0) ++k;
+    if (k == p->nsets) {
+      if (p->nsets == kMaxSets) return fail(TOP_ERR_INTERNAL, "lens set overflow");
+      p->sets[p->nsets++] = fs;
+    }
+    p->set_of[b - pos] = (unsigned char)k;
+  }
+  return TOP_OK;
+}
+
+// out[f] = M_f in[f / repeat] (conj(M_f) with conj) for fields [pos, pos + n) of a call.
+top_status modulate_fields(top_handle h, const top_grid* g, const Geometry& geo, const top_mod* mod, int conj,
+                           const double* lam, int64_t n_lz, int64_t pos, int64_t n, const float2* in, int repeat,
+                           float2* out, cudaStream_t st) {
+  const int2* circ = nullptr;
+  if (mod->flags & TOP_MOD_CIRC) TOP_TRY(circ_table(h, geo.ny, geo.nx, g->dy, g->dx, mod->radius, &circ));
+  const ModDev base = mod_dev(mod, conj, circ);
+  const long long plane = (long long)geo.ny * geo.nx;
+  for (int64_t c = 0; c < n; c += kMaxSets) {
+    const int64_t m = std::min<int64_t>(kMaxSets, n - c);
+    PassParams p{};
+    p.ny = geo.ny;
+    p.nx = geo.nx;
+    TOP_TRY(fill_lens_sets(h, g, mod, lam, n_lz, pos + c, m, &p));
+    p.nfields = int(m);
+    p.msrc = offset_mod(base, pos + c);
+    // a repeat group never straddles the chunks of kMaxSets fields when repeat divides them
+    p.in_repeat = repeat;
+    p.in = in + (repeat > 1 ? c / repeat : c) * plane;
+    p.out = out + c * plane;
+    TOP_TRY(timed(h, KK_AUX, st, "modulate", [&] { return launch_modulate(p, st); }));
+  }
+  return TOP_OK;
+}
+
+// A propagation whose padded size has no plan of its own (odd, or with prime factors above 5),
+// up to 2048 points per axis: rows by Bluestein forward transforms, a transpose, each column's
+// forward transform, H and inverse transform in one Bluestein line pass, a transpose back and the
+// rows' inverse transforms with the crop. Modulations run as separate passes; fused epilogues
+// (intensity, overlap, modulation gradients) need a planned size.
+top_status run_bluestein(top_handle h, const Request& q, const Geometry& geo, cudaStream_t st) {
+  const top_grid* g = q.g;
+  if (q.src_kind != SRC_FIELD || q.epi_kind != EPI_FIELD)
+    return fail(TOP_ERR_UNSUPPORTED, "padded size %d x %d has no FFT plan of its own: its Bluestein transforms cover "
+                "top_propagate and top_propagate_backward without modulation gradients", geo.Py, geo.Px);
+  TOP_TRY(bind(h));
+  const int64_t B = g->batch;
+  const int repeat = g->input_repeat > 1 ? g->input_repeat : 1;
+  CztPlan cx, cy;
+  TOP_TRY(czt_plan(h, geo.Px, &cx));
+  TOP_TRY(czt_plan(h, geo.Py, &cy));
+  std::vector<const float2*> tables(B);
+  for (int64_t b = 0; b < B; ++b) {
+    const double lam = q.lam[q.n_lz == 1 ? 0 : b], z = q.z[q.n_lz == 1 ? 0 : b];
+    const int method = resolve_method(g, geo.ny, geo.nx, lam, z);
+    if (method == TOP_DI)
+      return fail(TOP_ERR_UNSUPPORTED, "Direct Integration needs a padded size with an FFT plan of its own (got %d x %d)",
+                  geo.Py, geo.Px);
+    TOP_TRY(transfer_full_table(h, geo.Py, geo.Px, g->dy, g->dx, lam, z, method, st, &tables[b]));
+  }
+  const long long plane = (long long)geo.ny * geo.nx;
+  const long long wplane = (long long)geo.ny * geo.Px;
+  const bool pre = q.msrc && q.msrc->flags;
+  const bool post = q.mepi && q.mepi->flags;
+  const size_t per_field = sizeof(float2) * size_t(2 * wplane + (pre ? plane : 0)) + sizeof(void*);
+  int64_t chunk = std::max<int64_t>(1, int64_t((h->ws_limit > 4096 ? h->ws_limit - 4096 : 0) / per_field));
+  chunk = std::min<int64_t>({chunk, B, 65535});
+  if (repeat > 1) {
+    // whole repeat groups per chunk, and per modulation launch (kMaxSets fields)
+    if (pre && kMaxSets % repeat != 0)
+      return fail(TOP_ERR_UNSUPPORTED, "input_repeat %d with a source modulation on a Bluestein size needs a divisor "
+                  "of %d", repeat, kMaxSets);
+    chunk = std::max<int64_t>(repeat, chunk - chunk % repeat);
+  }
+  TOP_TRY(ensure_workspace(h, size_t(chunk) * (per_field - sizeof(void*)) + 256 + size_t(chunk) * sizeof(void*)));
+  float2* w1 = static_cast<float2*>(h->ws);
+  float2* w2 = w1 + chunk * wplane;
+  float2* src = w2 + chunk * wplane;
+  char* tail = reinterpret_cast<char*>(w1) + size_t(chunk) * (per_field - sizeof(void*));
+  tail = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(tail) + 255) & ~uintptr_t(255));
+  const float2** d_h = reinterpret_cast<const float2**>(tail);
+  const float2* in = static_cast<const float2*>(q.in);
+  float2* out = static_cast<float2*>(q.out);
+  for (int64_t pos = 0; pos < B; pos += chunk) {
+    const int64_t n = std::min<int64_t>(chunk, B - pos);
+    const float2* fin = in + (pos / repeat) * plane;
+    int in_rep = repeat;
+    if (pre) {
+      TOP_TRY(modulate_fields(h, g, geo, q.msrc, q.msrc_conj, q.lam, q.n_lz, pos, n, fin, repeat, src, st));
+      fin = src;
+      in_rep = 1;
+    }
+    TOP_CUDA(cudaMemcpyAsync(d_h, tables.data() + pos, size_t(n) * sizeof(void*), cudaMemcpyHostToDevice, st),
+             "cudaMemcpyAsync(transfer table pointers)");
+    CztParams r{};
+    r.mode = CZT_FWD;
+    r.in = fin;
+    r.in_fstride = plane;
+    r.in_lstride = geo.nx;
+    r.in_repeat = in_rep;
+    r.out = w1;
+    r.out_fstride = wplane;
+    r.out_lstride = geo.Px;
+    r.nlines = geo.ny;
+    r.nfields = int(n);
+    r.P = geo.Px;
+    r.n_in = geo.nx;
+    r.off_in = geo.ox;
+    r.k0 = 0;
+    r.n_out = geo.Px;
+    r.inv_l = 1.f / float(cx.L);
+    r.chirp = cx.chirp;
+    r.bh_fwd = cx.bh_fwd;
+    r.bh_inv = cx.bh_inv;
+    r.tw = cx.tw;
+    TOP_TRY(timed(h, KK_ROWS_FWD, st, "Bluestein rows", [&] { return launch_czt_pass(cx.L, r, st); }));
+    TOP_TRY(timed(h, KK_AUX, st, "transpose", [&] { return launch_transpose_rect(w1, w2, n, geo.ny, geo.Px, st); }));
+    CztParams c{};
+    c.mode = CZT_FILTER;
+    c.adjoint = q.adjoint;
+    c.in = w2;
+    c.in_fstride = wplane;
+    c.in_lstride = geo.ny;
+    c.in_repeat = 1;
+    c.out = w2;
+    c.out_fstride = wplane;
+    c.out_lstride = geo.ny;
+    c.nlines = geo.Px;
+    c.nfields = int(n);
+    c.P = geo.Py;
+    c.n_in = geo.ny;
+    c.off_in = geo.oy;
+    c.k0 = geo.oy;
+    c.n_out = geo.ny;
+    c.inv_l = 1.f / float(cy.L);
+    c.chirp = cy.chirp;
+    c.bh_fwd = cy.bh_fwd;
+    c.bh_inv = cy.bh_inv;
+    c.tw = cy.tw;
+    c.h = d_h;
+    TOP_TRY(timed(h, KK_COLS, st, "Bluestein columns", [&] { return launch_czt_pass(cy.L, c, st); }));
+    TOP_TRY(timed(h, KK_AUX, st, "transpose", [&] { return launch_transpose_rect(w2, w1, n, geo.Px, geo.ny, st); }));
+    CztParams v = r;
+    v.mode = CZT_INV;
+    v.in = w1;
+    v.in_fstride = wplane;
+    v.in_lstride = geo.Px;
+    v.in_repeat = 1;
+    v.out = out + pos * plane;
+    v.out_fstride = plane;
+    v.out_lstride = geo.nx;
+    v.n_in = geo.Px;
+    v.off_in = 0;
+    v.k0 = geo.ox;
+    v.n_out = geo.nx;
+    TOP_TRY(timed(h, KK_ROWS_INV, st, "Bluestein inverse rows", [&] { return launch_czt_pass(cx.L, v, st); }));
+    if (post)
+      TOP_TRY(modulate_fields(h, g, geo, q.mepi, q.mepi_conj, q.lam, q.n_lz, pos, n, out + pos * plane, 1,
+                              out + pos * plane, st));
+  }
+  return TOP_OK;
+}
+
 top_status run_propagation(top_handle h, const Request& q, cudaStream_t st) {
   const top_grid* g = q.g;
   Geometry geo;
   TOP_TRY(check_grid(g, &geo));
-  TOP_TRY(check_engines(geo));
+  const bool planned = has_engines(geo);
   TOP_TRY(check_lz(g, q.lam, q.z, q.n_lz, true));
   TOP_TRY(check_mod(q.msrc, "source modulation"));
   TOP_TRY(check_mod(q.mepi, "epilogue modulation"));
@@ -584,6 +888,7 @@ top_status run_propagation(top_handle h, const Request& q, cudaStream_t st) {
         if (p && !aligned16(p)) return fail(TOP_ERR_INVALID_ARG, "gradient output not 16-byte aligned");
     }
   }
+  if (!planned) return run_bluestein(h, q, geo, st);
   TOP_TRY(bind(h));
 
   // engine and split twiddles
@@ -1458,29 +1763,6 @@ static top_status modulation_common(top_handle h, const top_grid* g, const top_m
   p->nx = geo->nx;
   p->msrc = mod_dev(mod, 0, circ);
   p->mepi = p->msrc;
-  return TOP_OK;
-}
-
-static top_status fill_lens_sets(top_handle h, const top_grid* g, const top_mod* mod, const double* lambda,
-                                 int64_t n_lz, int64_t pos, int64_t n, PassParams* p) {
-  p->nsets = 0;
-  for (int64_t b = pos; b < pos + n; ++b) {
-    FieldSet fs{};
-    if (mod->flags & TOP_MOD_LENS) {
-      const double lam = lambda[n_lz == 1 ? 0 : b];
-      TOP_TRY(lens_table(h, g->nx, g->dx, lam, mod->focal_length, &fs.src_lx));
-      TOP_TRY(lens_table(h, g->ny, g->dy, lam, mod->focal_length, &fs.src_ly));
-    }
-    fs.epi_lx = fs.src_lx;
-    fs.epi_ly = fs.src_ly;
-    int k = 0;
-    while (k < p->nsets && std::memcmp(&p->sets[k], &fs, sizeof fs) != 0) ++k;
-    if (k == p->nsets) {
-      if (p->nsets == kMaxSets) return fail(TOP_ERR_INTERNAL, "lens set overflow");
-      p->sets[p->nsets++] = fs;
-    }
-    p->set_of[b - pos] = (unsigned char)k;
-  }
   return TOP_OK;
 }
 

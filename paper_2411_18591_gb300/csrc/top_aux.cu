@@ -1,9 +1,13 @@
 #include "top_aux.h"
+
+#include <algorithm>
+
 #include "top_passes.cuh"
 
 namespace top {
 
-// out[f] = M_f * in[f] (Eq. 1)
+// out[f] = M_f * in[f] (Eq. 1), conj(M_f) where the modulation asks for it; fields of a repeat
+// group (in_repeat > 1) read their group's input
 __global__ void __launch_bounds__(256) k_modulate(const __grid_constant__ PassParams p) {
   const long long plane = (long long)p.ny * p.nx;
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -11,8 +15,9 @@ __global__ void __launch_bounds__(256) k_modulate(const __grid_constant__ PassPa
   if (i >= plane) return;
   const int y = int(i / p.nx), x = int(i - (long long)y * p.nx);
   const FieldSet& fs = p.sets[p.set_of[f]];
-  const float2 m = mod_value(p.msrc, p.msrc.flags, 0, fs.src_lx, fs.src_ly, f, y, x, p.nx);
-  p.out[(long long)f * plane + i] = c_mul(ldg2(p.in + (long long)f * plane + i), m);
+  const float2 m = mod_value(p.msrc, p.msrc.flags, p.msrc.conj, fs.src_lx, fs.src_ly, f, y, x, p.nx);
+  const int fi = p.in_repeat > 1 ? f / p.in_repeat : f;  // fields in repeat groups share an input
+  p.out[(long long)f * plane + i] = c_mul(p.in[(long long)fi * plane + i], m);
 }
 
 // Backward of y = M x: grad_in = conj(M) g; parameter gradients summed over the fields of a
@@ -139,6 +144,28 @@ cudaError_t launch_reduce_partials(const float* part_phase, const float* part_am
 // multiply-add, so the evanescent decision is the same as an IEEE evaluation of that
 // expression), H = 0 where it is negative, else exp(2 pi i z sqrt(radicand)). Phases are
 // reduced in cycles (c - rint(c) is exact) before the sine and cosine.
+__device__ __forceinline__ float2 transfer_value(int akx, int aky, int Py, int Px, double dy, double dx, double lam,
+                                                 double z, int method) {
+  const double fx = double(akx) / (double(Px) * dx);
+  const double fy = double(aky) / (double(Py) * dy);
+  const double fx2 = __dmul_rn(fx, fx), fy2 = __dmul_rn(fy, fy);
+  const double norm = 1.0 / (double(Py) * double(Px));
+  double cyc;
+  if (method == TOP_AS) {
+    const double rad = __dsub_rn(__dsub_rn(1.0 / __dmul_rn(lam, lam), fx2), fy2);
+    if (rad < 0.0) return make_float2(0.f, 0.f);
+    const double c = __dmul_rn(z, sqrt(rad));
+    cyc = c - rint(c);
+  } else {
+    const double a = z / lam;
+    const double b = 0.5 * lam * z * (fx2 + fy2);
+    cyc = (a - rint(a)) - (b - rint(b));
+  }
+  double sn, cs;
+  sincospi(2.0 * cyc, &sn, &cs);
+  return make_float2(float(cs * norm), float(sn * norm));
+}
+
 __global__ void __launch_bounds__(256) k_transfer_table(float2* hq, int Py, int Px, double dy, double dx, double lam,
                                                         double z, int method) {
   const int my = Py / 2, even = my / 2 + 1;
@@ -151,27 +178,33 @@ __global__ void __launch_bounds__(256) k_transfer_table(float2* hq, int Py, int 
     return;
   }
   const int aky = j < even ? 2 * j : 2 * (j - even) + 1;
-  const double fx = double(akx) / (double(Px) * dx);
-  const double fy = double(aky) / (double(Py) * dy);
-  const double fx2 = __dmul_rn(fx, fx), fy2 = __dmul_rn(fy, fy);
-  const double norm = 1.0 / (double(Py) * double(Px));
-  double cyc;
-  if (method == TOP_AS) {
-    const double rad = __dsub_rn(__dsub_rn(1.0 / __dmul_rn(lam, lam), fx2), fy2);
-    if (rad < 0.0) {
-      *out = make_float2(0.f, 0.f);
-      return;
-    }
-    const double c = __dmul_rn(z, sqrt(rad));
-    cyc = c - rint(c);
-  } else {
-    const double a = z / lam;
-    const double b = 0.5 * lam * z * (fx2 + fy2);
-    cyc = (a - rint(a)) - (b - rint(b));
+  *out = transfer_value(akx, aky, Py, Px, dy, dx, lam, z, method);
+}
+
+// The same values on the whole padded grid in natural order, one row per kx: h[kx Py + ky], with
+// |k| = min(k, P - k) (any Py, Px).
+__global__ void __launch_bounds__(256) k_transfer_full(float2* h, int Py, int Px, double dy, double dx, double lam,
+                                                       double z, int method) {
+  const int ky = blockIdx.x * blockDim.x + threadIdx.x;
+  const int kx = blockIdx.y;
+  if (ky >= Py) return;
+  h[(long long)kx * Py + ky] = transfer_value(min(kx, Px - kx), min(ky, Py - ky), Py, Px, dy, dx, lam, z, method);
+}
+
+// out[b][c][r] = in[b][r][c] for [rows][cols] planes, through a 32 x 33 shared tile.
+__global__ void __launch_bounds__(256) k_transpose_rect(const float2* in, float2* out, int rows, int cols) {
+  __shared__ float2 tile[32][33];
+  const long long base = (long long)blockIdx.z * rows * cols;
+  const int bc = blockIdx.x * 32, br = blockIdx.y * 32;
+  for (int j = threadIdx.y; j < 32; j += 8) {
+    const int r = br + j, c = bc + threadIdx.x;
+    if (r < rows && c < cols) tile[j][threadIdx.x] = in[base + (long long)r * cols + c];
   }
-  double sn, cs;
-  sincospi(2.0 * cyc, &sn, &cs);
-  *out = make_float2(float(cs * norm), float(sn * norm));
+  __syncthreads();
+  for (int j = threadIdx.y; j < 32; j += 8) {
+    const int c = bc + j, r = br + threadIdx.x;
+    if (r < rows && c < cols) out[base + (long long)c * rows + r] = tile[threadIdx.x][j];
+  }
 }
 
 // h_z(x, y) dx dy of Eq. 3 at x = sx dx, y = sy dy with (sx, sy) the signed lags of the grid:
@@ -495,6 +528,23 @@ cudaError_t launch_transfer_table(float2* hq, int Py, int Px, double dy, double 
   const int my = Py / 2;
   dim3 grid((my + 2 + 255) / 256, Px / 2 + 1);
   TOP_LAUNCH(k_transfer_table, grid, 256, 0, s, hq, Py, Px, dy, dx, lam, z, method);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_transfer_full(float2* h, int Py, int Px, double dy, double dx, double lam, double z, int method,
+                                 cudaStream_t s) {
+  dim3 grid((Py + 255) / 256, Px);
+  TOP_LAUNCH(k_transfer_full, grid, 256, 0, s, h, Py, Px, dy, dx, lam, z, method);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_transpose_rect(const float2* in, float2* out, long long batch, int rows, int cols, cudaStream_t s) {
+  for (long long b0 = 0; b0 < batch; b0 += 65535) {
+    const unsigned nb = unsigned(std::min<long long>(65535, batch - b0));
+    dim3 grid((cols + 31) / 32, (rows + 31) / 32, nb);
+    const long long off = b0 * rows * cols;
+    TOP_LAUNCH(k_transpose_rect, grid, dim3(32, 8), 0, s, in + off, out + off, rows, cols);
+  }
   return cudaGetLastError();
 }
 

@@ -54,6 +54,11 @@ cudaError_t launch_resample(const float2* in, float2* out, long long batch, Resa
 // Quadrant table of H / (Py Px) for one (lambda, z) in the FieldSet::hq layout (float64 arithmetic).
 cudaError_t launch_transfer_table(float2* hq, int Py, int Px, double dy, double dx, double lam, double z, int method,
                                   cudaStream_t s);
+// The same values on the whole grid in natural order, h[kx Py + ky] (the Bluestein column lines).
+cudaError_t launch_transfer_full(float2* h, int Py, int Px, double dy, double dx, double lam, double z, int method,
+                                 cudaStream_t s);
+// out[b][c][r] = in[b][r][c] for a batch of [rows][cols] planes.
+cudaError_t launch_transpose_rect(const float2* in, float2* out, long long batch, int rows, int cols, cudaStream_t s);
 
 }  // namespace top
 

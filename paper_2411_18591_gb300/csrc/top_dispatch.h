@@ -35,4 +35,10 @@ TOP_DECLARE_UNIT(mixed)
 
 #undef TOP_DECLARE_UNIT
 
+// Bluestein line transforms (CztParams) on the power-of-two engines of a unit.
+cudaError_t launch_czt_small(int M, const CztParams& p, cudaStream_t s, bool* found);
+cudaError_t launch_czt_mid(int M, const CztParams& p, cudaStream_t s, bool* found);
+cudaError_t launch_czt_m1024(int M, const CztParams& p, cudaStream_t s, bool* found);
+cudaError_t launch_czt_large(int M, const CztParams& p, cudaStream_t s, bool* found);
+
 }  // namespace top

@@ -126,6 +126,38 @@ __host__ __device__ inline size_t src_plane_floats(const PassParams& p, int rows
   return n;
 }
 
+// Line transforms of any length P by Bluestein's chirp-z method (padded sizes without a plan of
+// their own): with c[n] = exp(-i pi n^2 / P), the DFT is X[k] = c[k] sum_n (x[n] c[n]) conj(c[k - n]),
+// a convolution done as an L-point FFT (L >= 2P - 1), a product with the transform of the chirp
+// (in bins) and an inverse L-point FFT; the inverse DFT uses the conjugate chirps.
+enum CztMode : int {
+  CZT_FWD = 0,     // forward DFT of the zero-padded line
+  CZT_INV = 1,     // inverse DFT (unnormalised), then the output window
+  CZT_FILTER = 2,  // forward DFT, times the transfer function (conjugated for the adjoint), inverse DFT, window
+};
+
+struct CztParams {
+  const float2* in;      // line i of field f at in + (f / in_repeat) in_fstride + i in_lstride
+  long long in_fstride;
+  long long in_lstride;
+  int in_repeat;
+  float2* out;           // window sample k - k0 of line i of field f at out + f out_fstride + i out_lstride
+  long long out_fstride;
+  long long out_lstride;
+  int nlines, nfields;
+  int P;                 // DFT length
+  int n_in, off_in;      // the line's samples sit at [off_in, off_in + n_in) of the zero-padded line
+  int k0, n_out;         // output window
+  int mode;              // CztMode
+  int adjoint;
+  float inv_l;           // 1 / L
+  const float2* chirp;   // c[n], n < P
+  const float2* bh_fwd;  // L-point transform of conj(c) on (-P, P), natural order
+  const float2* bh_inv;  // L-point transform of c on (-P, P)
+  const float2* tw;      // stage twiddles of the L-point engine
+  const float2* const* h;  // CZT_FILTER: per field, rows [line][P] of H / (Py Px) in natural order
+};
+
 // Largest dynamic shared memory of a fused chain block (R2 of one propagation + R1 of the next).
 constexpr size_t kChainSmemMax = 227 * 1024;
 

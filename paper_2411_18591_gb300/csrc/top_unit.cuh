@@ -1,6 +1,7 @@
 // Helpers that expand an engine list into the registry functions of one unit.
 #pragma once
 
+#include "top_czt.cuh"
 #include "top_dispatch.h"
 #include "top_passes.cuh"
 
@@ -46,4 +47,18 @@ inline cudaError_t launch_pass_of(int kind, const PassParams& p, const PassParam
     *found = false;                                                                                 \
     switch (M) { LIST(TOP_LAUNCH_CASE) default: return cudaSuccess; }                               \
   }                                                                                                 \
+  }
+
+#define TOP_CZT_CASE(EN) \
+  case EN::M:            \
+    *found = true;       \
+    return launch_czt<EN>(p, s);
+
+// Bluestein line transforms on the unit's (power-of-two) engines.
+#define TOP_DEFINE_CZT(name, LIST)                                                                 \
+  namespace top {                                                                                  \
+  cudaError_t launch_czt_##name(int M, const CztParams& p, cudaStream_t s, bool* found) {          \
+    *found = false;                                                                                \
+    switch (M) { LIST(TOP_CZT_CASE) default: return cudaSuccess; }                                 \
+  }                                                                                                \
   }

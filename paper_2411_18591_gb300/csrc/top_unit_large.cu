@@ -8,3 +8,4 @@ using Eng4096 = Engine<4096, 128, 16, 16, 16>;
 
 #define LIST(X) X(Eng2048) X(Eng4096)
 TOP_DEFINE_UNIT(large, LIST)
+TOP_DEFINE_CZT(large, LIST)

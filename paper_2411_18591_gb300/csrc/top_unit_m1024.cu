@@ -7,3 +7,4 @@ using Eng1024 = Engine<1024, 32, 32, 32>;
 
 #define LIST(X) X(Eng1024)
 TOP_DEFINE_UNIT(m1024, LIST)
+TOP_DEFINE_CZT(m1024, LIST)

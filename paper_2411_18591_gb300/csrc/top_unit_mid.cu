@@ -8,3 +8,4 @@ using Eng512 = Engine<512, 16, 16, 32>;
 
 #define LIST(X) X(Eng256) X(Eng512)
 TOP_DEFINE_UNIT(mid, LIST)
+TOP_DEFINE_CZT(mid, LIST)

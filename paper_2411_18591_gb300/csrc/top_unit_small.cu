@@ -10,3 +10,4 @@ using Eng128 = Engine<128, 8, 8, 16>;
 
 #define LIST(X) X(Eng16) X(Eng32) X(Eng64) X(Eng128)
 TOP_DEFINE_UNIT(small, LIST)
+TOP_DEFINE_CZT(small, LIST)
