@@ -136,7 +136,10 @@ int top_version(void);
 top_status top_set_workspace_limit(top_handle h, uint64_t bytes);
 
 /* Host-only plan query: padded sizes and per-field workspace bytes of a propagation.
- * Validates `g` exactly like the propagation calls. */
+ * Validates `g` exactly like the propagation calls. Padded sizes P = floor(pad n + 0.5) of
+ * 2 x {16 .. 4096 powers of two, 250, 500, 768, 1000} have FFT plans of their own (one
+ * field-sized workspace buffer); any other size up to 2048 per axis goes through Bluestein
+ * transforms (two buffers); larger unplanned sizes return TOP_ERR_UNSUPPORTED. */
 top_status top_plan_query(const top_grid* g, int64_t* py, int64_t* px, uint64_t* workspace_per_field);
 
 /* Eq. 6: z_critical = L dx / lambda. AS is the accurate method for z < z_critical. */
@@ -147,7 +150,12 @@ double top_zcritical(double L, double dx, double lambda);
 /* out = post * P_z(pre * in) for every field (Eq. 1 then Eq. 4, then Eq. 1).
  * in, out: complex64 [batch][ny][nx] device (in == out allowed).
  * lambda, z: host arrays of n_lz values, n_lz == 1 (shared) or == batch (per field).
- * pre, post: modulations or NULL. */
+ * pre, post: modulations or NULL.
+ * Padded sizes without an FFT plan of their own (odd, or with prime factors above 5; up to
+ * 2048 per axis) use Bluestein line transforms: the same result (a DFT of length P per axis),
+ * with the modulations as separate passes; TOP_DI is rejected there (TOP_ERR_UNSUPPORTED), and
+ * so are the fused variants (intensity, overlap, chains, ragged batches, modulation gradients,
+ * the no-alloc call), which need a planned size. */
 top_status top_propagate(top_handle h, const top_grid* g, const void* in, void* out,
                          const double* lambda, const double* z, int64_t n_lz,
                          const top_mod* pre, const top_mod* post, void* stream);

@@ -1528,10 +1528,17 @@ top_status top_set_workspace_limit(top_handle h, uint64_t bytes) {
 top_status top_plan_query(const top_grid* g, int64_t* py, int64_t* px, uint64_t* workspace_per_field) {
   Geometry geo;
   TOP_TRY(check_grid(g, &geo));
-  TOP_TRY(check_engines(geo));
+  // sizes without a plan of their own take Bluestein transforms (up to 2048 points per axis,
+  // two field-sized buffers)
+  const bool planned = has_engines(geo);
+  if (!planned) {
+    for (int P : {geo.Py, geo.Px})
+      if (2 * P - 1 > 4096) TOP_TRY(check_engines(geo));
+  }
   if (py) *py = geo.Py;
   if (px) *px = geo.Px;
-  if (workspace_per_field) *workspace_per_field = uint64_t(geo.Px) * uint64_t(geo.ny) * sizeof(float2);
+  if (workspace_per_field)
+    *workspace_per_field = uint64_t(planned ? 1 : 2) * uint64_t(geo.Px) * uint64_t(geo.ny) * sizeof(float2);
   return TOP_OK;
 }
 

@@ -82,10 +82,20 @@ def test_plan_query_padded_sizes(lib, ny, nx, pad, py, px):
     assert ws == px * ny * 8
 
 
+@pytest.mark.parametrize("ny,nx,pad,py,px", [(61, 61, 1.0, 61, 61), (20, 20, 1.7, 34, 34), (1021, 24, 2.0, 2042, 48)])
+def test_plan_query_bluestein_sizes(lib, ny, nx, pad, py, px):
+    """Padded sizes without a plan of their own go through Bluestein transforms (two field-sized
+    buffers per field)."""
+    st, gy, gx, ws = plan(lib, ny=ny, nx=nx, pad=pad)
+    assert st == 0
+    assert (gy, gx) == (py, px)
+    assert ws == 2 * px * ny * 8
+
+
 @pytest.mark.parametrize("kw,status", [
     (dict(batch=0), 1), (dict(ny=0), 1), (dict(dx=0.0), 1), (dict(dy=-1e-6), 1), (dict(dx=float("nan")), 1),
     (dict(pad=0.5), 1), (dict(pad=float("inf")), 1), (dict(method=7), 1), (dict(batch=6, input_repeat=4), 1),
-    (dict(ny=61, nx=61, pad=1.0), 2), (dict(ny=20, nx=20, pad=1.7), 2),
+    (dict(ny=16, nx=1500, pad=2.0), 2), (dict(ny=2049, nx=16, pad=1.0), 2),
 ])
 def test_plan_query_rejects(lib, kw, status):
     st, *_ = plan(lib, **kw)
