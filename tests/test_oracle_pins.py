@@ -120,6 +120,22 @@ def test_plane_wave_is_eigenvector(a, b):
     assert rel_l2(out, h * f) < 1e-12
 
 
+@pytest.mark.parametrize("a,b", [(0, 0), (4, -6), (-8, 5), (8, 6)])
+def test_plane_wave_is_eigenvector_at_prime_sizes(a, b):
+    """The same eigenvalue at prime padded sizes (13 x 17), where the frequency index a of an odd
+    size runs over -(P - 1)/2 .. (P - 1)/2: the padded sizes that take Bluestein transforms."""
+    py, px, dy, dx, lam, z = 13, 17, 2e-6, 1.5e-6, 0.8e-6, 3.7e-4
+    m = np.arange(px)[None, :]
+    l = np.arange(py)[:, None]
+    f = np.exp(2j * math.pi * (a * m / px + b * l / py))
+    k = 2 * math.pi / lam
+    kx = 2 * math.pi * a / (px * dx)
+    ky = 2 * math.pi * b / (py * dy)
+    h = np.exp(1j * z * math.sqrt(k * k - kx * kx - ky * ky))
+    out = O.propagate(f, dy, dx, lam, z, 1.0)[0]
+    assert rel_l2(out, h * f) < 1e-12
+
+
 def test_parseval_pad1():
     f = normal(3, (3, 20, 24)) + 1j * normal(4, (3, 20, 24))
     out = O.propagate(f, 5e-6, 5e-6, 633e-9, 0.07, 1.0)
