@@ -568,6 +568,26 @@ struct Request {
   double* pw_out;
 };
 
+// One field-sized (or coherence-tensor-sized) scratch buffer per handle, grown on demand.
+top_status coh_scratch(top_handle h, size_t bytes, void** out) {
+  if (h->coh_bytes < bytes) {
+    if (h->coh) {
+      TOP_CUDA(cudaDeviceSynchronize(), "cudaDeviceSynchronize(coherence scratch growth)");
+      cudaFree(h->coh);
+      h->coh = nullptr;
+      h->coh_bytes = 0;
+    }
+    cudaError_t e = cudaMalloc(&h->coh, bytes);
+    if (e != cudaSuccess) {
+      h->coh = nullptr;
+      return cuda_fail(e, "cudaMalloc(coherence scratch)");
+    }
+    h->coh_bytes = bytes;
+  }
+  *out = h->coh;
+  return TOP_OK;
+}
+
 // ============================================================================= Bluestein path
 
 // In-place radix-2 FFT in float64, X[k] = sum_n x[n] exp(-2 pi i n k / L), L a power of two.
@@ -719,11 +739,25 @@ top_status modulate_fields(top_handle h, const top_grid* g, const Geometry& geo,
 // (intensity, overlap, modulation gradients) need a planned size.
 top_status run_bluestein(top_handle h, const Request& q, const Geometry& geo, cudaStream_t st) {
   const top_grid* g = q.g;
-  if (q.src_kind != SRC_FIELD || q.epi_kind != EPI_FIELD)
+  if (q.src_kind != SRC_FIELD || (q.epi_kind != EPI_FIELD && q.epi_kind != EPI_MODGRAD))
     return fail(TOP_ERR_UNSUPPORTED, "padded size %d x %d has no FFT plan of its own: its Bluestein transforms cover "
-                "top_propagate and top_propagate_backward without modulation gradients", geo.Py, geo.Px);
+                "top_propagate and top_propagate_backward", geo.Py, geo.Px);
   TOP_TRY(bind(h));
   const int64_t B = g->batch;
+  const long long plane = (long long)geo.ny * geo.nx;
+  if (q.epi_kind == EPI_MODGRAD) {
+    // the adjoint propagation into a scratch field, then the modulation's own backward (input
+    // gradient conj(M) g and the parameter gradients from the saved input)
+    void* scratch = nullptr;
+    TOP_TRY(coh_scratch(h, sizeof(float2) * size_t(B) * size_t(plane), &scratch));
+    Request r = q;
+    r.epi_kind = EPI_FIELD;
+    r.out = scratch;
+    r.mepi = nullptr;
+    r.grads = nullptr;
+    TOP_TRY(run_bluestein(h, r, geo, st));
+    return top_modulate_backward(h, g, q.mepi, scratch, q.out, q.grads, q.lam, q.n_lz, st);
+  }
   const int repeat = g->input_repeat > 1 ? g->input_repeat : 1;
   CztPlan cx, cy;
   TOP_TRY(czt_plan(h, geo.Px, &cx));
@@ -737,7 +771,6 @@ top_status run_bluestein(top_handle h, const Request& q, const Geometry& geo, cu
                   geo.Py, geo.Px);
     TOP_TRY(transfer_full_table(h, geo.Py, geo.Px, g->dy, g->dx, lam, z, method, st, &tables[b]));
   }
-  const long long plane = (long long)geo.ny * geo.nx;
   const long long wplane = (long long)geo.ny * geo.Px;
   const bool pre = q.msrc && q.msrc->flags;
   const bool post = q.mepi && q.mepi->flags;
@@ -1859,24 +1892,6 @@ top_status top_mse_loss(top_handle h, int64_t n, const float* intensity, const f
 
 // ----------------------------------------------------------------------------- mutual coherence
 
-static top_status coh_scratch(top_handle h, size_t bytes, void** out) {
-  if (h->coh_bytes < bytes) {
-    if (h->coh) {
-      TOP_CUDA(cudaDeviceSynchronize(), "cudaDeviceSynchronize(coherence scratch growth)");
-      cudaFree(h->coh);
-      h->coh = nullptr;
-      h->coh_bytes = 0;
-    }
-    cudaError_t e = cudaMalloc(&h->coh, bytes);
-    if (e != cudaSuccess) {
-      h->coh = nullptr;
-      return cuda_fail(e, "cudaMalloc(coherence scratch)");
-    }
-    h->coh_bytes = bytes;
-  }
-  *out = h->coh;
-  return TOP_OK;
-}
 
 // Mask parameters of a coherence modulation M(r) (single wavelength).
 static top_status coh_mask_params(top_handle h, const top_grid* g, const top_mod* mask, double lam, PassParams* p) {

@@ -102,6 +102,56 @@ def test_bluestein_per_field_parameters_repeat_and_modulations(T):
     assert rel_l2(gi, refb) < TOL
 
 
+def test_bluestein_backward_with_modulation_gradients(T):
+    """The phase, amplitude and complex-mask gradients of the modulation before the propagation,
+    shared by the batch, at a prime padded size (adjoint propagation, then the modulation's
+    backward)."""
+    B, ny, nx, pad, d = 3, 61, 45, 1.0, 5e-6  # 61 x 45 = 3^2 5
+    x = cfield(51, (B, ny, nx))
+    lams = np.array([450e-9, 520e-9, 700e-9])
+    z = 3e-3
+    phi = uniform(53, (ny, nx), -np.pi, np.pi).astype(np.float32)
+    amp = uniform(54, (ny, nx), 0.2, 1.0).astype(np.float32)
+    cm = to_c64(np.exp(1j * uniform(55, (ny, nx), 0, 6.28)) * 0.8)
+    pre = T.Modulation(phase=dev(phi), amplitude=dev(amp), mask=dev(cm), radius=100e-6)
+    post = T.Modulation(focal_length=0.05)
+    g = cfield(57, (B, ny, nx))
+    gp = torch.zeros((ny, nx), dtype=torch.float32, device="cuda")
+    ga = torch.zeros_like(gp)
+    gm = torch.zeros((ny, nx), dtype=torch.complex64, device="cuda")
+    gi = host(T.top_propagate_backward(dev(g), d, d, lams, z, pad, pre=pre, post=post, saved_in=dev(x),
+                                       grad_phase=gp, grad_amplitude=ga, grad_mask=gm))
+    gy = np.stack([O.propagate_adjoint(g[i] * np.conj(O.lens(ny, nx, d, d, lams[i], 0.05)), d, d, lams[i], z,
+                                       pad)[0] for i in range(B)])
+    M = O.circ(ny, nx, d, d, 100e-6) * cm * amp * np.exp(1j * phi.astype(np.float64))
+    X = x.astype(np.complex128)
+    assert rel_l2(gi, np.conj(M) * gy) < TOL
+    assert rel_l2(host(gp), np.imag(gy * np.conj(M * X)).sum(0)) < TOL
+    assert rel_l2(host(ga), np.real(np.conj(gy) * (M / amp) * X).sum(0)) < TOL
+    assert rel_l2(host(gm), (gy * np.conj((M / cm) * X)).sum(0)) < TOL
+
+
+def test_bluestein_autograd_phase_mask(T):
+    """autograd.propagate with a trainable phase mask at a Bluestein size: the mask gradient of
+    L = sum w |y|^2 (a fixed detector weight w; at padding 1 the unweighted sum would not depend
+    on the mask) against the oracle (g = 2 w y)."""
+    ny, nx, pad, d, lam, z = 37, 37, 1.0, 4e-6, 600e-9, 2e-3
+    x = cfield(59, (2, ny, nx))
+    phi = uniform(61, (ny, nx), -np.pi, np.pi).astype(np.float32)
+    w = uniform(63, (ny, nx), 0.0, 1.0)
+    from paper_2411_18591_gb300 import autograd as A
+    xt = dev(x)
+    pt = dev(phi).requires_grad_(True)
+    y = A.propagate(xt, d, d, lam, z, pad, phase=pt)
+    (dev(w.astype(np.float32)) * y.abs() ** 2).sum().backward()
+    M = np.exp(1j * phi.astype(np.float64))
+    X = x.astype(np.complex128)
+    yo = O.propagate(X * M, d, d, lam, z, pad)
+    gy = O.propagate_adjoint(2 * w * yo, d, d, lam, z, pad)
+    assert rel_l2(host(y.detach()), yo) < TOL
+    assert rel_l2(host(pt.grad), np.imag(gy * np.conj(M * X)).sum(0)) < TOL
+
+
 def test_bluestein_limits_are_reported(T):
     x = dev(cfield(43, (1, 61, 61)))
     with pytest.raises(T.TopError, match="Direct Integration"):
