@@ -42,6 +42,15 @@ __device__ __forceinline__ long long ws_index(int kpos, int y, int ny) {
   return ((long long)(kpos >> 2) * ny + y) * 4 + (kpos & 3);
 }
 
+// A two-stage plan holds one radix-RL butterfly per thread (E == RL): lane t of half r holds the
+// bins kbase(t) + e M/RL, and with M/RL a multiple of 4 their workspace samples in row y sit at
+// ws_index(r M + kbase(t), y) + e (M/RL) ny. Returns that first sample; the step is (M/RL) ny.
+template <class EN>
+__device__ __forceinline__ long long direct_base(int r, int t, int y, int ny) {
+  static_assert(EN::E == EN::RL && (EN::M / EN::RL) % 4 == 0, "direct bins need one butterfly a thread");
+  return ws_index(r * EN::M + EN::kbase(t), y, ny);
+}
+
 // Rows per block of the row passes; two thread groups (the two halves) per row. Two-stage plans
 // move their bins directly between registers and the workspace (DIRECT); deeper plans stage them
 // through a shared tile [2M][LD].
@@ -345,8 +354,10 @@ __device__ __forceinline__ void forward_rows(const PassParams& p, int f, int y0,
   if constexpr (SH::DIRECT) {
     // bins straight to the workspace: four consecutive lanes fill one 32-byte sector
     if (row < nrows) {
+      float2* wp = ws + direct_base<EX>(r, t, y0 + row, ny);
+      const int step = (M / EX::RL) * ny;
 #pragma unroll
-      for (int e = 0; e < E; ++e) ws[ws_index(r * M + EX::bin(t, e), y0 + row, ny)] = v[e];
+      for (int e = 0; e < E; ++e) wp[e * step] = v[e];
     }
   } else {
     __syncthreads();  // the exchange buffers alias the tile
@@ -801,6 +812,25 @@ __device__ __forceinline__ void combine_rows(const PassParams& p, const FieldSet
       const int y = y0 + rr;
       const int2 rg = (m.flags & TOP_MOD_CIRC) ? __ldg(m.circ + y) : make_int2(0, p.nx - 1);
       const float2 ly = (m.flags & TOP_MOD_LENS) ? ldg2(fs.epi_ly + y) : make_float2(1.f, 0.f);
+      if constexpr (X2 && (M / 2) % NT == 0) {
+        // nx = M: the lower half of the row combines e + o from slots M/2 on, the upper half e - o
+        // from slot 0 on, a fixed number of samples a thread in each
+        const float2* ev = smem + rr * M;
+        const float2* od = smem + (ROWS + rr) * M;
+#pragma unroll 4
+        for (int i = 0; i < M / 2 / NT; ++i) {
+          const int x = threadIdx.x + i * NT;
+          epilogue_planes<KIND>(p, fs, *ep, f, first, y, x, rr * M + x, ly, rg,
+                                c_add(ev[x + M / 2], od[x + M / 2]), acc);
+        }
+#pragma unroll 4
+        for (int i = 0; i < M / 2 / NT; ++i) {
+          const int x = M / 2 + threadIdx.x + i * NT;
+          epilogue_planes<KIND>(p, fs, *ep, f, first, y, x, rr * M + x, ly, rg,
+                                c_sub(ev[x - M / 2], od[x - M / 2]), acc);
+        }
+        continue;
+      }
       for (int x = threadIdx.x; x < p.nx; x += NT) {
         int pos;
         bool upper;
@@ -860,10 +890,15 @@ __device__ __forceinline__ void inverse_rows(const PassParams& p, int f, int y0,
   float2 v[E];
   if constexpr (SH::DIRECT) {
     // bins straight from the workspace: four consecutive lanes read one 32-byte sector
-    const bool valid = row < nrows;
+    if (row < nrows) {
+      const float2* wp = ws + direct_base<EX>(r, t, y0 + row, ny);
+      const int step = (M / EX::RL) * ny;
 #pragma unroll
-    for (int e = 0; e < E; ++e)
-      v[e] = valid ? ws[ws_index(r * M + EX::bin(t, e), y0 + row, ny)] : make_float2(0.f, 0.f);
+      for (int e = 0; e < E; ++e) v[e] = wp[e * step];
+    } else {
+#pragma unroll
+      for (int e = 0; e < E; ++e) v[e] = make_float2(0.f, 0.f);
+    }
   } else {
     // the tile [2M][LD] from the workspace in address order (ROWS rows x 4 lines per block)
     for (int i = threadIdx.x; i < 2 * M * ROWS; i += NT) {
@@ -1084,6 +1119,27 @@ __global__ void __launch_bounds__(RowShape<EX>::THREADS, RowShape<EX>::MINB_INV)
   const SrcPlanes sp = stage_src_planes<EX>(pb, f, y0, nrows, reinterpret_cast<float*>(smem + chain_planes_off<EX>(nx)));
   inverse_rows<EX, X2>(pa, f, y0, nrows, smem, grp, t);
   __syncthreads();
+  if constexpr (X2 && (M / 2) % NT == 0) {
+    // nx = M: lower half e + o from slots M/2 on, upper half e - o from slot 0 on
+    for (int rr = 0; rr < ROWS; ++rr) {
+      const float2* ev = smem + rr * M;
+      const float2* od = smem + (ROWS + rr) * M;
+      float2* out = pa.out ? pa.out + (long long)f * pa.out_stride + (long long)(y0 + rr) * nx : nullptr;
+      const bool live = rr < nrows;
+#pragma unroll 4
+      for (int i = 0; i < M / NT; ++i) {
+        const int x = threadIdx.x + i * NT;
+        const bool upper = i >= M / 2 / NT;
+        const int pos = upper ? x - M / 2 : x + M / 2;
+        float2 val = make_float2(0.f, 0.f);
+        if (live) {
+          val = upper ? c_sub(ev[pos], od[pos]) : c_add(ev[pos], od[pos]);
+          if (out) out[x] = val;
+        }
+        rows[rr * M + x] = val;
+      }
+    }
+  } else {
   for (int rr = 0; rr < ROWS; ++rr) {
     for (int x = threadIdx.x; x < nx; x += NT) {
       float2 val = make_float2(0.f, 0.f);
@@ -1105,6 +1161,7 @@ __global__ void __launch_bounds__(RowShape<EX>::THREADS, RowShape<EX>::MINB_INV)
       }
       rows[rr * nx + x] = val;
     }
+  }
   }
   top_cp_async_wait_all();
   __syncthreads();
