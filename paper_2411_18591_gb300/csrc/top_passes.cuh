@@ -876,45 +876,34 @@ __device__ __forceinline__ void combine_rows(const PassParams& p, const FieldSet
   }
 }
 
-// Load the bins of rows y0 .. y0 + nrows - 1 of field f, inverse-transform them and leave both
-// halves in natural order in shared memory [r][ROWS][M] at `smem`, the odd one times
-// exp(2 pi i pos / P). Ends before the barrier that makes the halves visible.
-template <class EX, bool X2>
-__device__ __forceinline__ void inverse_rows(const PassParams& p, int f, int y0, int nrows, float2* smem, int grp,
-                                             int t) {
-  using SH = RowShape<EX>;
-  constexpr int E = EX::E, M = EX::M, ROWS = SH::ROWS, LD = SH::LD, NT = SH::THREADS;
+// Bins of this thread's half row (row y0 + row of field f) straight from the workspace into
+// registers (two-stage plans): four consecutive lanes read one 32-byte sector.
+template <class EX>
+__device__ __forceinline__ void load_bins(const PassParams& p, int f, int y0, int nrows, int grp, int t,
+                                          float2 (&v)[EX::E]) {
+  constexpr int E = EX::E, M = EX::M;
   const int row = grp >> 1, r = grp & 1;
-  const int ny = p.ny;
-  const float2* ws = p.ws + (long long)f * p.ws_stride;
-  float2 v[E];
-  if constexpr (SH::DIRECT) {
-    // bins straight from the workspace: four consecutive lanes read one 32-byte sector
-    if (row < nrows) {
-      const float2* wp = ws + direct_base<EX>(r, t, y0 + row, ny);
-      const int step = (M / EX::RL) * ny;
+  if (row < nrows) {
+    const float2* wp = p.ws + (long long)f * p.ws_stride + direct_base<EX>(r, t, y0 + row, p.ny);
+    const int step = (M / EX::RL) * p.ny;
 #pragma unroll
-      for (int e = 0; e < E; ++e) v[e] = wp[e * step];
-    } else {
-#pragma unroll
-      for (int e = 0; e < E; ++e) v[e] = make_float2(0.f, 0.f);
-    }
+    for (int e = 0; e < E; ++e) v[e] = wp[e * step];
   } else {
-    // the tile [2M][LD] from the workspace in address order (ROWS rows x 4 lines per block)
-    for (int i = threadIdx.x; i < 2 * M * ROWS; i += NT) {
-      const int c = i & 3, q = i >> 2;
-      const int yo = q % ROWS, blk = q / ROWS;
-      smem[SH::tslot(4 * blk + c) * LD + yo] =
-          yo < nrows ? ws[((long long)blk * ny + y0 + yo) * 4 + c] : make_float2(0.f, 0.f);
-    }
-    __syncthreads();
 #pragma unroll
-    for (int e = 0; e < E; ++e) v[e] = smem[SH::tslot(r * M + EX::bin(t, e)) * LD + row];
-    __syncthreads();  // the tile aliases the exchange buffers
+    for (int e = 0; e < E; ++e) v[e] = make_float2(0.f, 0.f);
   }
+}
+
+// Inverse-transform the bins in v and leave both halves in natural order in shared memory
+// [r][ROWS][M] at `smem`, the odd one times exp(2 pi i pos / P). Ends before the barrier that makes
+// the halves visible.
+template <class EX, bool X2>
+__device__ __forceinline__ void inverse_halves(const PassParams& p, float2 (&v)[EX::E], float2* smem, int grp, int t) {
+  using SH = RowShape<EX>;
+  constexpr int E = EX::E, M = EX::M, ROWS = SH::ROWS;
+  const int row = grp >> 1, r = grp & 1;
   EX::inv(v, smem + grp * EX::BUF, t, p.twx);
   __syncthreads();  // the exchange buffers alias the half-row buffers
-  // both halves in natural order -> shared [r][ROWS][M], the odd one times exp(2 pi i pos / P)
   float2* hrow = smem + (r * ROWS + row) * M;
   if (r) {
     if constexpr (X2) {
@@ -936,6 +925,36 @@ __device__ __forceinline__ void inverse_rows(const PassParams& p, int f, int y0,
 #pragma unroll
     for (int e = 0; e < E; ++e) hrow[EX::in_pos(t, e)] = v[e];
   }
+}
+
+// Load the bins of rows y0 .. y0 + nrows - 1 of field f, inverse-transform them and leave both
+// halves in natural order in shared memory [r][ROWS][M] at `smem`, the odd one times
+// exp(2 pi i pos / P). Ends before the barrier that makes the halves visible.
+template <class EX, bool X2>
+__device__ __forceinline__ void inverse_rows(const PassParams& p, int f, int y0, int nrows, float2* smem, int grp,
+                                             int t) {
+  using SH = RowShape<EX>;
+  constexpr int E = EX::E, M = EX::M, ROWS = SH::ROWS, LD = SH::LD, NT = SH::THREADS;
+  const int row = grp >> 1, r = grp & 1;
+  const int ny = p.ny;
+  const float2* ws = p.ws + (long long)f * p.ws_stride;
+  float2 v[E];
+  if constexpr (SH::DIRECT) {
+    load_bins<EX>(p, f, y0, nrows, grp, t, v);
+  } else {
+    // the tile [2M][LD] from the workspace in address order (ROWS rows x 4 lines per block)
+    for (int i = threadIdx.x; i < 2 * M * ROWS; i += NT) {
+      const int c = i & 3, q = i >> 2;
+      const int yo = q % ROWS, blk = q / ROWS;
+      smem[SH::tslot(4 * blk + c) * LD + yo] =
+          yo < nrows ? ws[((long long)blk * ny + y0 + yo) * 4 + c] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < E; ++e) v[e] = smem[SH::tslot(r * M + EX::bin(t, e)) * LD + row];
+    __syncthreads();  // the tile aliases the exchange buffers
+  }
+  inverse_halves<EX, X2>(p, v, smem, grp, t);
 }
 
 template <class EX, bool X2>
@@ -1020,14 +1039,24 @@ __global__ void __launch_bounds__(RowShape<EX>::THREADS, RowShape<EX>::MINB_INV)
     }
   };
 
+  // two-stage plans load the next field's bins into the registers the transform has freed while
+  // the current field's halves are combined, so the loads overlap the epilogue
+  float2 v[E];
+  if constexpr (SH::DIRECT) load_bins<EX>(p, f0, y0, nrows, grp, t, v);
 #pragma unroll 1
   for (int f = f0; f < f1; ++f) {
     const FieldSet& fs = p.sets[p.set_of[f]];
-    const float2* ws = p.ws + (long long)f * p.ws_stride;
     if (staged) stage_field(f);
-    inverse_rows<EX, X2>(p, f, y0, nrows, smem, grp, t);
+    if constexpr (SH::DIRECT) {
+      inverse_halves<EX, X2>(p, v, smem, grp, t);
+    } else {
+      inverse_rows<EX, X2>(p, f, y0, nrows, smem, grp, t);
+    }
     if (staged) top_cp_async_wait_all();
     __syncthreads();
+    if constexpr (SH::DIRECT) {
+      if (f + 1 < f1) load_bins<EX>(p, f + 1, y0, nrows, grp, t, v);
+    }
     // combine the halves over the cropped window, epilogue, coalesced store
     const EpiPlanes* epp = staged ? &ep : nullptr;
     OvAcc acc{0.0, 0.0, 0.0};
