@@ -133,16 +133,20 @@ def bus_id_of(dev_index: int):
 # ----------------------------------------------------------------------------- CPU oracle sample
 
 def oracle_sample_step(obj_field, lam, fourf_cfg, phase, target):
-    """The oracle (FP64, host) on one field of the workload: 4 forward + 2 backward propagations."""
+    """The oracle (FP64, host) on one field of the workload: 4 forward + 2 backward propagations.
+    Returns (seconds, loss, pupil-phase gradient)."""
     import oracle as O
     c = fourf_cfg
     t0 = time.perf_counter()
     loss, g_phi, _ = O.fourf_loss_and_grad(obj_field[None], [lam], c["d"], c["f"], c["lens_radius"],
                                            c["pupil_radius"], phase, 1, target[None], c["pad"])
-    return time.perf_counter() - t0
+    return time.perf_counter() - t0, loss, g_phi
 
 
-def cpu_baseline(steps: int, warmup: int, budget_s: float = 25.0):
+def cpu_baseline(steps: int, warmup: int, budget_s: float = 25.0, want_sample: bool = False):
+    """The oracle timed on one field of the workload. With want_sample, also returns that field's
+    inputs and the oracle's results on it (the 4f loss and pupil-phase gradient, and one AS
+    propagation and its adjoint of the object field), for the parity of the GPU line."""
     n = S.CFG4["n"]
     c = S.CFG4
     obj = S.cfg4_objects(1, 1, n)[0, 0].astype(np.complex128)
@@ -152,18 +156,51 @@ def cpu_baseline(steps: int, warmup: int, budget_s: float = 25.0):
     cfg = dict(d=c["d"], f=c["f"], lens_radius=c["lens_radius"], pupil_radius=c["pupil_radius"], pad=c["pad"])
     times = []
     t_start = time.perf_counter()
+    loss = g_phi = None
     for i in range(warmup + steps):
-        dt = oracle_sample_step(obj, lam, cfg, phase, target)
+        dt, loss, g_phi = oracle_sample_step(obj, lam, cfg, phase, target)
         if i >= warmup:
             times.append(dt)
         if time.perf_counter() - t_start > budget_s and len(times) >= 1:
             break
     per = statistics.median(times)
     units = (4 + 2) / 2.0
-    return {"value": units / per, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "1 of 384 fields (object 0, Ex, 450 nm): the full 4f chain in float64 numpy "
-                      "(4 forward + 2 backward propagations, 2048^2 FFTs), loss on that field's intensity; "
-                      f"{len(times)} timed of {warmup + len(times)} runs, median {per:.2f} s per field"}
+    cb = {"value": units / per, "unit": UNIT, "cores": 1, "kind": "oracle",
+          "sample": "1 of 384 fields (object 0, Ex, 450 nm): the full 4f chain in float64 numpy "
+                    "(4 forward + 2 backward propagations, 2048^2 FFTs), loss on that field's intensity; "
+                    f"{len(times)} timed of {warmup + len(times)} runs, median {per:.2f} s per field"}
+    if not want_sample:
+        return cb
+    import oracle as O
+    fwd = O.propagate(obj[None], c["d"], c["d"], lam, c["f"], c["pad"])[0]
+    bwd = O.propagate_adjoint(obj[None], c["d"], c["d"], lam, c["f"], c["pad"])[0]
+    sample = dict(obj=obj, lam=lam, phase=phase, target=target, loss=float(loss), g_phi=g_phi, fwd=fwd, bwd=bwd)
+    return cb, sample
+
+
+def gpu_parity(dev, sample):
+    """rel-L2 of the GPU path against the oracle's results on the sampled field: one AS propagation
+    and its adjoint (the unit of the metric), and the 4f step's loss and pupil-phase gradient."""
+    import torch
+    from paper_2411_18591_gb300 import binding as Bd
+    from paper_2411_18591_gb300.fourf import FourF
+    c = S.CFG4
+    rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    x = torch.from_numpy(sample["obj"].astype(np.complex64)[None]).to(dev)
+    fwd = Bd.top_propagate(x, c["d"], c["d"], sample["lam"], c["f"], c["pad"]).cpu().numpy()[0]
+    bwd = Bd.top_propagate_backward(x, c["d"], c["d"], sample["lam"], c["f"], c["pad"]).cpu().numpy()[0]
+    one = FourF(n=c["n"], d=c["d"], f=c["f"], lens_radius=c["lens_radius"], pupil_radius=c["pupil_radius"],
+                objects=1, comps=1, wavelengths=(sample["lam"],), pad=c["pad"])
+    phase = torch.from_numpy(sample["phase"].astype(np.float32)).to(dev)
+    target = torch.from_numpy(sample["target"].astype(np.float32)[None]).to(dev)
+    gphase = torch.empty_like(phase)
+    loss, _ = one.step(x, phase, target, gphase)
+    torch.cuda.synchronize()
+    return {"rel_l2_propagate": rel(fwd, sample["fwd"]), "rel_l2_propagate_backward": rel(bwd, sample["bwd"]),
+            "rel_err_fourf_loss": abs(float(loss.item()) - sample["loss"]) / abs(sample["loss"]),
+            "rel_l2_fourf_pupil_grad": rel(gphase.cpu().numpy().astype(np.float64), sample["g_phi"]),
+            "sample": "object 0, Ex, 450 nm of the workload (1024^2, 2x padding) against the float64 oracle",
+            "tolerance": 1e-5}
 
 
 # ----------------------------------------------------------------------------- reference arm
@@ -391,7 +428,8 @@ def run_ours(args, rank, world):
     if rank == 0 and world == 1 and not args.no_context:
         line["context"] = context_paths(dev, c)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(2, 0)
+        line["cpu_baseline"], sample = cpu_baseline(2, 0, want_sample=True)
+        line["parity"] = gpu_parity(dev, sample)
     if rank == 0:
         print(json.dumps(line), flush=True)
 
