@@ -72,7 +72,7 @@ struct TransferEntry {
 struct CztPlan {
   int L = 0;
   const float2* chirp = nullptr;
-  const float2* bh_fwd = nullptr;
+  const float2* bh_fwd = nullptr;  // in the engine's slot order
   const float2* bh_inv = nullptr;
   const float2* tw = nullptr;
 };
@@ -613,6 +613,27 @@ void host_fft(std::vector<std::complex<double>>& a) {
   }
 }
 
+// The frequency bin that lane t of an engine holds in slot e after its forward transform (the
+// engine's digit-reversed output order): slot e = q RL + j holds bin kbase(t + G q) + j M / RL, where
+// kbase gathers the digits of stages 0 .. NS-2 of the position (t + G q) RL.
+int engine_bin(const EngineInfo& info, int t, int e) {
+  const int NS = info.NS, RL = info.R[NS - 1];
+  auto span = [&](int s) {
+    int p = 1;
+    for (int i = s + 1; i < NS; ++i) p *= info.R[i];
+    return p;
+  };
+  auto weight = [&](int s) {
+    int p = 1;
+    for (int i = 0; i < s; ++i) p *= info.R[i];
+    return p;
+  };
+  const int q = e / RL, j = e % RL, b = t + info.G * q;
+  int k = 0;
+  for (int s = 0; s < NS - 1; ++s) k += ((b / (span(s) / RL)) % info.R[s]) * weight(s);
+  return k + j * (info.M / RL);
+}
+
 // Tables of the Bluestein transforms of length P: c[n] = exp(-i pi n^2 / P) with n^2 reduced
 // modulo 2 P in integers (exact), and the L-point transforms of conj(c) and c on the lags
 // (-P, P) wrapped modulo L, in float64, rounded once.
@@ -643,11 +664,18 @@ top_status czt_plan(top_handle h, int P, CztPlan* out) {
   }
   host_fft(bf);
   host_fft(bi);
+  // in the engine's slot order: entry e G + t holds the bin that lane t keeps in slot e after the
+  // forward transform, so a warp reads consecutive entries
+  EngineInfo info;
+  if (!find_engine(L, &info)) return fail(TOP_ERR_INTERNAL, "no %d-point engine for the Bluestein transforms", L);
   std::vector<float2> hf(L), hi(L);
-  for (int k = 0; k < L; ++k) {
-    hf[k] = make_float2(float(bf[k].real()), float(bf[k].imag()));
-    hi[k] = make_float2(float(bi[k].real()), float(bi[k].imag()));
-  }
+  const int E = L / info.G;
+  for (int t = 0; t < info.G; ++t)
+    for (int e = 0; e < E; ++e) {
+      const int k = engine_bin(info, t, e);
+      hf[size_t(e) * info.G + t] = make_float2(float(bf[k].real()), float(bf[k].imag()));
+      hi[size_t(e) * info.G + t] = make_float2(float(bi[k].real()), float(bi[k].imag()));
+    }
   CztPlan plan;
   plan.L = L;
   float2 *dc = nullptr, *df = nullptr, *di = nullptr;

@@ -24,13 +24,14 @@ struct CztShape {
   static constexpr int MINB = 4;  // 128 registers a thread
 };
 
-// conv = IFFT_L(FFT_L(v) * bh) (unnormalised), natural order in and out
+// conv = IFFT_L(FFT_L(v) * bh) (unnormalised), natural order in and out; bh in the engine's slot
+// order (entry e G + t: the bin lane t holds in slot e), so a warp's reads are consecutive
 template <class EN>
 __device__ __forceinline__ void czt_convolve(float2 (&v)[EN::E], float2* buf, int t, const float2* __restrict__ tw,
                                              const float2* __restrict__ bh) {
   EN::fwd(v, buf, t, tw);
 #pragma unroll
-  for (int e = 0; e < EN::E; ++e) v[e] = c_mul(v[e], __ldg(bh + EN::bin(t, e)));
+  for (int e = 0; e < EN::E; ++e) v[e] = c_mul(v[e], __ldg(bh + e * EN::G + t));
   EN::inv(v, buf, t, tw);
 }
 

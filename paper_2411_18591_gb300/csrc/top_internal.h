@@ -152,8 +152,8 @@ struct CztParams {
   int adjoint;
   float inv_l;           // 1 / L
   const float2* chirp;   // c[n], n < P
-  const float2* bh_fwd;  // L-point transform of conj(c) on (-P, P), natural order
-  const float2* bh_inv;  // L-point transform of c on (-P, P)
+  const float2* bh_fwd;  // L-point transform of conj(c) on (-P, P), entry e G + t = the bin of lane t, slot e
+  const float2* bh_inv;  // L-point transform of c on (-P, P), same order
   const float2* tw;      // stage twiddles of the L-point engine
   const float2* const* h;  // CZT_FILTER: per field, rows [line][P] of H / (Py Px) in natural order
 };
