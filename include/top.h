@@ -153,10 +153,10 @@ double top_zcritical(double L, double dx, double lambda);
  * pre, post: modulations or NULL.
  * Padded sizes without an FFT plan of their own (odd, or with prime factors above 5; up to
  * 2048 per axis) use Bluestein line transforms: the same result (a DFT of length P per axis),
- * with the modulations as separate passes (top_propagate_backward's modulation gradients
- * follow from the adjoint propagation by the modulation's own backward); TOP_DI is rejected
- * there (TOP_ERR_UNSUPPORTED), and so are the fused variants (intensity, overlap, chains, ragged
- * batches, the no-alloc call), which need a planned size. */
+ * with modulations, intensities and the intensity backward's source as separate passes, and
+ * modulation gradients from the adjoint propagation by the modulation's own backward; this holds
+ * for the backward, intensity, chain and ragged calls too. TOP_DI, the overlap calls and the
+ * no-alloc call need a planned size there (TOP_ERR_UNSUPPORTED). */
 top_status top_propagate(top_handle h, const top_grid* g, const void* in, void* out,
                          const double* lambda, const double* z, int64_t n_lz,
                          const top_mod* pre, const top_mod* post, void* stream);

@@ -84,6 +84,8 @@ struct top_ctx {
   size_t ws_bytes = 0;
   void* coh = nullptr;  // one coherence tensor of scratch for the transposes
   size_t coh_bytes = 0;
+  void* chain = nullptr;  // the intermediate fields of a chain at a padded size without a plan
+  size_t chain_bytes = 0;
   std::vector<void*> allocs;  // cached tables, freed with the handle
   std::map<int, float2*> eng_tw;
   std::map<int, float2*> split_tw;
@@ -568,22 +570,28 @@ struct Request {
   double* pw_out;
 };
 
-// One field-sized (or coherence-tensor-sized) scratch buffer per handle, grown on demand.
-top_status coh_scratch(top_handle h, size_t bytes, void** out) {
-  if (h->coh_bytes < bytes) {
-    if (h->coh) {
-      TOP_CUDA(cudaDeviceSynchronize(), "cudaDeviceSynchronize(coherence scratch growth)");
-      cudaFree(h->coh);
-      h->coh = nullptr;
-      h->coh_bytes = 0;
+// A scratch buffer owned by the handle, grown on demand (the previous contents are not kept).
+top_status grow_scratch(void** buf, size_t* have, size_t bytes, const char* what) {
+  if (*have < bytes) {
+    if (*buf) {
+      TOP_CUDA(cudaDeviceSynchronize(), "cudaDeviceSynchronize(scratch growth)");
+      cudaFree(*buf);
+      *buf = nullptr;
+      *have = 0;
     }
-    cudaError_t e = cudaMalloc(&h->coh, bytes);
+    cudaError_t e = cudaMalloc(buf, bytes);
     if (e != cudaSuccess) {
-      h->coh = nullptr;
-      return cuda_fail(e, "cudaMalloc(coherence scratch)");
+      *buf = nullptr;
+      return cuda_fail(e, what);
     }
-    h->coh_bytes = bytes;
+    *have = bytes;
   }
+  return TOP_OK;
+}
+
+// One field-sized (or coherence-tensor-sized) scratch buffer per handle.
+top_status coh_scratch(top_handle h, size_t bytes, void** out) {
+  TOP_TRY(grow_scratch(&h->coh, &h->coh_bytes, bytes, "cudaMalloc(coherence scratch)"));
   *out = h->coh;
   return TOP_OK;
 }
@@ -760,32 +768,15 @@ top_status modulate_fields(top_handle h, const top_grid* g, const Geometry& geo,
   return TOP_OK;
 }
 
-// A propagation whose padded size has no plan of its own (odd, or with prime factors above 5),
-// up to 2048 points per axis: rows by Bluestein forward transforms, a transpose, each column's
-// forward transform, H and inverse transform in one Bluestein line pass, a transpose back and the
-// rows' inverse transforms with the crop. Modulations run as separate passes; fused epilogues
-// (intensity, overlap, modulation gradients) need a planned size.
-top_status run_bluestein(top_handle h, const Request& q, const Geometry& geo, cudaStream_t st) {
+// A field-to-field propagation (modulations before and after as separate passes) whose padded
+// size has no plan of its own (odd, or with prime factors above 5), up to 2048 points per axis:
+// rows by Bluestein forward transforms, a transpose, each column's forward transform, H and
+// inverse transform in one Bluestein line pass, a transpose back and the rows' inverse
+// transforms with the crop.
+top_status bluestein_fields(top_handle h, const Request& q, const Geometry& geo, cudaStream_t st) {
   const top_grid* g = q.g;
-  if (q.src_kind != SRC_FIELD || (q.epi_kind != EPI_FIELD && q.epi_kind != EPI_MODGRAD))
-    return fail(TOP_ERR_UNSUPPORTED, "padded size %d x %d has no FFT plan of its own: its Bluestein transforms cover "
-                "top_propagate and top_propagate_backward", geo.Py, geo.Px);
-  TOP_TRY(bind(h));
   const int64_t B = g->batch;
   const long long plane = (long long)geo.ny * geo.nx;
-  if (q.epi_kind == EPI_MODGRAD) {
-    // the adjoint propagation into a scratch field, then the modulation's own backward (input
-    // gradient conj(M) g and the parameter gradients from the saved input)
-    void* scratch = nullptr;
-    TOP_TRY(coh_scratch(h, sizeof(float2) * size_t(B) * size_t(plane), &scratch));
-    Request r = q;
-    r.epi_kind = EPI_FIELD;
-    r.out = scratch;
-    r.mepi = nullptr;
-    r.grads = nullptr;
-    TOP_TRY(run_bluestein(h, r, geo, st));
-    return top_modulate_backward(h, g, q.mepi, scratch, q.out, q.grads, q.lam, q.n_lz, st);
-  }
   const int repeat = g->input_repeat > 1 ? g->input_repeat : 1;
   CztPlan cx, cy;
   TOP_TRY(czt_plan(h, geo.Px, &cx));
@@ -899,6 +890,58 @@ top_status run_bluestein(top_handle h, const Request& q, const Geometry& geo, cu
                               out + pos * plane, st));
   }
   return TOP_OK;
+}
+
+// The propagation calls at padded sizes without a plan of their own: the intensity backward's
+// source (2 w gI psi) and the detector intensity (Eq. 14) run as separate passes around
+// bluestein_fields, and modulation gradients follow the adjoint propagation through the
+// modulation's own backward. The overlap epilogue needs a planned size.
+top_status run_bluestein(top_handle h, const Request& q, const Geometry& geo, cudaStream_t st) {
+  const top_grid* g = q.g;
+  if (q.epi_kind == EPI_OVERLAP)
+    return fail(TOP_ERR_UNSUPPORTED, "padded size %d x %d has no FFT plan of its own: the overlap epilogue needs "
+                "a planned size (the Bluestein transforms cover the other propagation calls)", geo.Py, geo.Px);
+  TOP_TRY(bind(h));
+  const int64_t B = g->batch;
+  const long long plane = (long long)geo.ny * geo.nx;
+  const bool need_src = q.src_kind == SRC_INTENSITY;
+  const bool need_field = q.epi_kind == EPI_MODGRAD || (q.epi_kind == EPI_INTENSITY && !q.out);
+  float2* scratch = nullptr;
+  if (need_src || need_field) {
+    void* p = nullptr;
+    TOP_TRY(coh_scratch(h, sizeof(float2) * size_t(B) * size_t(plane) * size_t(int(need_src) + int(need_field)), &p));
+    scratch = static_cast<float2*>(p);
+  }
+  float2* src_buf = scratch;
+  float2* field_buf = need_src ? scratch + B * plane : scratch;
+  Request r = q;
+  if (need_src) {
+    TOP_TRY(timed(h, KK_AUX, st, "intensity source", [&] {
+      return launch_intensity_source(static_cast<const float2*>(q.psi_src), q.gI, q.weights, int(q.group), B, plane,
+                                     src_buf, st);
+    }));
+    r.src_kind = SRC_FIELD;
+    r.in = src_buf;
+  }
+  if (q.epi_kind == EPI_FIELD) return bluestein_fields(h, r, geo, st);
+  if (q.epi_kind == EPI_MODGRAD) {
+    // the adjoint propagation into a scratch field, then the modulation's own backward (input
+    // gradient conj(M) g and the parameter gradients from the saved input)
+    r.epi_kind = EPI_FIELD;
+    r.out = field_buf;
+    r.mepi = nullptr;
+    r.grads = nullptr;
+    TOP_TRY(bluestein_fields(h, r, geo, st));
+    return top_modulate_backward(h, g, q.mepi, field_buf, q.out, q.grads, q.lam, q.n_lz, st);
+  }
+  // EPI_INTENSITY: the (modulated) field, kept in field_out when given, then the group sums
+  float2* field = q.out ? static_cast<float2*>(q.out) : field_buf;
+  r.epi_kind = EPI_FIELD;
+  r.out = field;
+  TOP_TRY(bluestein_fields(h, r, geo, st));
+  return timed(h, KK_AUX, st, "intensity", [&] {
+    return launch_intensity_sum(field, q.weights, int(q.group), B / q.group, plane, q.outf, st);
+  });
 }
 
 top_status run_propagation(top_handle h, const Request& q, cudaStream_t st) {
@@ -1187,7 +1230,6 @@ top_status run_chain(top_handle h, const top_grid* g, const void* in, void* out,
                      const double* lam, int64_t n_lz, const top_stage* stages, int K, cudaStream_t st) {
   Geometry geo;
   TOP_TRY(check_grid(g, &geo));
-  TOP_TRY(check_engines(geo));
   TOP_TRY(check_lz(g, lam, nullptr, n_lz, false));
   if (!stages || K < 1) return fail(TOP_ERR_INVALID_ARG, "a chain needs at least one stage");
   for (int k = 0; k < K; ++k) {
@@ -1213,6 +1255,40 @@ top_status run_chain(top_handle h, const top_grid* g, const void* in, void* out,
       if (stages[k].keep == in) return fail(TOP_ERR_INVALID_ARG, "input_repeat > 1 needs keep buffers apart from the input");
   }
   TOP_TRY(bind(h));
+  if (!has_engines(geo)) {
+    // a padded size without a plan of its own: the stages one by one through the Bluestein path,
+    // each stage's field to its keep buffer or to one scratch field set (in place from the second
+    // stage on), the last stage's to out and the intensity
+    for (int P : {geo.Py, geo.Px})
+      if (2 * P - 1 > 4096) TOP_TRY(check_engines(geo));
+    const long long plane = (long long)geo.ny * geo.nx;
+    TOP_TRY(grow_scratch(&h->chain, &h->chain_bytes, sizeof(float2) * size_t(B) * size_t(plane),
+                         "cudaMalloc(chain scratch)"));
+    float2* tmp = static_cast<float2*>(h->chain);
+    const void* cur = in;
+    for (int k = 0; k < K; ++k) {
+      top_grid gk = *g;
+      if (k > 0) gk.input_repeat = 0;
+      const std::vector<double> zk(size_t(n_lz), stages[k].z);
+      Request q{};
+      q.g = &gk; q.lam = lam; q.z = zk.data(); q.n_lz = n_lz; q.adjoint = 0;
+      q.src_kind = SRC_FIELD; q.in = cur; q.group = 1;
+      q.msrc = stages[k].pre; q.msrc_conj = 0;
+      q.epi_kind = EPI_FIELD;
+      void* dst = nullptr;
+      if (k + 1 < K) {
+        dst = stages[k].keep ? stages[k].keep : static_cast<void*>(tmp);
+        q.out = dst;
+      } else if (inten) {
+        q.epi_kind = EPI_INTENSITY; q.out = out; q.outf = inten; q.group = group;
+      } else {
+        q.out = out;
+      }
+      TOP_TRY(run_bluestein(h, q, geo, st));
+      cur = dst;
+    }
+    return TOP_OK;
+  }
 
   const float2 *twx, *twy, *wpx, *wpy;
   TOP_TRY(engine_twiddles(h, geo.Px / 2, &twx));
@@ -1407,7 +1483,6 @@ top_status run_ragged(top_handle h, int count, const top_grid* grids, const void
   for (int i = 0; i < count; ++i) {
     const top_grid* g = &grids[i];
     TOP_TRY(check_grid(g, &geos[i]));
-    TOP_TRY(check_engines(geos[i]));
     if (g->batch != 1) return fail(TOP_ERR_INVALID_ARG, "ragged field %d: batch must be 1 (got %lld)", i, (long long)g->batch);
     if (g->input_repeat > 1) return fail(TOP_ERR_INVALID_ARG, "ragged field %d: input_repeat must be 0 or 1", i);
     if (!(std::isfinite(lam[i]) && lam[i] > 0)) return fail(TOP_ERR_INVALID_ARG, "lambda[%d] must be finite and > 0", i);
@@ -1416,11 +1491,21 @@ top_status run_ragged(top_handle h, int count, const top_grid* grids, const void
     TOP_TRY(check_ptr(out[i], "ragged output field"));
   }
   TOP_TRY(bind(h));
+  // fields at padded sizes without a plan of their own go one by one through the Bluestein path
+  for (int i = 0; i < count; ++i) {
+    if (has_engines(geos[i])) continue;
+    Request q{};
+    q.g = &grids[i]; q.lam = &lam[i]; q.z = &z[i]; q.n_lz = 1; q.adjoint = backward ? 1 : 0;
+    q.src_kind = SRC_FIELD; q.in = in[i]; q.group = 1;
+    q.epi_kind = EPI_FIELD; q.out = out[i];
+    TOP_TRY(run_bluestein(h, q, geos[i], st));
+  }
   // groups of one geometry and method, in first-appearance order
   std::vector<std::vector<int>> groups;
   std::vector<std::array<int, 5>> keys;
   for (int i = 0; i < count; ++i) {
     const Geometry& q = geos[i];
+    if (!has_engines(q)) continue;
     const std::array<int, 5> key = {q.ny, q.nx, q.Py, q.Px, grids[i].method};
     size_t k = 0;
     while (k < keys.size() && keys[k] != key) ++k;
@@ -1570,6 +1655,7 @@ top_status top_destroy(top_handle h) {
   for (void* p : h->allocs) cudaFree(p);
   if (h->ws) cudaFree(h->ws);
   if (h->coh) cudaFree(h->coh);
+  if (h->chain) cudaFree(h->chain);
   for (auto& pe : h->pending) {
     cudaEventDestroy(pe.second.first);
     cudaEventDestroy(pe.second.second);

@@ -531,6 +531,56 @@ cudaError_t launch_transfer_table(float2* hq, int Py, int Px, double dy, double 
   return cudaGetLastError();
 }
 
+// out_b = 2 w_b gI[b / group] psi_b: the source of the intensity backward (Eq. 14, chain rule).
+__global__ void __launch_bounds__(256) k_intensity_source(const float2* psi, const float* gI, const float* weights,
+                                                          int group, long long plane, float2* out) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long b = blockIdx.y;
+  if (i >= plane) return;
+  const float w = weights ? weights[b] : 1.f;
+  const float g = gI[(b / group) * plane + i];
+  out[b * plane + i] = c_scale(psi[b * plane + i], 2.f * w * g);
+}
+
+// I[g] = sum over the group's fields, in field order, of w_b |psi_b|^2 (Eq. 14).
+__global__ void __launch_bounds__(256) k_intensity_sum(const float2* psi, const float* weights, int group,
+                                                       long long plane, float* out) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long g = blockIdx.y;
+  if (i >= plane) return;
+  float acc = 0.f;
+  for (long long b = g * group; b < (g + 1) * group; ++b) {
+    const float2 v = psi[b * plane + i];
+    const float w = weights ? weights[b] : 1.f;
+    const float e = w * fmaf(v.x, v.x, v.y * v.y);
+    acc = b == g * group ? e : acc + e;
+  }
+  out[g * plane + i] = acc;
+}
+
+cudaError_t launch_intensity_source(const float2* psi, const float* gI, const float* weights, int group,
+                                    long long batch, long long plane, float2* out, cudaStream_t s) {
+  const long long step = 65535 - 65535 % group;  // launches of whole groups
+  for (long long b0 = 0; b0 < batch; b0 += step) {
+    const unsigned nb = unsigned(std::min<long long>(step, batch - b0));
+    dim3 grid(unsigned((plane + 255) / 256), nb);
+    TOP_LAUNCH(k_intensity_source, grid, 256, 0, s, psi + b0 * plane, gI + (b0 / group) * plane,
+               weights ? weights + b0 : nullptr, group, plane, out + b0 * plane);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_intensity_sum(const float2* psi, const float* weights, int group, long long ngroups, long long plane,
+                                 float* out, cudaStream_t s) {
+  for (long long g0 = 0; g0 < ngroups; g0 += 65535) {
+    const unsigned ng = unsigned(std::min<long long>(65535, ngroups - g0));
+    dim3 grid(unsigned((plane + 255) / 256), ng);
+    TOP_LAUNCH(k_intensity_sum, grid, 256, 0, s, psi + g0 * group * plane, weights ? weights + g0 * group : nullptr,
+               group, plane, out + g0 * plane);
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_transfer_full(float2* h, int Py, int Px, double dy, double dx, double lam, double z, int method,
                                  cudaStream_t s) {
   dim3 grid((Py + 255) / 256, Px);

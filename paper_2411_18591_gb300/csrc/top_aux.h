@@ -57,6 +57,12 @@ cudaError_t launch_transfer_table(float2* hq, int Py, int Px, double dy, double 
 // The same values on the whole grid in natural order, h[kx Py + ky] (the Bluestein column lines).
 cudaError_t launch_transfer_full(float2* h, int Py, int Px, double dy, double dx, double lam, double z, int method,
                                  cudaStream_t s);
+// Intensity (Eq. 14) as separate passes: out_b = 2 w_b gI[b / group] psi_b (the backward's source),
+// and I[g] = sum over group g's fields, in field order, of w_b |psi_b|^2. weights may be null (1).
+cudaError_t launch_intensity_source(const float2* psi, const float* gI, const float* weights, int group,
+                                    long long batch, long long plane, float2* out, cudaStream_t s);
+cudaError_t launch_intensity_sum(const float2* psi, const float* weights, int group, long long ngroups, long long plane,
+                                 float* out, cudaStream_t s);
 // out[b][c][r] = in[b][r][c] for a batch of [rows][cols] planes.
 cudaError_t launch_transpose_rect(const float2* in, float2* out, long long batch, int rows, int cols, cudaStream_t s);
 

@@ -5,7 +5,9 @@ Every comparison is element-wise rel-L2 over the whole output with the propagati
 tolerance (1e-5): prime sizes (61, 127, 257), products with 7, 11, 13, a padded size
 of 2042 (4096-point transforms), sizes below the smallest plan (16), one axis planned
 and the other not, per-field wavelengths and distances, the Fresnel form, repeated
-inputs, modulations before and after, the adjoint (backward) and its identity.
+inputs, modulations before and after, the adjoint (backward) and its identity, modulation
+gradients and the autograd wrapper, grouped intensities and their backward, fused chains and
+ragged batches mixing planned and unplanned sizes.
 """
 import numpy as np
 import pytest
@@ -152,11 +154,84 @@ def test_bluestein_autograd_phase_mask(T):
     assert rel_l2(host(pt.grad), np.imag(gy * np.conj(M * X)).sum(0)) < TOL
 
 
+def test_bluestein_intensity_forward_and_backward(T):
+    """Grouped, weighted detector intensity (Eq. 14) and its backward with phase gradients at a
+    prime padded size: the intensity sums and the backward source as separate passes."""
+    B, group, ny, nx, pad, d = 4, 2, 53, 40, 1.0, 5e-6  # 53 (prime) x 40 = 8 5
+    x = cfield(71, (B, ny, nx))
+    lams = np.array([450e-9, 520e-9, 600e-9, 700e-9])
+    z = 2e-3
+    w = uniform(73, (B,), 0.5, 1.5).astype(np.float32)
+    phi = uniform(75, (ny, nx), -np.pi, np.pi).astype(np.float32)
+    pre = T.Modulation(phase=dev(phi))
+    inten, psi = T.top_propagate_intensity(dev(x), d, d, lams, z, pad, group=group, weights=dev(w), pre=pre,
+                                           keep_field=True)
+    M = np.exp(1j * phi.astype(np.float64))
+    X = x.astype(np.complex128)
+    po = np.stack([O.propagate(X[i] * M, d, d, lams[i], z, pad)[0] for i in range(B)])
+    iref = O.intensity_sum(po, group, w.astype(np.float64))
+    assert rel_l2(host(psi), po) < TOL
+    assert rel_l2(host(inten), iref) < TOL
+    gI = uniform(77, (B // group, ny, nx), -1.0, 1.0).astype(np.float32)
+    gp = torch.zeros((ny, nx), dtype=torch.float32, device="cuda")
+    gi = host(T.top_propagate_intensity_backward(psi, dev(gI), d, d, lams, z, pad, group=group, weights=dev(w),
+                                                 pre=pre, saved_in=dev(x), grad_phase=gp))
+    src = 2 * w[:, None, None].astype(np.float64) * np.repeat(gI.astype(np.float64), group, axis=0) * po
+    gy = np.stack([O.propagate_adjoint(src[i], d, d, lams[i], z, pad)[0] for i in range(B)])
+    assert rel_l2(gi, np.conj(M) * gy) < TOL
+    assert rel_l2(host(gp), np.imag(gy * np.conj(M * X)).sum(0)) < TOL
+
+
+def test_bluestein_fused_chain_equals_the_same_calls(T):
+    """A three-stage chain with a kept field and the grouped intensity at a padded size without a
+    plan equals the same sequence of calls, bit for bit."""
+    ny, nx, pad, d = 45, 45, 1.0, 6e-6  # 45 = 3^2 5
+    lams = [450e-9, 600e-9, 700e-9, 520e-9]
+    x = dev(cfield(79, (4, ny, nx)))
+    phi = uniform(81, (ny, nx), -np.pi, np.pi).astype(np.float32)
+    pupil = T.Modulation(phase=dev(phi), radius=0.3 * ny * d)
+    lens = T.Modulation(focal_length=0.05)
+    keep = torch.empty_like(x)
+    zs = [1e-3, 2e-3, 1.5e-3]
+    out, inten = T.top_fused_chain(x, d, d, lams, [T.Stage(zs[0], keep=keep), T.Stage(zs[1], pre=lens),
+                                                   T.Stage(zs[2], pre=pupil)], pad, intensity_group=2)
+    y = T.top_propagate(x, d, d, lams, zs[0], pad)
+    k = y.clone()
+    y = T.top_propagate(y, d, d, lams, zs[1], pad, pre=lens)
+    i_ref, y_ref = T.top_propagate_intensity(y, d, d, lams, zs[2], pad, group=2, pre=pupil, keep_field=True)
+    torch.cuda.synchronize()
+    assert torch.equal(keep, k)
+    assert torch.equal(out, y_ref)
+    assert torch.equal(inten, i_ref)
+    ref = O.propagate(host(x).astype(np.complex128), d, d, lams, zs[0], pad)
+    assert rel_l2(host(keep), ref) < TOL
+
+
+def test_bluestein_ragged_batch_with_planned_and_unplanned_sizes(T):
+    descs = [(61, 61, 1.0), (64, 64, 2.0), (45, 37, 2.0), (48, 96, 2.667)]
+    xs = [dev(cfield(83 + i, (ny, nx))) for i, (ny, nx, _) in enumerate(descs)]
+    lams = [450e-9, 500e-9, 550e-9, 600e-9]
+    zs = [1e-3, 2e-3, 3e-3, 4e-3]
+    for pad in sorted({p for *_, p in descs}):
+        idx = [i for i, desc in enumerate(descs) if desc[2] == pad]
+        ys = T.top_propagate_ragged([xs[i] for i in idx], [4e-6] * len(idx), [lams[i] for i in idx],
+                                    [zs[i] for i in idx], pad)
+        gs = T.top_propagate_ragged(ys, [4e-6] * len(idx), [lams[i] for i in idx], [zs[i] for i in idx], pad,
+                                    backward=True)
+        for j, i in enumerate(idx):
+            xh = host(xs[i]).astype(np.complex128)
+            ref = O.propagate(xh, 4e-6, 4e-6, lams[i], zs[i], pad)[0]
+            assert rel_l2(host(ys[j]), ref) < TOL
+            back = O.propagate_adjoint(host(ys[j]).astype(np.complex128), 4e-6, 4e-6, lams[i], zs[i], pad)[0]
+            assert rel_l2(host(gs[j]), back) < TOL
+
+
 def test_bluestein_limits_are_reported(T):
     x = dev(cfield(43, (1, 61, 61)))
     with pytest.raises(T.TopError, match="Direct Integration"):
         T.top_propagate(x, 2e-6, 2e-6, 600e-9, 1e-2, 2.0, "di")  # 122 = 2 61
-    with pytest.raises(T.TopError, match="Bluestein"):
-        T.top_propagate_intensity(x, 2e-6, 2e-6, 600e-9, 1e-3, 1.0)
+    tgt = dev(cfield(44, (1, 61, 61)))
+    with pytest.raises(T.TopError, match="overlap"):
+        T.top_propagate_overlap(x, tgt, 2e-6, 2e-6, 600e-9, 1e-3, 1.0)
     with pytest.raises(T.TopError, match="2048"):
         T.top_propagate(dev(cfield(45, (1, 16, 1500))), 2e-6, 2e-6, 600e-9, 1e-3, 2.0)  # 3000 = 8 3 125
