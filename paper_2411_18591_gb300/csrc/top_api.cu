@@ -893,23 +893,23 @@ top_status bluestein_fields(top_handle h, const Request& q, const Geometry& geo,
 }
 
 // The propagation calls at padded sizes without a plan of their own: the intensity backward's
-// source (2 w gI psi) and the detector intensity (Eq. 14) run as separate passes around
-// bluestein_fields, and modulation gradients follow the adjoint propagation through the
-// modulation's own backward. The overlap epilogue needs a planned size.
+// source (2 w gI psi), the detector intensity (Eq. 14) and the overlap sums (Eq. 7) run as
+// separate passes around bluestein_fields, and modulation gradients follow the adjoint
+// propagation through the modulation's own backward.
 top_status run_bluestein(top_handle h, const Request& q, const Geometry& geo, cudaStream_t st) {
   const top_grid* g = q.g;
-  if (q.epi_kind == EPI_OVERLAP)
-    return fail(TOP_ERR_UNSUPPORTED, "padded size %d x %d has no FFT plan of its own: the overlap epilogue needs "
-                "a planned size (the Bluestein transforms cover the other propagation calls)", geo.Py, geo.Px);
   TOP_TRY(bind(h));
   const int64_t B = g->batch;
   const long long plane = (long long)geo.ny * geo.nx;
   const bool need_src = q.src_kind == SRC_INTENSITY;
-  const bool need_field = q.epi_kind == EPI_MODGRAD || (q.epi_kind == EPI_INTENSITY && !q.out);
+  const bool need_field = q.epi_kind == EPI_MODGRAD || ((q.epi_kind == EPI_INTENSITY || q.epi_kind == EPI_OVERLAP) && !q.out);
+  constexpr int kOvTiles = 64;  // partial sums per field of the overlap (fixed order)
+  const size_t ov_bytes = q.epi_kind == EPI_OVERLAP ? sizeof(double) * 3 * kOvTiles * size_t(B) : 0;
   float2* scratch = nullptr;
-  if (need_src || need_field) {
+  if (need_src || need_field || ov_bytes) {
     void* p = nullptr;
-    TOP_TRY(coh_scratch(h, sizeof(float2) * size_t(B) * size_t(plane) * size_t(int(need_src) + int(need_field)), &p));
+    TOP_TRY(coh_scratch(h, sizeof(float2) * size_t(B) * size_t(plane) * size_t(int(need_src) + int(need_field)) + ov_bytes,
+                        &p));
     scratch = static_cast<float2*>(p);
   }
   float2* src_buf = scratch;
@@ -934,13 +934,23 @@ top_status run_bluestein(top_handle h, const Request& q, const Geometry& geo, cu
     TOP_TRY(bluestein_fields(h, r, geo, st));
     return top_modulate_backward(h, g, q.mepi, field_buf, q.out, q.grads, q.lam, q.n_lz, st);
   }
-  // EPI_INTENSITY: the (modulated) field, kept in field_out when given, then the group sums
+  // EPI_INTENSITY / EPI_OVERLAP: the (modulated) field, kept in field_out when given, then the
+  // group sums of Eq. 14 or the overlaps and powers of Eq. 7
   float2* field = q.out ? static_cast<float2*>(q.out) : field_buf;
   r.epi_kind = EPI_FIELD;
   r.out = field;
   TOP_TRY(bluestein_fields(h, r, geo, st));
-  return timed(h, KK_AUX, st, "intensity", [&] {
-    return launch_intensity_sum(field, q.weights, int(q.group), B / q.group, plane, q.outf, st);
+  if (q.epi_kind == EPI_INTENSITY)
+    return timed(h, KK_AUX, st, "intensity", [&] {
+      return launch_intensity_sum(field, q.weights, int(q.group), B / q.group, plane, q.outf, st);
+    });
+  double* part = reinterpret_cast<double*>(scratch + B * plane * (int(need_src) + int(need_field)));
+  TOP_TRY(timed(h, KK_AUX, st, "overlap partial sums", [&] {
+    return launch_overlap_partials(field, static_cast<const float2*>(q.target), q.target_stride, B, plane, kOvTiles,
+                                   part, st);
+  }));
+  return timed(h, KK_AUX, st, "overlap sums", [&] {
+    return launch_overlap_finish(part, kOvTiles, int(B), g->dy * g->dx, q.ov_out, q.pw_out, st);
   });
 }
 

@@ -558,6 +558,51 @@ __global__ void __launch_bounds__(256) k_intensity_sum(const float2* psi, const 
   out[g * plane + i] = acc;
 }
 
+// Partial sums of Eq. 7 over the fields of a batch: block (tile, b) adds psi conj(phi) and |psi|^2
+// over samples tile * 256 + tid + k * ntiles * 256 in float64, then the block's threads in a fixed
+// order, into part[(b ntiles + tile) 3 + {0, 1, 2}] (the layout k_overlap_finish reads).
+__global__ void __launch_bounds__(256) k_overlap_partials(const float2* psi, const float2* target,
+                                                          long long target_stride, long long plane, double* part) {
+  __shared__ double red[3 * 256];
+  const int tile = blockIdx.x, ntiles = gridDim.x;
+  const long long b = blockIdx.y;
+  double re = 0.0, im = 0.0, pw = 0.0;
+  for (long long i = (long long)tile * 256 + threadIdx.x; i < plane; i += (long long)ntiles * 256) {
+    const float2 v = psi[b * plane + i];
+    const float2 t = target[b * target_stride + i];
+    const double vx = v.x, vy = v.y, px = t.x, py = t.y;
+    re = fma(vx, px, fma(vy, py, re));
+    im = fma(vy, px, fma(-vx, py, im));
+    pw = fma(vx, vx, fma(vy, vy, pw));
+  }
+  red[3 * threadIdx.x] = re;
+  red[3 * threadIdx.x + 1] = im;
+  red[3 * threadIdx.x + 2] = pw;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sr = 0.0, si = 0.0, sp = 0.0;
+    for (int k = 0; k < 256; ++k) {
+      sr += red[3 * k];
+      si += red[3 * k + 1];
+      sp += red[3 * k + 2];
+    }
+    double* out = part + (b * ntiles + tile) * 3;
+    out[0] = sr;
+    out[1] = si;
+    out[2] = sp;
+  }
+}
+
+cudaError_t launch_overlap_partials(const float2* psi, const float2* target, long long target_stride, long long batch,
+                                    long long plane, int ntiles, double* part, cudaStream_t s) {
+  for (long long b0 = 0; b0 < batch; b0 += 65535) {
+    const unsigned nb = unsigned(std::min<long long>(65535, batch - b0));
+    TOP_LAUNCH(k_overlap_partials, dim3(ntiles, nb), 256, 0, s, psi + b0 * plane, target + b0 * target_stride,
+               target_stride, plane, part + b0 * ntiles * 3);
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_intensity_source(const float2* psi, const float* gI, const float* weights, int group,
                                     long long batch, long long plane, float2* out, cudaStream_t s) {
   const long long step = 65535 - 65535 % group;  // launches of whole groups

@@ -63,6 +63,10 @@ cudaError_t launch_intensity_source(const float2* psi, const float* gI, const fl
                                     long long batch, long long plane, float2* out, cudaStream_t s);
 cudaError_t launch_intensity_sum(const float2* psi, const float* weights, int group, long long ngroups, long long plane,
                                  float* out, cudaStream_t s);
+// Per-field partial sums of Eq. 7 (psi conj(phi), |psi|^2; float64, fixed order) in ntiles tiles,
+// part[(b ntiles + tile) 3 + c], for launch_overlap_finish; target_stride 0 shares phi.
+cudaError_t launch_overlap_partials(const float2* psi, const float2* target, long long target_stride, long long batch,
+                                    long long plane, int ntiles, double* part, cudaStream_t s);
 // out[b][c][r] = in[b][r][c] for a batch of [rows][cols] planes.
 cudaError_t launch_transpose_rect(const float2* in, float2* out, long long batch, int rows, int cols, cudaStream_t s);
 

@@ -331,7 +331,7 @@ def test_errors_are_reported_not_launched(T):
     from paper_2411_18591_gb300._lib import TopError
     x = dev(cfield(60, (1, 61, 61)))
     with pytest.raises(TopError, match="UNSUPPORTED"):
-        T.top_propagate_overlap(x, x, 1e-6, 1e-6, 5e-7, 1e-3, 1.0)  # overlap epilogue at an unplanned (odd) size
+        T.top_propagate(x, 1e-6, 1e-6, 5e-7, 1e-3, 1.0, "di")  # DI at an unplanned (odd) padded size
     with pytest.raises(TopError, match="INVALID_ARG"):
         T.top_propagate(dev(cfield(61, (1, 64, 64))), 1e-6, 1e-6, -5e-7, 1e-3, 2.0)   # negative wavelength
     big = dev(cfield(62, (1, 64, 65)))
