@@ -155,8 +155,9 @@ double top_zcritical(double L, double dx, double lambda);
  * 2048 per axis) use Bluestein line transforms: the same result (a DFT of length P per axis),
  * with modulations, intensities and the intensity backward's source as separate passes, and
  * modulation gradients from the adjoint propagation by the modulation's own backward; this holds
- * for the backward, intensity, overlap, chain and ragged calls too. TOP_DI and the no-alloc
- * call need a planned size there (TOP_ERR_UNSUPPORTED). */
+ * for the backward, intensity, overlap, chain and ragged calls and for TOP_DI (its kernel
+ * transformed by the same line transforms) too. The no-alloc call needs a planned size
+ * (TOP_ERR_UNSUPPORTED). */
 top_status top_propagate(top_handle h, const top_grid* g, const void* in, void* out,
                          const double* lambda, const double* z, int64_t n_lz,
                          const top_mod* pre, const top_mod* post, void* stream);

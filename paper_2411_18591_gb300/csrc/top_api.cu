@@ -712,10 +712,67 @@ top_status transfer_full_table(top_handle h, int Py, int Px, double dy, double d
   void* p = nullptr;
   TOP_CUDA(cudaMalloc(&p, size_t(Px) * size_t(Py) * sizeof(float2)), "cudaMalloc(transfer table)");
   h->allocs.push_back(p);
-  TOP_CUDA(launch_transfer_full(static_cast<float2*>(p), Py, Px, dy, dx, lam, z, method, st), "transfer table");
-  TOP_CUDA(cudaStreamSynchronize(st), "cudaStreamSynchronize(transfer table)");
-  h->transfer_full[key] = static_cast<float2*>(p);
-  *out = static_cast<float2*>(p);
+  float2* tab = static_cast<float2*>(p);
+  if (method == TOP_DI) {
+    // DI: the sampled kernel h_z dx dy at the grid's signed lags, forward-transformed by Bluestein
+    // rows, a transpose and Bluestein columns into [kx][ky], divided by Py Px
+    CztPlan cx, cy;
+    TOP_TRY(czt_plan(h, Px, &cx));
+    TOP_TRY(czt_plan(h, Py, &cy));
+    const size_t plane = size_t(Py) * size_t(Px);
+    void* buf = nullptr;
+    TOP_CUDA(cudaMalloc(&buf, 2 * plane * sizeof(float2)), "cudaMalloc(DI kernel samples)");
+    float2* a = static_cast<float2*>(buf);
+    float2* b = a + plane;
+    CztParams r{};
+    r.mode = CZT_FWD;
+    r.in = a;
+    r.in_fstride = (long long)plane;
+    r.in_lstride = Px;
+    r.in_repeat = 1;
+    r.out = b;
+    r.out_fstride = (long long)plane;
+    r.out_lstride = Px;
+    r.nlines = Py;
+    r.nfields = 1;
+    r.P = Px;
+    r.n_in = Px;
+    r.off_in = 0;
+    r.k0 = 0;
+    r.n_out = Px;
+    r.inv_l = float(1.0 / double(cx.L));
+    r.chirp = cx.chirp;
+    r.bh_fwd = cx.bh_fwd;
+    r.bh_inv = cx.bh_inv;
+    r.tw = cx.tw;
+    CztParams c = r;
+    c.in = a;
+    c.in_lstride = Py;
+    c.out = tab;
+    c.out_lstride = Py;
+    c.nlines = Px;
+    c.P = Py;
+    c.n_in = Py;
+    c.n_out = Py;
+    c.inv_l = float(1.0 / (double(cy.L) * double(Py) * double(Px)));
+    c.chirp = cy.chirp;
+    c.bh_fwd = cy.bh_fwd;
+    c.bh_inv = cy.bh_inv;
+    c.tw = cy.tw;
+    cudaError_t e = launch_di_samples(a, Py, Px, dy, dx, lam, z, st);
+    if (e == cudaSuccess) e = launch_czt_pass(cx.L, r, st);
+    if (e == cudaSuccess) e = launch_transpose_rect(b, a, 1, Py, Px, st);
+    if (e == cudaSuccess) e = launch_czt_pass(cy.L, c, st);
+    const cudaError_t es = cudaStreamSynchronize(st);
+    cudaFree(buf);
+    if (e != cudaSuccess) return cuda_fail(e, "DI table");
+    if (es != cudaSuccess) return cuda_fail(es, "cudaStreamSynchronize(DI table)");
+  } else {
+    TOP_CUDA(launch_transfer_full(tab, Py, Px, dy, dx, lam, z, method, st), "transfer table");
+    TOP_CUDA(cudaStreamSynchronize(st), "cudaStreamSynchronize(transfer table)");
+  }
+  h->transfer_full[key] = tab;
+  *out = tab;
   return TOP_OK;
 }
 
@@ -785,9 +842,12 @@ top_status bluestein_fields(top_handle h, const Request& q, const Geometry& geo,
   for (int64_t b = 0; b < B; ++b) {
     const double lam = q.lam[q.n_lz == 1 ? 0 : b], z = q.z[q.n_lz == 1 ? 0 : b];
     const int method = resolve_method(g, geo.ny, geo.nx, lam, z);
-    if (method == TOP_DI)
-      return fail(TOP_ERR_UNSUPPORTED, "Direct Integration needs a padded size with an FFT plan of its own (got %d x %d)",
-                  geo.Py, geo.Px);
+    if (method == TOP_DI) {
+      if (geo.Py < 2 * geo.ny - 1 || geo.Px < 2 * geo.nx - 1)
+        return fail(TOP_ERR_INVALID_ARG, "DI needs padded sizes >= 2 n - 1 (got %dx%d for %dx%d; pad >= 2)", geo.Py,
+                    geo.Px, geo.ny, geo.nx);
+      if (!(z > 0)) return fail(TOP_ERR_INVALID_ARG, "DI needs z > 0 (got %g)", z);
+    }
     TOP_TRY(transfer_full_table(h, geo.Py, geo.Px, g->dy, g->dx, lam, z, method, st, &tables[b]));
   }
   const long long wplane = (long long)geo.ny * geo.Px;

@@ -7,7 +7,7 @@ of 2042 (4096-point transforms), sizes below the smallest plan (16), one axis pl
 and the other not, per-field wavelengths and distances, the Fresnel form, repeated
 inputs, modulations before and after, the adjoint (backward) and its identity, modulation
 gradients and the autograd wrapper, grouped intensities and their backward, fused chains and
-ragged batches mixing planned and unplanned sizes, overlaps and powers.
+ragged batches mixing planned and unplanned sizes, overlaps and powers, Direct Integration.
 """
 import numpy as np
 import pytest
@@ -245,9 +245,26 @@ def test_bluestein_overlap_and_power(T, per_field):
     assert rel_l2(pw.cpu().numpy(), O.power(po, d, d)) < TOL
 
 
+@pytest.mark.parametrize("n", [45, 61])
+def test_bluestein_direct_integration(T, n):
+    """DI (Eq. 2-3) at padded sizes without a plan of their own (90 = 2 3^2 5, 122 = 2 61): the
+    kernel's samples transformed by Bluestein rows and columns; and TOP_AUTO beyond z_critical."""
+    d, lam = 4e-6, 633e-9
+    x = cfield(95, (2, n, n))
+    z = 0.05  # beyond z_critical = n d^2 / lambda (1.1 mm and 1.5 mm)
+    for method in ("di", "auto"):
+        out = host(T.top_propagate(dev(x), d, d, lam, z, 2.0, method))
+        ref = O.propagate(x.astype(np.complex128), d, d, lam, z, 2.0, O.DI)
+        assert rel_l2(out, ref) < TOL
+    back = host(T.top_propagate_backward(dev(x), d, d, lam, z, 2.0, "di"))
+    assert rel_l2(back, O.propagate_adjoint(x.astype(np.complex128), d, d, lam, z, 2.0, O.DI)) < TOL
+
+
 def test_bluestein_limits_are_reported(T):
     x = dev(cfield(43, (1, 61, 61)))
-    with pytest.raises(T.TopError, match="Direct Integration"):
-        T.top_propagate(x, 2e-6, 2e-6, 600e-9, 1e-2, 2.0, "di")  # 122 = 2 61
+    with pytest.raises(T.TopError, match="2 n - 1"):
+        T.top_propagate(x, 2e-6, 2e-6, 600e-9, 1e-2, 1.0, "di")  # DI needs a padded size >= 2 n - 1
+    with pytest.raises(T.TopError, match="UNSUPPORTED"):
+        T.top_propagate_noalloc(x, 2e-6, 2e-6, 600e-9, 1e-3, 1.0, out=x)  # the no-alloc call needs a plan
     with pytest.raises(T.TopError, match="2048"):
         T.top_propagate(dev(cfield(45, (1, 16, 1500))), 2e-6, 2e-6, 600e-9, 1e-3, 2.0)  # 3000 = 8 3 125

@@ -331,7 +331,7 @@ def test_errors_are_reported_not_launched(T):
     from paper_2411_18591_gb300._lib import TopError
     x = dev(cfield(60, (1, 61, 61)))
     with pytest.raises(TopError, match="UNSUPPORTED"):
-        T.top_propagate(x, 1e-6, 1e-6, 5e-7, 1e-3, 1.0, "di")  # DI at an unplanned (odd) padded size
+        T.top_propagate_noalloc(x, 1e-6, 1e-6, 5e-7, 1e-3, 1.0, out=x)  # no-alloc call at an unplanned (odd) size
     with pytest.raises(TopError, match="INVALID_ARG"):
         T.top_propagate(dev(cfield(61, (1, 64, 64))), 1e-6, 1e-6, -5e-7, 1e-3, 2.0)   # negative wavelength
     big = dev(cfield(62, (1, 64, 65)))
