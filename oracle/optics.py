@@ -29,7 +29,7 @@ paper (TorchOptics, arXiv 2411.18591):
 * a field moves between grids of different spacing by nearest or bilinear interpolation of
   the centred sample positions (§3), samples outside the input grid counting as zero.
 
-Readings of points the paper leaves open (each listed in the design doc):
+Readings of points the paper leaves open:
 
 * padded size P = floor(pad * n + 0.5) per axis; the field sits at offset
   floor((P - n)/2) of the padded grid and is cropped from the same window;

@@ -88,7 +88,7 @@ def test_padded_size_and_offset():
 
 
 def test_zcritical():
-    # Eq. 6 with the parameters of the SURVEY Gaussian case: L = 2.56 mm, 10 um, 700 nm
+    # Eq. 6 for a 256-sample, 10 um grid at 700 nm: L = 2.56 mm
     assert O.z_critical(256 * 10e-6, 10e-6, 700e-9) == pytest.approx(0.0365714285714, rel=1e-12)
 
 
