@@ -138,7 +138,7 @@ top_status top_set_workspace_limit(top_handle h, uint64_t bytes);
 /* Host-only plan query: padded sizes and per-field workspace bytes of a propagation.
  * Validates `g` exactly like the propagation calls. Padded sizes P = floor(pad n + 0.5) of
  * 2 x {16 .. 4096 powers of two, 250, 500, 768, 1000} have FFT plans of their own (one
- * field-sized workspace buffer); any other size up to 2048 per axis goes through Bluestein
+ * field-sized workspace buffer); any other size up to 4096 per axis goes through Bluestein
  * transforms (two buffers); larger unplanned sizes return TOP_ERR_UNSUPPORTED. */
 top_status top_plan_query(const top_grid* g, int64_t* py, int64_t* px, uint64_t* workspace_per_field);
 
@@ -152,7 +152,7 @@ double top_zcritical(double L, double dx, double lambda);
  * lambda, z: host arrays of n_lz values, n_lz == 1 (shared) or == batch (per field).
  * pre, post: modulations or NULL.
  * Padded sizes without an FFT plan of their own (odd, or with prime factors above 5; up to
- * 2048 per axis) use Bluestein line transforms: the same result (a DFT of length P per axis),
+ * 4096 per axis) use Bluestein line transforms: the same result (a DFT of length P per axis),
  * with modulations, intensities and the intensity backward's source as separate passes, and
  * modulation gradients from the adjoint propagation by the modulation's own backward; this holds
  * for the backward, intensity, overlap, chain and ragged calls and for TOP_DI (its kernel

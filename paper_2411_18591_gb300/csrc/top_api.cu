@@ -68,13 +68,15 @@ struct TransferEntry {
   float2* hq = nullptr;
 };
 
-// Bluestein tables of one line length P (CztParams): L-point engine, chirp, chirp transforms.
+// Bluestein tables of one line length P (CztParams): convolution length L = 2M, chirp, chirp
+// transforms split by parity, M-point engine twiddles, split twiddles of L.
 struct CztPlan {
   int L = 0;
   const float2* chirp = nullptr;
-  const float2* bh_fwd = nullptr;  // in the engine's slot order
+  const float2* bh_fwd = nullptr;  // halves in the M-point engine's slot order
   const float2* bh_inv = nullptr;
   const float2* tw = nullptr;
+  const float2* wsplit = nullptr;
 };
 
 struct top_ctx {
@@ -188,9 +190,16 @@ cudaError_t launch_pass(int kind, int M, const PassParams& p, cudaStream_t s, co
   return cudaErrorInvalidValue;
 }
 
+// Bluestein line pass with convolution length L: one L-point engine up to 4096, two halves on the
+// 4096-point engine for 8192.
 cudaError_t launch_czt_pass(int L, const CztParams& p, cudaStream_t s) {
   bool found = false;
-  cudaError_t e = launch_czt_small(L, p, s, &found);
+  cudaError_t e;
+  if (L > 4096) {
+    e = launch_czt_split_large(L / 2, p, s, &found);
+    return found ? e : cudaErrorInvalidValue;
+  }
+  e = launch_czt_small(L, p, s, &found);
   if (found) return e;
   e = launch_czt_mid(L, p, s, &found);
   if (found) return e;
@@ -482,8 +491,8 @@ top_status check_engines(const Geometry& geo) {
   if (!has_engines(geo))
     return fail(TOP_ERR_UNSUPPORTED,
                 "padded size %d x %d has no FFT plan of its own (planned: 2 x {16 .. 4096 powers of two, 250, 500, 768, "
-                "1000}); other sizes up to 2048 go through Bluestein transforms in top_propagate and "
-                "top_propagate_backward only", geo.Py, geo.Px);
+                "1000}); other sizes up to 4096 go through Bluestein transforms, which do not take this call",
+                geo.Py, geo.Px);
   return TOP_OK;
 }
 
@@ -653,8 +662,8 @@ top_status czt_plan(top_handle h, int P, CztPlan* out) {
   }
   int L = 16;
   while (L < 2 * P - 1) L *= 2;
-  if (L > 4096)
-    return fail(TOP_ERR_UNSUPPORTED, "padded size %d has no FFT plan and is above the 2048 points of the Bluestein "
+  if (L > 8192)
+    return fail(TOP_ERR_UNSUPPORTED, "padded size %d has no FFT plan and is above the 4096 points of the Bluestein "
                 "transforms", P);
   std::vector<float2> chirp(P);
   std::vector<std::complex<double>> bf(L), bi(L);
@@ -672,18 +681,23 @@ top_status czt_plan(top_handle h, int P, CztPlan* out) {
   }
   host_fft(bf);
   host_fft(bi);
-  // in the engine's slot order: entry e G + t holds the bin that lane t keeps in slot e after the
-  // forward transform, so a warp reads consecutive entries
+  // in the slot order of the engine that runs the transforms, so a warp reads consecutive entries
+  // (entry e G + t holds the bin lane t keeps in slot e after the forward transform): the L-point
+  // engine, or for L = 8192 the 4096-point one with the table split by parity (half r holds the
+  // bins 2k + r, at r M)
+  const bool split = L > 4096;
+  const int M = split ? L / 2 : L;
   EngineInfo info;
-  if (!find_engine(L, &info)) return fail(TOP_ERR_INTERNAL, "no %d-point engine for the Bluestein transforms", L);
+  if (!find_engine(M, &info)) return fail(TOP_ERR_INTERNAL, "no %d-point engine for the Bluestein transforms", M);
   std::vector<float2> hf(L), hi(L);
-  const int E = L / info.G;
-  for (int t = 0; t < info.G; ++t)
-    for (int e = 0; e < E; ++e) {
-      const int k = engine_bin(info, t, e);
-      hf[size_t(e) * info.G + t] = make_float2(float(bf[k].real()), float(bf[k].imag()));
-      hi[size_t(e) * info.G + t] = make_float2(float(bi[k].real()), float(bi[k].imag()));
-    }
+  const int E = M / info.G;
+  for (int r = 0; r < (split ? 2 : 1); ++r)
+    for (int t = 0; t < info.G; ++t)
+      for (int e = 0; e < E; ++e) {
+        const int k = split ? 2 * engine_bin(info, t, e) + r : engine_bin(info, t, e);
+        hf[size_t(r) * M + size_t(e) * info.G + t] = make_float2(float(bf[k].real()), float(bf[k].imag()));
+        hi[size_t(r) * M + size_t(e) * info.G + t] = make_float2(float(bi[k].real()), float(bi[k].imag()));
+      }
   CztPlan plan;
   plan.L = L;
   float2 *dc = nullptr, *df = nullptr, *di = nullptr;
@@ -693,7 +707,8 @@ top_status czt_plan(top_handle h, int P, CztPlan* out) {
   plan.chirp = dc;
   plan.bh_fwd = df;
   plan.bh_inv = di;
-  TOP_TRY(engine_twiddles(h, L, &plan.tw));
+  TOP_TRY(engine_twiddles(h, M, &plan.tw));
+  if (split) TOP_TRY(split_twiddles(h, L, &plan.wsplit));
   h->czt[P] = plan;
   *out = plan;
   return TOP_OK;
@@ -745,6 +760,7 @@ top_status transfer_full_table(top_handle h, int Py, int Px, double dy, double d
     r.bh_fwd = cx.bh_fwd;
     r.bh_inv = cx.bh_inv;
     r.tw = cx.tw;
+    r.wsplit = cx.wsplit;
     CztParams c = r;
     c.in = a;
     c.in_lstride = Py;
@@ -759,6 +775,7 @@ top_status transfer_full_table(top_handle h, int Py, int Px, double dy, double d
     c.bh_fwd = cy.bh_fwd;
     c.bh_inv = cy.bh_inv;
     c.tw = cy.tw;
+    c.wsplit = cy.wsplit;
     cudaError_t e = launch_di_samples(a, Py, Px, dy, dx, lam, z, st);
     if (e == cudaSuccess) e = launch_czt_pass(cx.L, r, st);
     if (e == cudaSuccess) e = launch_transpose_rect(b, a, 1, Py, Px, st);
@@ -826,7 +843,7 @@ top_status modulate_fields(top_handle h, const top_grid* g, const Geometry& geo,
 }
 
 // A field-to-field propagation (modulations before and after as separate passes) whose padded
-// size has no plan of its own (odd, or with prime factors above 5), up to 2048 points per axis:
+// size has no plan of its own (odd, or with prime factors above 5), up to 4096 points per axis:
 // rows by Bluestein forward transforms, a transpose, each column's forward transform, H and
 // inverse transform in one Bluestein line pass, a transpose back and the rows' inverse
 // transforms with the crop.
@@ -904,6 +921,7 @@ top_status bluestein_fields(top_handle h, const Request& q, const Geometry& geo,
     r.bh_fwd = cx.bh_fwd;
     r.bh_inv = cx.bh_inv;
     r.tw = cx.tw;
+    r.wsplit = cx.wsplit;
     TOP_TRY(timed(h, KK_ROWS_FWD, st, "Bluestein rows", [&] { return launch_czt_pass(cx.L, r, st); }));
     TOP_TRY(timed(h, KK_AUX, st, "transpose", [&] { return launch_transpose_rect(w1, w2, n, geo.ny, geo.Px, st); }));
     CztParams c{};
@@ -928,6 +946,7 @@ top_status bluestein_fields(top_handle h, const Request& q, const Geometry& geo,
     c.bh_fwd = cy.bh_fwd;
     c.bh_inv = cy.bh_inv;
     c.tw = cy.tw;
+    c.wsplit = cy.wsplit;
     c.h = d_h;
     TOP_TRY(timed(h, KK_COLS, st, "Bluestein columns", [&] { return launch_czt_pass(cy.L, c, st); }));
     TOP_TRY(timed(h, KK_AUX, st, "transpose", [&] { return launch_transpose_rect(w2, w1, n, geo.Px, geo.ny, st); }));
@@ -1330,7 +1349,7 @@ top_status run_chain(top_handle h, const top_grid* g, const void* in, void* out,
     // each stage's field to its keep buffer or to one scratch field set (in place from the second
     // stage on), the last stage's to out and the intensity
     for (int P : {geo.Py, geo.Px})
-      if (2 * P - 1 > 4096) TOP_TRY(check_engines(geo));
+      if (2 * P - 1 > 8192) TOP_TRY(check_engines(geo));
     const long long plane = (long long)geo.ny * geo.nx;
     TOP_TRY(grow_scratch(&h->chain, &h->chain_bytes, sizeof(float2) * size_t(B) * size_t(plane),
                          "cudaMalloc(chain scratch)"));
@@ -1745,12 +1764,12 @@ top_status top_set_workspace_limit(top_handle h, uint64_t bytes) {
 top_status top_plan_query(const top_grid* g, int64_t* py, int64_t* px, uint64_t* workspace_per_field) {
   Geometry geo;
   TOP_TRY(check_grid(g, &geo));
-  // sizes without a plan of their own take Bluestein transforms (up to 2048 points per axis,
+  // sizes without a plan of their own take Bluestein transforms (up to 4096 points per axis,
   // two field-sized buffers)
   const bool planned = has_engines(geo);
   if (!planned) {
     for (int P : {geo.Py, geo.Px})
-      if (2 * P - 1 > 4096) TOP_TRY(check_engines(geo));
+      if (2 * P - 1 > 8192) TOP_TRY(check_engines(geo));
   }
   if (py) *py = geo.Py;
   if (px) *px = geo.Px;

@@ -40,5 +40,7 @@ cudaError_t launch_czt_small(int M, const CztParams& p, cudaStream_t s, bool* fo
 cudaError_t launch_czt_mid(int M, const CztParams& p, cudaStream_t s, bool* found);
 cudaError_t launch_czt_m1024(int M, const CztParams& p, cudaStream_t s, bool* found);
 cudaError_t launch_czt_large(int M, const CztParams& p, cudaStream_t s, bool* found);
+// The same as two halves on the 4096-point engine (convolution length 8192).
+cudaError_t launch_czt_split_large(int M, const CztParams& p, cudaStream_t s, bool* found);
 
 }  // namespace top

@@ -150,11 +150,15 @@ struct CztParams {
   int k0, n_out;         // output window
   int mode;              // CztMode
   int adjoint;
-  float inv_l;           // 1 / L
+  float inv_l;           // 1 / L, L the convolution length
   const float2* chirp;   // c[n], n < P
-  const float2* bh_fwd;  // L-point transform of conj(c) on (-P, P), entry e G + t = the bin of lane t, slot e
-  const float2* bh_inv;  // L-point transform of c on (-P, P), same order
-  const float2* tw;      // stage twiddles of the L-point engine
+  // L-point transforms of conj(c) (forward) and c (inverse) on the lags (-P, P), entry e G + t = the
+  // bin lane t of the transforming engine holds in slot e; for L = 8192 split by parity (half r,
+  // bins 2k + r, at r L/2, on the 4096-point engine)
+  const float2* bh_fwd;
+  const float2* bh_inv;
+  const float2* tw;      // stage twiddles of the transforming engine
+  const float2* wsplit;  // L = 8192: exp(-2 pi i p / L), p < L/2
   const float2* const* h;  // CZT_FILTER: per field, rows [line][P] of H / (Py Px) in natural order
 };
 

@@ -62,3 +62,17 @@ inline cudaError_t launch_pass_of(int kind, const PassParams& p, const PassParam
     switch (M) { LIST(TOP_CZT_CASE) default: return cudaSuccess; }                                 \
   }                                                                                                \
   }
+
+#define TOP_CZT_SPLIT_CASE(EN) \
+  case EN::M:                  \
+    *found = true;             \
+    return launch_czt_split<EN>(p, s);
+
+// Bluestein line transforms as two halves on the unit's engines of half the convolution length.
+#define TOP_DEFINE_CZT_SPLIT(name, LIST)                                                           \
+  namespace top {                                                                                  \
+  cudaError_t launch_czt_split_##name(int M, const CztParams& p, cudaStream_t s, bool* found) {    \
+    *found = false;                                                                                \
+    switch (M) { LIST(TOP_CZT_SPLIT_CASE) default: return cudaSuccess; }                           \
+  }                                                                                                \
+  }

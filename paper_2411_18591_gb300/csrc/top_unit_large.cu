@@ -9,3 +9,5 @@ using Eng4096 = Engine<4096, 128, 16, 16, 16>;
 #define LIST(X) X(Eng2048) X(Eng4096)
 TOP_DEFINE_UNIT(large, LIST)
 TOP_DEFINE_CZT(large, LIST)
+#define SPLIT_LIST(X) X(Eng4096)
+TOP_DEFINE_CZT_SPLIT(large, SPLIT_LIST)

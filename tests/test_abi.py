@@ -95,7 +95,7 @@ def test_plan_query_bluestein_sizes(lib, ny, nx, pad, py, px):
 @pytest.mark.parametrize("kw,status", [
     (dict(batch=0), 1), (dict(ny=0), 1), (dict(dx=0.0), 1), (dict(dy=-1e-6), 1), (dict(dx=float("nan")), 1),
     (dict(pad=0.5), 1), (dict(pad=float("inf")), 1), (dict(method=7), 1), (dict(batch=6, input_repeat=4), 1),
-    (dict(ny=16, nx=1500, pad=2.0), 2), (dict(ny=2049, nx=16, pad=1.0), 2),
+    (dict(ny=16, nx=2500, pad=2.0), 2), (dict(ny=4097, nx=16, pad=1.0), 2),
 ])
 def test_plan_query_rejects(lib, kw, status):
     st, *_ = plan(lib, **kw)

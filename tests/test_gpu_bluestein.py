@@ -53,7 +53,8 @@ CASES = [
     (100, 90, 2.31),   # 231 = 3 7 11, 208 = 16 13
     (8, 16, 2.0),      # 16 x 32: 16 is below the smallest plan
     (45, 37, 2.0),     # 90, 74 = 2 37
-    (1021, 24, 2.0),   # 2042 = 2 1021: 4096-point transforms; 48 planned
+    (1021, 24, 2.0),   # 2042 = 2 1021: two 2048-point halves per transform; 48 planned
+    (3001, 16, 1.0),   # 3001 (prime): two 4096-point halves per transform
 ]
 
 
@@ -266,5 +267,5 @@ def test_bluestein_limits_are_reported(T):
         T.top_propagate(x, 2e-6, 2e-6, 600e-9, 1e-2, 1.0, "di")  # DI needs a padded size >= 2 n - 1
     with pytest.raises(T.TopError, match="UNSUPPORTED"):
         T.top_propagate_noalloc(x, 2e-6, 2e-6, 600e-9, 1e-3, 1.0, out=x)  # the no-alloc call needs a plan
-    with pytest.raises(T.TopError, match="2048"):
-        T.top_propagate(dev(cfield(45, (1, 16, 1500))), 2e-6, 2e-6, 600e-9, 1e-3, 2.0)  # 3000 = 8 3 125
+    with pytest.raises(T.TopError, match="4096"):
+        T.top_propagate(dev(cfield(45, (1, 16, 2500))), 2e-6, 2e-6, 600e-9, 1e-3, 2.0)  # 5000 = 8 5^4
