@@ -208,6 +208,23 @@ def test_bluestein_fused_chain_equals_the_same_calls(T):
     assert rel_l2(host(keep), ref) < TOL
 
 
+def test_bluestein_chain_with_repeated_inputs(T):
+    """Two inputs each feeding three wavelengths (input_repeat 3) through a two-stage chain at a
+    padded size without a plan: equal to the same calls on the repeated inputs."""
+    ny, nx, pad, d = 37, 41, 1.0, 5e-6
+    lams = [450e-9, 550e-9, 650e-9] * 2
+    x = dev(cfield(97, (2, ny, nx)))
+    lens = T.Modulation(focal_length=0.04, radius=0.4 * ny * d)
+    out, inten = T.top_fused_chain(x, d, d, lams, [T.Stage(1e-3), T.Stage(2e-3, pre=lens)], pad,
+                                   intensity_group=3, input_repeat=3)
+    xr = x.repeat_interleave(3, dim=0)
+    y = T.top_propagate(xr, d, d, lams, 1e-3, pad)
+    i_ref, y_ref = T.top_propagate_intensity(y, d, d, lams, 2e-3, pad, group=3, pre=lens, keep_field=True)
+    torch.cuda.synchronize()
+    assert torch.equal(out, y_ref)
+    assert torch.equal(inten, i_ref)
+
+
 def test_bluestein_ragged_batch_with_planned_and_unplanned_sizes(T):
     descs = [(61, 61, 1.0), (64, 64, 2.0), (45, 37, 2.0), (48, 96, 2.667)]
     xs = [dev(cfield(83 + i, (ny, nx))) for i, (ny, nx, _) in enumerate(descs)]
