@@ -408,14 +408,18 @@ def run_ours(args, rank, world):
     launches_step = cols_n / args.steps
     cols_s_step = cols_ms / args.steps / 1000.0
     achieved = bytes_step / cols_s_step / 1e9
+    # ncu's DRAM bytes of a full column pass per field (workspace in and out, 2u algorithmic), as
+    # bytes per algorithmic byte, times the algorithmic bytes of an average launch of the step
     traffic = profiled_traffic("cols")
+    traffic_launch = None if traffic is None else traffic / (2 * u) * bytes_step / launches_step
     roofline = {"kernel": "cols (column pass: y-FFT x H x inverse y-FFT)", "bound": "hbm", "achieved": achieved,
                 "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
-                "traffic": None if traffic is None else traffic * sysm.batch, "peak_source": peak_kind,
+                "traffic": traffic_launch, "peak_source": peak_kind,
                 "algorithmic_bytes_per_launch": bytes_step / launches_step,
                 "avg_launch_ms": cols_s_step / launches_step * 1000.0,
                 "algorithmic_bytes_per_step": bytes_step, "launches_per_step": launches_step,
-                "traffic_note": "ncu dram bytes of one full column launch (workspace in, workspace out)",
+                "traffic_note": "ncu dram bytes of a full column pass per field (profiles/cols_summary.md) per "
+                                "algorithmic byte, times the algorithmic bytes of an average launch of the step",
                 "dominant_by_time": dominant,
                 "kernel_ms_per_step": {k: v[0] / args.steps for k, v in kinds.items()}}
     launches = int(sum(v[1] for v in prof.values()))
