@@ -544,6 +544,32 @@ def test_coherence_mask_gradient_vs_finite_differences():
     assert np.max(np.abs(fd - g_phi.reshape(-1))) < 1e-6 * np.max(np.abs(fd))
 
 
+def test_intensity_sum_closed_form():
+    """Eq. 14 on constant fields c_b: each group's plane is sum_b w_b |c_b|^2 (here 30 and 5.25
+    unweighted, 21.5 and 13.25 with the weights)."""
+    c = np.array([1, 2j, 3 + 4j, 0.5, -1, 2])
+    fields = c[:, None, None] * np.ones((6, 3, 4))
+    i = O.intensity_sum(fields, 3)
+    np.testing.assert_allclose(i[:, 0, 0], [30.0, 5.25], rtol=1e-15)
+    assert np.all(i == i[:, :1, :1])
+    iw = O.intensity_sum(fields, 3, [1.0, 2.0, 0.5, 1.0, 1.0, 3.0])
+    np.testing.assert_allclose(iw[:, 0, 0], [21.5, 13.25], rtol=1e-15)
+
+
+def test_fourf_images_the_inverted_object():
+    """The 4f system with an open pupil is an imaging system: the intensity at the output plane
+    is the object's, inverted through the axis (a Gaussian 150 um right and 100 um down of the
+    axis arrives 150 um left and 100 um up). A diverging lens, a swapped order or a missing
+    inversion fails it."""
+    n, d, f, lam = 128, 10e-6, 0.05, 500e-9
+    x = (np.arange(n) - (n - 1) / 2) * d
+    X, Y = np.meshgrid(x, x)
+    obj = np.exp(-((X - 150e-6) ** 2 + (Y + 100e-6) ** 2) / (80e-6) ** 2).astype(np.complex128)[None]
+    p4, _ = O.fourf_forward(obj, [lam], d, f, 0.64e-3, 0.64e-3, np.zeros((n, n)), 2.0)
+    image = np.abs(p4[0]) ** 2
+    assert rel_l2(image, np.abs(obj[0][::-1, ::-1]) ** 2) < 1e-5
+
+
 def test_fourf_pupil_gradient_vs_finite_differences():
     n, d, f = 16, 20e-6, 0.05
     lams = np.array([500e-9, 650e-9, 500e-9, 650e-9])
