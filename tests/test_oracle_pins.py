@@ -59,6 +59,32 @@ def test_dft_naive_matches_library(p):
     assert rel_l2(O.idft2(a, naive=True), np.moveaxis(x2, 1, -2)) < 1e-13
 
 
+def _naive_line_dft(x, sign):
+    """X[k] = sum_n x[n] exp(sign 2 pi i (k n mod P) / P) for one line, in blocks of k."""
+    p = x.shape[0]
+    n = np.arange(p, dtype=np.int64)
+    out = np.empty(p, dtype=np.complex128)
+    for k0 in range(0, p, 256):
+        k = np.arange(k0, min(p, k0 + 256), dtype=np.int64)
+        kn = np.outer(k, n) % p
+        out[k0:k0 + k.size] = np.exp(sign * 2j * math.pi * kn.astype(np.float64) / p) @ x
+    return out
+
+
+@pytest.mark.parametrize("p", [2039, 2048, 4096, 8192])
+def test_library_fft_matches_definition_at_kernel_lengths(p):
+    """The oracle's library FFT on single lines of the padded lengths the kernels transform (2048,
+    4096 and 8192 points, and the prime 2039 that the Bluestein path covers), along either axis,
+    against the DFT written out from its definition."""
+    x = normal(31 + p, (p,)) + 1j * normal(32 + p, (p,))
+    ref = _naive_line_dft(x, -1)
+    assert rel_l2(O.dft2(x[:, None])[:, 0], ref) < 1e-12
+    assert rel_l2(O.dft2(x[None, :])[0], ref) < 1e-12
+    inv = _naive_line_dft(x, +1) / p
+    assert rel_l2(O.idft2(x[:, None])[:, 0], inv) < 1e-12
+    assert rel_l2(O.idft2(x[None, :])[0], inv) < 1e-12
+
+
 def test_dft_of_delta_and_exponential():
     p = 12
     for n0 in range(p):
