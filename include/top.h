@@ -323,6 +323,19 @@ top_status top_jones(top_handle h, const top_grid* g, int64_t inner, const void*
 top_status top_jones_backward(top_handle h, const top_grid* g, int64_t inner, const void* J, const double* j_uniform,
                               const void* saved_in, const void* grad_out, void* grad_in, void* grad_J, void* stream);
 
+/* Jones matrices of the polarisation elements of §5.1 (the polariser, circular polariser and
+ * waveplate calls of the paper's polarisation listings), written as the j_uniform argument of
+ * top_jones: out is host double[18], one 3x3 matrix row-major as (re, im) pairs, with the 2x2
+ * block on (x, y) and J_zz = 1, zero z couplings. Host-only, no device work; out is caller-owned.
+ * TOP_ERR_INVALID_ARG for a NULL out or a non-finite angle, out untouched then.
+ *   linear polariser, transmission axis at theta to x: J = u u^T, u = (cos theta, sin theta);
+ *   circular polariser passing (1, i h)/sqrt 2 (h = +1 or -1): J = v v^H;
+ *   waveplate with its fast axis at theta and the given retardance (pi/2 quarter-wave, pi
+ *   half-wave): J = u u^T + exp(i retardance) w w^T, w = (-sin theta, cos theta). */
+top_status top_jones_linear_polarizer(double theta, double* out);
+top_status top_jones_circular_polarizer(int handedness, double* out);
+top_status top_jones_waveplate(double retardance, double theta, double* out);
+
 /* Power of every field, sum |psi_b|^2 dx dy (device double[batch]; float64, fixed order). */
 top_status top_field_power(top_handle h, const top_grid* g, const void* field, double* power, void* stream);
 

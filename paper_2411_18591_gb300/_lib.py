@@ -81,6 +81,9 @@ SIGNATURES = {
     "top_jones": (C.c_int, [_P, _GRID, _I64, _P, _D, _P, _P, _P]),
     "top_jones_backward": (C.c_int, [_P, _GRID, _I64, _P, _D, _P, _P, _P, _P, _P]),
     "top_field_power": (C.c_int, [_P, _GRID, _P, _P, _P]),
+    "top_jones_linear_polarizer": (C.c_int, [C.c_double, _D]),
+    "top_jones_circular_polarizer": (C.c_int, [C.c_int, _D]),
+    "top_jones_waveplate": (C.c_int, [C.c_double, C.c_double, _D]),
     "top_propagate_overlap": (C.c_int, [_P, _GRID, _P, _P, _P, _I64, _P, _P, _D, _D, _I64, _MOD, _MOD, _P]),
     "top_overlap_loss": (C.c_int, [_P, _GRID, _P, _P, _I64, _P, _P, _P]),
     "top_propagate_coherence": (C.c_int, [_P, _GRID, _P, _P, _D, _D, _MOD, _P]),

@@ -228,37 +228,28 @@ def _interp(mode: str) -> int:
 # ----------------------------------------------------------------------------- polarisation
 
 
-def jones_3x3(j2) -> "np.ndarray":
-    """A 2x2 Jones matrix on (x, y) extended to (x, y, z) with the z component unchanged."""
+def _jones_matrix(call, *args):
+    """A 3x3 Jones matrix from one of the library's constructors, as complex128 [3, 3]."""
     import numpy as np
-    m = np.zeros((3, 3), dtype=np.complex128)
-    m[:2, :2] = np.asarray(j2, dtype=np.complex128)
-    m[2, 2] = 1.0
-    return m
+    out = (C.c_double * 18)()
+    check(call(*args, out))
+    v = np.frombuffer(out, dtype=np.float64)
+    return (v[0::2] + 1j * v[1::2]).reshape(3, 3)
 
 
 def linear_polarizer(theta: float):
     """Linear polariser with its transmission axis at theta to x (§5.1)."""
-    import math
-    c, s = math.cos(theta), math.sin(theta)
-    return jones_3x3([[c * c, c * s], [c * s, s * s]])
+    return _jones_matrix(_lib.load().top_jones_linear_polarizer, float(theta))
 
 
 def circular_polarizer(handedness: int = 1):
-    """Circular polariser passing (1, i handedness) / sqrt 2."""
-    import math
-    import numpy as np
-    v = np.array([1.0, 1j * handedness]) / math.sqrt(2.0)
-    return jones_3x3(np.outer(v, np.conj(v)))
+    """Circular polariser passing (1, i handedness) / sqrt 2 (§5.1)."""
+    return _jones_matrix(_lib.load().top_jones_circular_polarizer, int(handedness))
 
 
 def waveplate(retardance: float, theta: float = 0.0):
     """Waveplate of the given retardance with its fast axis at theta (quarter-wave: pi/2, half-wave: pi)."""
-    import math
-    import numpy as np
-    c, s = math.cos(theta), math.sin(theta)
-    r = np.array([[c, s], [-s, c]])
-    return jones_3x3(r.T @ np.diag([1.0, np.exp(1j * retardance)]) @ r)
+    return _jones_matrix(_lib.load().top_jones_waveplate, float(retardance), float(theta))
 
 
 def _jones_args(jones):

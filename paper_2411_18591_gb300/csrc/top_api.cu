@@ -1827,6 +1827,55 @@ top_status top_overlap_loss(top_handle h, const top_grid* g, const double* overl
   });
 }
 
+// The Jones matrices of the elements of §5.1 as 3 x 3 matrices on (x, y, z), row-major (re, im)
+// pairs: the 2 x 2 block acts on (x, y), the z component passes unchanged (J_zz = 1).
+static void jones_put(double* out, const double (&re)[4], const double (&im)[4]) {
+  for (int k = 0; k < 18; ++k) out[k] = 0.0;
+  const int at[4] = {0, 1, 3, 4};  // (x, x), (x, y), (y, x), (y, y) in the 3 x 3 order
+  for (int k = 0; k < 4; ++k) {
+    out[2 * at[k]] = re[k];
+    out[2 * at[k] + 1] = im[k];
+  }
+  out[2 * 8] = 1.0;
+}
+
+top_status top_jones_linear_polarizer(double theta, double* out) {
+  if (!out) return fail(TOP_ERR_INVALID_ARG, "output matrix is NULL");
+  if (!std::isfinite(theta)) return fail(TOP_ERR_INVALID_ARG, "theta must be finite");
+  // projector on the transmission axis (cos theta, sin theta)
+  const double c = std::cos(theta), s = std::sin(theta);
+  jones_put(out, {c * c, c * s, s * c, s * s}, {0.0, 0.0, 0.0, 0.0});
+  return TOP_OK;
+}
+
+top_status top_jones_circular_polarizer(int handedness, double* out) {
+  if (!out) return fail(TOP_ERR_INVALID_ARG, "output matrix is NULL");
+  if (handedness != 1 && handedness != -1) return fail(TOP_ERR_INVALID_ARG, "handedness must be +1 or -1");
+  // projector on (1, i h) / sqrt 2: entries 1/2, -i h/2, i h/2, 1/2
+  const double h = 0.5 * handedness;
+  jones_put(out, {0.5, 0.0, 0.0, 0.5}, {0.0, -h, h, 0.0});
+  return TOP_OK;
+}
+
+top_status top_jones_waveplate(double retardance, double theta, double* out) {
+  if (!out) return fail(TOP_ERR_INVALID_ARG, "output matrix is NULL");
+  if (!std::isfinite(retardance) || !std::isfinite(theta))
+    return fail(TOP_ERR_INVALID_ARG, "retardance and theta must be finite");
+  // fast axis u = (cos theta, sin theta) passes unchanged, the slow axis v = (-sin theta, cos theta)
+  // is delayed by exp(i retardance): J = u u^T + exp(i retardance) v v^T
+  const double c = std::cos(theta), s = std::sin(theta);
+  const double er = std::cos(retardance), ei = std::sin(retardance);
+  const double uu[4] = {c * c, c * s, s * c, s * s};
+  const double vv[4] = {s * s, -s * c, -c * s, c * c};
+  double re[4], im[4];
+  for (int k = 0; k < 4; ++k) {
+    re[k] = uu[k] + er * vv[k];
+    im[k] = ei * vv[k];
+  }
+  jones_put(out, re, im);
+  return TOP_OK;
+}
+
 static top_status jones_common(const top_grid* g, int64_t inner, const void* J, const double* ju, Jones3* m,
                                int64_t* groups) {
   if (!g) return fail(TOP_ERR_INVALID_ARG, "grid is NULL");

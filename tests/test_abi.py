@@ -5,6 +5,7 @@ host-only calls (plan query, validation, z_critical, status strings) must work
 without a device; and nothing here launches a kernel.
 """
 import ctypes as C
+import math
 import os
 import re
 import subprocess
@@ -123,3 +124,32 @@ def test_create_without_gpu_reports_cuda_error(lib):
     st = cdll.top_create(C.byref(h), 0)
     assert st in (1, 4)  # no device: TOP_ERR_CUDA (or INVALID_ARG when the runtime reports zero devices)
     assert h.value is None
+
+
+def _jones(lib, name, *args):
+    import numpy as np
+    out = (C.c_double * 18)()
+    st = getattr(lib.load(), name)(*args, out)
+    v = np.frombuffer(out, dtype=np.float64)
+    return st, (v[0::2] + 1j * v[1::2]).reshape(3, 3)
+
+
+@pytest.mark.parametrize("theta", [0.0, 0.3, math.pi / 4, math.pi / 2, -1.1])
+def test_jones_constructors_match_the_oracle(lib, theta):
+    """The library's Jones matrices (host-only calls) against the oracle's matrix products (§5.1)."""
+    import numpy as np
+    st, m = _jones(lib, "top_jones_linear_polarizer", C.c_double(theta))
+    assert st == 0 and np.abs(m - O.linear_polarizer(theta)).max() < 1e-15
+    for ret in (math.pi / 2, math.pi, 0.7):
+        st, m = _jones(lib, "top_jones_waveplate", C.c_double(ret), C.c_double(theta))
+        assert st == 0 and np.abs(m - O.waveplate(ret, theta)).max() < 1e-15
+    for hand in (1, -1):
+        st, m = _jones(lib, "top_jones_circular_polarizer", hand)
+        assert st == 0 and np.abs(m - O.circular_polarizer(hand)).max() < 1e-15
+
+
+def test_jones_constructors_reject_bad_arguments(lib):
+    cdll = lib.load()
+    assert _jones(lib, "top_jones_circular_polarizer", 0)[0] == 1
+    assert _jones(lib, "top_jones_linear_polarizer", C.c_double(float("nan")))[0] == 1
+    assert cdll.top_jones_waveplate(C.c_double(1.0), C.c_double(0.0), None) == 1
