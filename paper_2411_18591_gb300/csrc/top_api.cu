@@ -1540,7 +1540,7 @@ top_status run_chain(top_handle h, const top_grid* g, const void* in, void* out,
     }
     for (int k = 1; k < K; ++k) {
       if (fused[k]) {
-        TOP_TRY(timed(h, KK_ROWS_INV, st, "fused row pass",
+        TOP_TRY(timed(h, KK_ROWS_CHAIN, st, "fused row pass",
                       [&] { return launch_pass(PASS_ROWS_CHAIN, geo.Px / 2, ps[k - 1], st, &ps[k]); }));
       } else {
         // two launches through the kept field or the scratch
@@ -2324,7 +2324,7 @@ top_status top_profile_read(top_handle h, int cap, const char** kinds, double* m
     h->pool.push_back(pe.second.second);
   }
   h->pending.clear();
-  static const char* names[KK_COUNT] = {"rows_fwd", "cols", "rows_inv", "aux"};
+  static const char* names[KK_COUNT] = {"rows_fwd", "cols", "rows_inv", "aux", "rows_chain"};
   int w = 0;
   for (int k = 0; k < KK_COUNT && w < cap; ++k, ++w) {
     if (kinds) kinds[w] = names[k];

@@ -36,6 +36,10 @@ namespace top {
 #ifndef TOP_ROW_THREADS
 #define TOP_ROW_THREADS 64
 #endif
+// Whether two-stage plans move their row bins directly between registers and the workspace.
+#ifndef TOP_ROW_DIRECT
+#define TOP_ROW_DIRECT 1
+#endif
 
 // Workspace index of sample (kpos, y) in the four-line block layout.
 __device__ __forceinline__ long long ws_index(int kpos, int y, int ny) {
@@ -59,7 +63,7 @@ struct RowShape {
   static constexpr int ROWS = (TOP_ROW_THREADS / EN::G) >= 1 ? (TOP_ROW_THREADS / EN::G) : 1;
   static constexpr int GROUPS = 2 * ROWS;
   static constexpr int THREADS = GROUPS * EN::G;
-  static constexpr bool DIRECT = EN::NS == 2;
+  static constexpr bool DIRECT = TOP_ROW_DIRECT && EN::NS == 2;
   // tile [2M][LD], bin k of a row at tslot(k) * LD + row: an odd stride keeps the column writes
   // free of bank conflicts; plans whose lanes hold bins 16 apart pad the bin index instead
   static constexpr int LD = EN::BIN_PAD ? (ROWS % 2 ? ROWS : ROWS + 1) : ROWS + 1;
@@ -1201,12 +1205,113 @@ __global__ void __launch_bounds__(RowShape<EX>::THREADS, RowShape<EX>::MINB_INV)
   forward_rows<EX, X2>(pb, f, y0, nrows, rows, smem, grp, t);
 }
 
+}  // namespace top
+
+#include "top_pair_rows.cuh"
+
+namespace top {
+
 // ----------------------------------------------------------------------------- launchers
 
 template <class K>
 inline cudaError_t set_smem(K kernel, size_t bytes) {
   if (bytes <= 48 * 1024) return cudaSuccess;
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+// Whether the pair-local row passes take the rows of plan EX at padding exactly 2.
+#ifndef TOP_PAIR_ROWS
+#define TOP_PAIR_ROWS 1
+#endif
+template <class EX>
+constexpr bool pair_rows() {
+  return TOP_PAIR_ROWS && PairRows<EX>::OK;
+}
+// Epilogues the pair-local inverse pass covers.
+inline bool pair_epilogue(const PassParams& p) {
+  return p.nx % 4 == 0 && (p.epi_kind == EPI_FIELD || p.epi_kind == EPI_INTENSITY ||
+                           (p.epi_kind == EPI_MODGRAD && !p.part_amp && !p.part_mask));
+}
+
+// Largest shared memory of a pair-local block: the exchange buffers and, after them, two rows of
+// staged operands (at most eight floats a sample).
+template <class EX>
+constexpr size_t pair_smem_max() {
+  return PairRows<EX>::SMEM + sizeof(float) * 2 * 8 * EX::M;
+}
+
+// The pair-local forward pass stages its source row in the pair's exchange buffers.
+template <class EX>
+inline bool pair_fwd_fits(const PassParams& p) {
+  return p.nx % 4 == 0 && size_t(pair_src_floats(p)) * sizeof(float) <= 2 * EX::BUF * sizeof(float2);
+}
+
+// The pair kernels are compiled for the modulation flag sets of common elements (none, a lens or
+// a phase mask behind an aperture) and for flags read at run time.
+constexpr uint32_t kLensCirc = TOP_MOD_LENS | TOP_MOD_CIRC;
+constexpr uint32_t kPhaseCirc = TOP_MOD_PHASE | TOP_MOD_CIRC;
+
+template <class EX, uint32_t MF>
+cudaError_t launch_rows_fwd_pair_k(const PassParams& p, cudaStream_t s) {
+  using PR = PairRows<EX>;
+  static const cudaError_t attr = set_smem(k_rows_fwd_pair<EX, MF>, PR::SMEM);
+  if (attr != cudaSuccess) return attr;
+  dim3 grid((p.ny + PR::ROWS - 1) / PR::ROWS, p.nfields);
+  TOP_LAUNCH((k_rows_fwd_pair<EX, MF>), grid, PR::THREADS, PR::SMEM, s, p);
+  return cudaGetLastError();
+}
+
+template <class EX>
+cudaError_t launch_rows_fwd_pair(const PassParams& p, cudaStream_t s) {
+  if (p.msrc.flags == 0) return launch_rows_fwd_pair_k<EX, 0>(p, s);
+  if (p.msrc.flags == kLensCirc) return launch_rows_fwd_pair_k<EX, kLensCirc>(p, s);
+  return launch_rows_fwd_pair_k<EX, TOP_MOD_DYNAMIC>(p, s);
+}
+
+template <class EX, int KIND, uint32_t MF>
+cudaError_t launch_rows_inv_pair_k(const PassParams& p, cudaStream_t s) {
+  using PR = PairRows<EX>;
+  static const cudaError_t attr = set_smem(k_rows_inv_pair<EX, KIND, MF>, pair_smem_max<EX>());
+  if (attr != cudaSuccess) return attr;
+  PassParams q = p;
+  // a field epilogue has no group: a block runs its rows of a few consecutive fields
+  if (KIND == EPI_FIELD) q.group = p.nfields < 4 ? p.nfields : 4;
+  const size_t bytes = PR::SMEM + sizeof(float) * 2 * size_t((pair_epi_floats<KIND>(q) + 3) & ~3);
+  dim3 grid((q.ny + PR::ROWS - 1) / PR::ROWS, (q.nfields + q.group - 1) / q.group);
+  TOP_LAUNCH((k_rows_inv_pair<EX, KIND, MF>), grid, PR::THREADS, bytes, s, q);
+  return cudaGetLastError();
+}
+
+template <class EX>
+cudaError_t launch_rows_inv_pair(const PassParams& p, cudaStream_t s) {
+  const uint32_t fl = p.mepi.flags;
+  if (p.epi_kind == EPI_FIELD)
+    return fl == 0 ? launch_rows_inv_pair_k<EX, EPI_FIELD, 0>(p, s) : launch_rows_inv_pair_k<EX, EPI_FIELD, TOP_MOD_DYNAMIC>(p, s);
+  if (p.epi_kind == EPI_INTENSITY)
+    return fl == 0 ? launch_rows_inv_pair_k<EX, EPI_INTENSITY, 0>(p, s)
+                   : launch_rows_inv_pair_k<EX, EPI_INTENSITY, TOP_MOD_DYNAMIC>(p, s);
+  return fl == kPhaseCirc ? launch_rows_inv_pair_k<EX, EPI_MODGRAD, kPhaseCirc>(p, s)
+                          : launch_rows_inv_pair_k<EX, EPI_MODGRAD, TOP_MOD_DYNAMIC>(p, s);
+}
+
+template <class EX, uint32_t MF>
+cudaError_t launch_rows_chain_pair_k(const PassParams& pa, const PassParams& pb, cudaStream_t s) {
+  using PR = PairRows<EX>;
+  static const cudaError_t attr = set_smem(k_rows_chain_pair<EX, MF>, pair_smem_max<EX>());
+  if (attr != cudaSuccess) return attr;
+  const size_t bytes = PR::SMEM + sizeof(float) * 2 * size_t((pair_mod_floats(pb.msrc.flags, pb.nx) + 3) & ~3);
+  dim3 grid((pa.ny + PR::ROWS - 1) / PR::ROWS, pa.nfields);
+  TOP_LAUNCH((k_rows_chain_pair<EX, MF>), grid, PR::THREADS, bytes, s, pa, pb);
+  return cudaGetLastError();
+}
+
+template <class EX>
+cudaError_t launch_rows_chain_pair(const PassParams& pa, const PassParams& pb, cudaStream_t s) {
+  const uint32_t fl = pb.msrc.flags;
+  if (fl == kLensCirc) return launch_rows_chain_pair_k<EX, kLensCirc>(pa, pb, s);
+  if (fl == kPhaseCirc) return launch_rows_chain_pair_k<EX, kPhaseCirc>(pa, pb, s);
+  if (fl == 0) return launch_rows_chain_pair_k<EX, 0>(pa, pb, s);
+  return launch_rows_chain_pair_k<EX, TOP_MOD_DYNAMIC>(pa, pb, s);
 }
 
 template <class EX, bool X2>
@@ -1266,6 +1371,9 @@ inline bool exact2(int n, int M, int o) { return n == M && o == M / 2; }
 
 template <class EX>
 cudaError_t launch_rows_fwd(const PassParams& p, cudaStream_t s) {
+  if constexpr (pair_rows<EX>()) {
+    if (exact2(p.nx, p.Mx, p.ox) && pair_fwd_fits<EX>(p)) return launch_rows_fwd_pair<EX>(p, s);
+  }
   return exact2(p.nx, p.Mx, p.ox) ? launch_rows_fwd_t<EX, true>(p, s) : launch_rows_fwd_t<EX, false>(p, s);
 }
 
@@ -1276,11 +1384,17 @@ cudaError_t launch_cols(const PassParams& p, cudaStream_t s) {
 
 template <class EX>
 cudaError_t launch_rows_chain(const PassParams& pa, const PassParams& pb, cudaStream_t s) {
+  if constexpr (pair_rows<EX>()) {
+    if (exact2(pa.nx, pa.Mx, pa.ox) && pa.nx % 4 == 0) return launch_rows_chain_pair<EX>(pa, pb, s);
+  }
   return exact2(pa.nx, pa.Mx, pa.ox) ? launch_rows_chain_t<EX, true>(pa, pb, s) : launch_rows_chain_t<EX, false>(pa, pb, s);
 }
 
 template <class EX>
 cudaError_t launch_rows_inv(const PassParams& p, cudaStream_t s) {
+  if constexpr (pair_rows<EX>()) {
+    if (exact2(p.nx, p.Mx, p.ox) && pair_epilogue(p)) return launch_rows_inv_pair<EX>(p, s);
+  }
   return exact2(p.nx, p.Mx, p.ox) ? launch_rows_inv_t<EX, true>(p, s) : launch_rows_inv_t<EX, false>(p, s);
 }
 
