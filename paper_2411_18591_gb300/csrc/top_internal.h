@@ -67,6 +67,7 @@ struct PassParams {
   int src_kind;
   int epi_kind;
   int fp64_r;      // reserved
+  int l2_ahead;    // blocks ahead whose input a block prefetches into L2 (0: none)
 
   // buffers (element strides per field)
   const float2* in;   long long in_stride;

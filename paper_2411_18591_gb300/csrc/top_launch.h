@@ -33,6 +33,14 @@ __device__ __forceinline__ void top_cp_async_wait_group() {
 }
 #endif
 
+#ifndef TOP_L2_PREFETCH
+#define TOP_L2_PREFETCH
+// Bring `bytes` (a multiple of 16) from a 16-byte aligned global address into L2, asynchronously.
+__device__ __forceinline__ void top_prefetch_l2(const void* gsrc, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(gsrc), "r"(bytes) : "memory");
+}
+#endif
+
 #ifndef TOP_NAMED_BARRIER
 #define TOP_NAMED_BARRIER
 // Barrier `id` (1..15) among `count` threads (a multiple of 32, whole warps) of the block.

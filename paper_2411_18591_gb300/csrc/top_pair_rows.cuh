@@ -20,11 +20,11 @@ namespace top {
 // Blocks per SM the pair-local inverse pass is compiled for (its group loop holds the next
 // field's bins, this field's samples and the group sums in registers at once).
 #ifndef TOP_PAIR_INV_MINB
-#define TOP_PAIR_INV_MINB 4
+#define TOP_PAIR_INV_MINB 3
 #endif
 // Whether the inverse pass loads the next field's bins before this field's epilogue.
 #ifndef TOP_PAIR_PREFETCH
-#define TOP_PAIR_PREFETCH 0
+#define TOP_PAIR_PREFETCH 1
 #endif
 
 template <class EX>
@@ -69,6 +69,17 @@ __device__ __forceinline__ void pair_store_bins(const PassParams& p, int f, int 
   const int step = (EX::M / EX::RL) * p.ny;
 #pragma unroll
   for (int e = 0; e < EX::E; ++e) wp[e * step] = v[e];
+}
+
+// The block l2_ahead blocks later in launch order (the next wave of resident blocks), whose source
+// rows the forward pass prefetches into L2.
+__device__ __forceinline__ bool ahead_block(const PassParams& p, int& f, int& tile) {
+  if (p.l2_ahead <= 0) return false;
+  const long long lb = (long long)blockIdx.y * gridDim.x + blockIdx.x + p.l2_ahead;
+  if (lb >= (long long)gridDim.x * gridDim.y) return false;
+  f = int(lb / gridDim.x);
+  tile = int(lb % gridDim.x);
+  return true;
 }
 
 // Positions of lane t: own slot k of warp r sits at lo_pos(k) + (r ? M/2 : 0), its field sample
@@ -249,6 +260,16 @@ __global__ void __launch_bounds__(PairRows<EX>::THREADS, 4) k_rows_fwd_pair(cons
   const bool inten = p.src_kind == SRC_INTENSITY;
   const ModDev& m = p.msrc;
   const uint32_t flags = mod_flags<MF>(m);
+  if (threadIdx.x == 0) {
+    int fa, tile;
+    if (ahead_block(p, fa, tile)) {
+      const int ya = tile * PR::ROWS, na = min(PR::ROWS, p.ny - ya);
+      const long long rowa = (long long)ya * nx;
+      const float2* src = inten ? p.psi + (long long)fa * p.psi_stride + rowa : field_in(p, fa) + rowa;
+      top_prefetch_l2(src, unsigned(na) * nx * 8u);
+      if (inten) top_prefetch_l2(p.gI + (long long)(fa / p.src_group) * p.gI_stride + rowa, unsigned(na) * nx * 4u);
+    }
+  }
   PairPlanes pp{};
   if (live) {
     const long long row0 = (long long)y * nx;
@@ -294,8 +315,9 @@ __host__ __device__ inline int pair_epi_floats(const PassParams& p) {
 
 // Epilogues of the pair-local inverse pass: EPI_FIELD, EPI_INTENSITY (summed over the group in
 // registers, field order), EPI_MODGRAD with at most the phase partials (summed the same way).
-// A block runs its rows of p.group consecutive fields; the operands of field f are copied while its
-// rows are transformed.
+// A block runs its rows of p.group consecutive fields (with TOP_PAIR_PREFETCH, loading the next
+// field's bins while the current one's epilogue runs); the operands of field f are copied while
+// its rows are transformed.
 template <class EX, int KIND, uint32_t MF>
 __global__ void __launch_bounds__(PairRows<EX>::THREADS, TOP_PAIR_INV_MINB) k_rows_inv_pair(const __grid_constant__ PassParams p) {
   using PR = PairRows<EX>;

@@ -463,6 +463,25 @@ __device__ __forceinline__ void apply_transfer(float2 (&v)[EY::E], const float2*
   }
 }
 
+// apply_transfer for two-stage plans with one butterfly a thread, from a row in shared memory: slot e
+// holds bin kbase(t) + e M/RL, below M/2 exactly for e < RL/2, so the mirror choice is fixed per slot.
+template <class EY>
+__device__ __forceinline__ void apply_transfer_direct(float2 (&v)[EY::E], const float2* row, int r, bool adjoint,
+                                                      int t) {
+  constexpr int M = EY::M, S = M / EY::RL;
+  const float2* part = row + r * (M / 2 + 1);
+  const int kb = EY::kbase(t);
+  const float2* up = part + kb;             // entry k = kb + e S for e < RL/2
+  const float2* down = part + (M - r - kb);  // entry M - r - k for e >= RL/2
+  if (adjoint) {
+#pragma unroll
+    for (int e = 0; e < EY::E; ++e) v[e] = c_mulc(v[e], e < EY::RL / 2 ? up[e * S] : down[-e * S]);
+  } else {
+#pragma unroll
+    for (int e = 0; e < EY::E; ++e) v[e] = c_mul(v[e], e < EY::RL / 2 ? up[e * S] : down[-e * S]);
+  }
+}
+
 // Workspace index of copy j of the CB columns from kpos0 (sample j / CB of column kpos0 + j % CB):
 // a four-line block is one contiguous stretch; a pair covers half of each of its 32-byte rows.
 template <int CB>
@@ -515,12 +534,30 @@ __global__ void __launch_bounds__(ColShape<EY>::THREADS, ColShape<EY>::MINB) k_c
     return kx <= p.Px / 2 ? kx : p.Px - kx;
   };
 
+  // the columns of the block one wave of resident blocks later go to L2 while this one works
+  if (threadIdx.x == 0 && p.l2_ahead > 0 && !p.spec_in) {
+    const long long nb = (long long)gridDim.x * gridDim.y;
+    const long long lb = (long long)blockIdx.y * gridDim.x + blockIdx.x + p.l2_ahead;
+    if (lb < nb) {
+      const int kp = int(lb % gridDim.x) * COLS;
+      const int k0 = kp & ~3, k1 = min((kp + COLS + 3) & ~3, p.Px);
+      top_prefetch_l2(p.ws + (lb / gridDim.x) * p.ws_stride + (long long)k0 * ny, unsigned(k1 - k0) * ny * 8u);
+    }
+  }
   // (A) de-interleave each unit of CB columns into contiguous lines: copy j of a unit holds
   // sample j / CB of its line j % CB (not needed when the column starts from a stored spectrum)
   if (!p.spec_in) {
-    for (int u = 0; u < ncols; u += CB) {
-      for (int j = threadIdx.x; j < CB * ny; j += NT)
-        top_cp_async8(smem + (u + j % CB) * LS + j / CB, ws + col_src<CB>(j, kpos0 + u, ny));
+    if constexpr (X2 && CB == 4 && COLS == 4 && (4 * M) % NT == 0) {
+      // one four-line block of M samples a line, contiguous: thread i copies samples i + NT k
+      const float2* src = ws + (long long)kpos0 * M + threadIdx.x;
+      float2* dst = smem + (threadIdx.x & 3) * LS + (threadIdx.x >> 2);
+#pragma unroll
+      for (int k = 0; k < 4 * M / NT; ++k) top_cp_async8(dst + k * (NT / 4), src + k * NT);
+    } else {
+      for (int u = 0; u < ncols; u += CB) {
+        for (int j = threadIdx.x; j < CB * ny; j += NT)
+          top_cp_async8(smem + (u + j % CB) * LS + j / CB, ws + col_src<CB>(j, kpos0 + u, ny));
+      }
     }
   }
   top_cp_async_commit();
@@ -591,7 +628,11 @@ __global__ void __launch_bounds__(ColShape<EY>::THREADS, ColShape<EY>::MINB) k_c
   if constexpr (SH::template stage_h<X2>()) {
     top_cp_async_wait_all();
     column_sync<EY, COLS>(cl);  // the column's transfer-function row is in place
-    apply_transfer<EY, true>(v, hrows + cl * SH::HSS, r, p.adjoint, t);
+    if constexpr (EY::NS == 2 && EY::E == EY::RL && !EY::BIN_PAD) {
+      apply_transfer_direct<EY>(v, hrows + cl * SH::HSS, r, p.adjoint, t);
+    } else {
+      apply_transfer<EY, true>(v, hrows + cl * SH::HSS, r, p.adjoint, t);
+    }
   } else if constexpr (EY::BIN_PAD) {
     // lanes hold bins 16 apart: the half's part of the row goes, read in order, into the half's
     // own exchange buffer (free between the transforms) and is applied from there
@@ -604,6 +645,58 @@ __global__ void __launch_bounds__(ColShape<EY>::THREADS, ColShape<EY>::MINB) k_c
     apply_transfer<EY, false>(v, fs.hq + (long long)abs_kx(cl) * SH::HS, r, p.adjoint, t);
   }
   EY::inv(v, xbuf, t, p.twy);
+  if constexpr (X2 && CB == 4 && COLS == 4 && (4 * M) % NT == 0 && EY::NS == 2 && EY::E == EY::RL &&
+                EY::radix(0) % 2 == 0) {
+    // Balanced combine: with slot k of the half below M/2 at position lo(k) and its partner at
+    // lo(k) + M/2, the column's sample y = pos +/- M/2 is E[pos] -/+ O'[pos]. The even warp sends
+    // E above M/2 through its own line, the odd warp O' below M/2 through its buffer; the even
+    // warp then writes the samples y >= M/2 (its slots below M/2) into the odd buffer's upper half,
+    // the odd warp the samples y < M/2 into the line's lower half.
+    constexpr int R0 = EY::radix(0), HM = M / 2, H = E / 2;
+    auto lo = [](int k) { return (k / (R0 / 2)) * R0 + k % (R0 / 2); };
+    EY::sync_group();  // every lane is past the last reads of its exchange buffer
+    if (r) {
+      const float2 wt = ldg2(p.wpy + t);
+      for_slots(
+          [&](auto ec) {
+            constexpr int e = decltype(ec)::value;
+            v[e] = c_mulc(v[e], slot_split_twiddle<EY, e>(wt));  // O' = exp(2 pi i pos / P) O
+          },
+          std::make_integer_sequence<int, E>{});
+#pragma unroll
+      for (int k = 0; k < H; ++k) obuf[EY::in_pos(t, lo(k))] = v[lo(k)];
+    } else {
+#pragma unroll
+      for (int k = 0; k < H; ++k) line[EY::in_pos(t, lo(k)) + HM] = v[lo(k) + R0 / 2];
+    }
+    column_sync<EY, COLS>(cl);
+    if (r) {
+#pragma unroll
+      for (int k = 0; k < H; ++k) {
+        const int pos = EY::in_pos(t, lo(k));
+        line[pos] = c_add(line[pos + HM], v[lo(k) + R0 / 2]);  // y = pos: E[pos + M/2] + O'[pos + M/2]
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < H; ++k) {
+        const int pos = EY::in_pos(t, lo(k));
+        obuf[pos + HM] = c_sub(v[lo(k)], obuf[pos]);  // y = pos + M/2: E[pos] - O'[pos]
+      }
+    }
+    __syncthreads();
+    // (B) the samples y < M/2 from the lines, y >= M/2 from the odd buffers, interleaved as in (A)
+    {
+      float2* dst = ws + (long long)kpos0 * M + threadIdx.x;
+      const int c = threadIdx.x & 3, y0 = threadIdx.x >> 2;
+      const float2* lo_src = smem + c * LS + y0;
+      const float2* hi_src = smem + COLS * LS + c * EY::BUF + y0;
+#pragma unroll
+      constexpr int YS = NT / 4;  // rows per step
+      static_assert(HM % YS == 0, "a step's rows lie on one side of M/2");
+      for (int k = 0; k < 4 * M / NT; ++k) dst[k * NT] = (k * YS < HM) ? lo_src[k * YS] : hi_src[k * YS];
+    }
+    return;
+  }
   EY::sync_group();  // every lane is past the last reads of its exchange buffer
   if (r) {
     if constexpr (X2) {
@@ -1219,6 +1312,20 @@ inline cudaError_t set_smem(K kernel, size_t bytes) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+// Blocks of a kernel resident on the whole device at the given block shape (0 if unknown).
+template <class K>
+inline int resident_blocks(K kernel, int threads, size_t smem) {
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess)
+    return 0;
+  return sms * per_sm;
+}
+
+#ifndef TOP_L2_AHEAD
+#define TOP_L2_AHEAD 1
+#endif
+
 // Whether the pair-local row passes take the rows of plan EX at padding exactly 2.
 #ifndef TOP_PAIR_ROWS
 #define TOP_PAIR_ROWS 1
@@ -1256,8 +1363,11 @@ cudaError_t launch_rows_fwd_pair_k(const PassParams& p, cudaStream_t s) {
   using PR = PairRows<EX>;
   static const cudaError_t attr = set_smem(k_rows_fwd_pair<EX, MF>, PR::SMEM);
   if (attr != cudaSuccess) return attr;
+  static const int resident = resident_blocks(k_rows_fwd_pair<EX, MF>, PR::THREADS, PR::SMEM);
+  PassParams q = p;
+  q.l2_ahead = TOP_L2_AHEAD ? resident : 0;
   dim3 grid((p.ny + PR::ROWS - 1) / PR::ROWS, p.nfields);
-  TOP_LAUNCH((k_rows_fwd_pair<EX, MF>), grid, PR::THREADS, PR::SMEM, s, p);
+  TOP_LAUNCH((k_rows_fwd_pair<EX, MF>), grid, PR::THREADS, PR::SMEM, s, q);
   return cudaGetLastError();
 }
 
@@ -1332,13 +1442,18 @@ cudaError_t launch_rows_fwd_t(const PassParams& p, cudaStream_t s) {
   }
 }
 
+
 template <class EY, bool X2>
 cudaError_t launch_cols_t(const PassParams& p, cudaStream_t s) {
   using SH = ColShape<EY>;
   static const cudaError_t attr = set_smem(k_cols<EY, X2>, SH::SMEM_MAX);
   if (attr != cudaSuccess) return attr;
+  const size_t bytes = SH::template smem<X2>(p.ny);
+  static const int resident = resident_blocks(k_cols<EY, X2>, SH::THREADS, bytes);
+  PassParams q = p;
+  q.l2_ahead = TOP_L2_AHEAD ? resident : 0;
   dim3 grid((p.Px + SH::COLS - 1) / SH::COLS, p.nfields);
-  TOP_LAUNCH((k_cols<EY, X2>), grid, SH::THREADS, SH::template smem<X2>(p.ny), s, p);
+  TOP_LAUNCH((k_cols<EY, X2>), grid, SH::THREADS, bytes, s, q);
   return cudaGetLastError();
 }
 
