@@ -1,5 +1,7 @@
 #include "top_aux.h"
 
+#include <cstring>
+
 #include <algorithm>
 
 #include "top_passes.cuh"
@@ -114,6 +116,32 @@ __global__ void __launch_bounds__(256) k_mse_final(long long n, const double* pa
     __syncthreads();
   }
   if (threadIdx.x == 0) *loss = red[0] / double(n);
+}
+
+// A chunk of words carried in the kernel's parameters.
+constexpr int kPutWords = 1024;
+struct PutChunk {
+  unsigned long long w[kPutWords];
+};
+
+__global__ void __launch_bounds__(256) k_put(unsigned long long* dst, int n, const __grid_constant__ PutChunk c) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = c.w[i];
+}
+
+cudaError_t launch_put(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+  if (bytes % 8 != 0) return cudaErrorInvalidValue;
+  const size_t words = bytes / 8;
+  auto* d = static_cast<unsigned long long*>(dst);
+  const auto* h = static_cast<const unsigned char*>(src);
+  PutChunk c;
+  for (size_t w0 = 0; w0 < words; w0 += kPutWords) {
+    const int n = int(words - w0 < size_t(kPutWords) ? words - w0 : size_t(kPutWords));
+    std::memcpy(c.w, h + w0 * 8, size_t(n) * 8);
+    TOP_LAUNCH(k_put, 1, 256, 0, s, d + w0, n, c);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t launch_modulate(const PassParams& p, cudaStream_t s) {

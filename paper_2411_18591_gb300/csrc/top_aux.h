@@ -11,6 +11,15 @@ namespace top {
 
 constexpr int kMseBlocks = 1024;
 
+// Write `bytes` (a multiple of 8) from host memory to device memory `dst` in stream order by kernel
+// launches whose parameters carry the bytes: no host-to-device copy from pageable memory (which
+// waits for the stream and cannot be captured in a CUDA graph), no pinned staging to keep alive.
+cudaError_t launch_put(void* dst, const void* src, size_t bytes, cudaStream_t s);
+
+// Device address of the static scratch of top_propagate_noalloc (TOP_NOALLOC_SCRATCH_BYTES) on the
+// current device, looked up with cudaGetSymbolAddress on the first call per device.
+cudaError_t noalloc_scratch_address(void** out);
+
 cudaError_t launch_modulate(const PassParams& p, cudaStream_t s);
 cudaError_t launch_modulate_backward(const PassParams& p, cudaStream_t s);
 cudaError_t launch_reduce_partials(const float* part_phase, const float* part_amp, const float2* part_mask,

@@ -29,7 +29,8 @@ def field(seed, b, n):
 
 
 def test_noalloc_equals_propagate_on_calls_in_a_row(T):
-    """Six 1024^2 fields with their own wavelengths: three fit the scratch at a time (two chunks)."""
+    """Six 1024^2 fields with their own wavelengths: two fields and their two tables fit the scratch at
+    a time (three chunks)."""
     lam = list(np.linspace(450e-9, 700e-9, 6))
     z = [0.05] * 6
     xs = [field(11, 6, 1024), field(12, 6, 1024)]
