@@ -132,7 +132,9 @@ const char* top_last_error(void);
 const char* top_status_string(top_status s);
 /* TOP_ABI_VERSION of the loaded library. */
 int top_version(void);
-/* Cap on the handle's workspace in bytes (default 8 GiB); larger batches run in chunks. */
+/* Cap on the handle's workspace in bytes (default 8 GiB, at least 1 MiB: TOP_ERR_INVALID_ARG
+ * below); larger batches run in chunks, and a call whose smallest chunk needs more returns
+ * TOP_ERR_OOM before launching anything. */
 top_status top_set_workspace_limit(top_handle h, uint64_t bytes);
 
 /* Host-only plan query: padded sizes and per-field workspace bytes of a propagation.
@@ -166,9 +168,15 @@ top_status top_propagate(top_handle h, const top_grid* g, const void* in, void* 
  * mixed workloads): field i has its own grid grids[i] (batch 1, input_repeat 0 or 1),
  * wavelength lambda[i], distance z[i] and device buffers in[i] -> out[i] (complex64 [ny][nx],
  * 16-byte aligned; in[i] == out[i] allowed). out[i] = P_z(in[i]) (Eq. 4), or the adjoint
- * P_z^H when `backward` is non-zero. Fields with the same padded geometry and method share
- * launches (per-field pointers replace the batch strides); grids, in, out, lambda, z are host
- * arrays of `count` entries. Results equal top_propagate / top_propagate_backward per field. */
+ * P_z^H when `backward` is non-zero. Fields with the same size and padded size share one launch
+ * of each pass whatever their method, spacing, wavelength and distance (per-field pointers to the
+ * fields and to their transfer-function tables replace the batch strides; up to 2048 fields a
+ * launch, fewer when the workspace limit asks for it); padded sizes without a plan of their own
+ * run field by field through the Bluestein transforms. The per-field lists reach the device
+ * through the parameters of small kernels in stream order (no host-to-device copy), so once the
+ * handle holds the tables and workspace a call launches kernels only. grids, in, out, lambda, z
+ * are host arrays of `count` entries. Results equal top_propagate / top_propagate_backward per
+ * field. */
 top_status top_propagate_ragged(top_handle h, int count, const top_grid* grids, const void* const* in,
                                 void* const* out, const double* lambda, const double* z, int backward, void* stream);
 
@@ -194,6 +202,25 @@ top_status top_fused_chain(top_handle h, const top_grid* g, const void* in, void
                            int64_t group, const double* lambda, int64_t n_lz, const top_stage* stages,
                            int nstages, void* stream);
 
+/* Backward of a chain ending at the grouped intensity (§4 through a System of §2): with the
+ * forward chain of top_fused_chain (x_k = P_{z_k}(pre_k x_{k-1}), k = 1 .. nstages, the same
+ * `stages` in forward order; their keep pointers are not used) and
+ * I[b / group] = sum of |x_K|^2 over each group of fields (Eq. 14), given the saved last field
+ * `field` = x_K (complex64 [batch][ny][nx]) and grad_intensity = dL/dI ([batch / group][ny][nx]
+ * float32): g_K = 2 dL/dI x_K, then for k = K .. 1 h_k = P_{z_k}^H g_k (conj(H)) and
+ * g_{k-1} = conj(pre_k) h_k. grad_in (may be NULL when first_grads asks for a gradient) receives
+ * g_0; first_grads (may be NULL) the gradients of stages[0].pre's phase / amplitude / mask from
+ * h_1 and its saved_in = x_0, as top_propagate_backward gives them. Each stage boundary (inverse
+ * rows of one adjoint propagation, conj(pre) of its element, forward rows of the next) is one
+ * fused row pass; padded sizes without a plan, or boundaries whose operands do not fit, run as
+ * separate propagations through a field-sized scratch with the same results. Results equal the
+ * sequence top_propagate_intensity_backward (stage K, post NULL) then top_propagate_backward
+ * (stage k with post = pre_{k+1}) down to stage 1. lambda: host, n_lz values (1 or batch);
+ * g->input_repeat 0 or 1. */
+top_status top_fused_chain_backward(top_handle h, const top_grid* g, const void* field, const float* grad_intensity,
+                                    int64_t group, const double* lambda, int64_t n_lz, const top_stage* stages,
+                                    int nstages, const top_mod_grads* first_grads, void* grad_in, void* stream);
+
 /* Bytes of the library's static device scratch used by top_propagate_noalloc. */
 #define TOP_NOALLOC_SCRATCH_BYTES (64u << 20)
 
@@ -207,17 +234,22 @@ top_status top_fused_chain(top_handle h, const top_grid* g, const void* in, void
  *
  * Scratch: the twiddle and transfer-function tables and the frequency-domain workspace of
  * each chunk of fields live in one static device array of TOP_NOALLOC_SCRATCH_BYTES per
- * device (the current device of the calling thread). Every call rewrites the tables on
- * `stream` (twiddles copied from the host, transfer functions built by a kernel), so nothing
- * in the scratch needs to start at zero. Fields are processed in chunks that fit: one field
- * needs Px * ny * 8 bytes of workspace and each distinct (lambda, z) of a chunk a table of
- * (Px/2 + 1)(Py/2 + 1) * 8 bytes (1024^2 fields at 2x padding: 16 MiB and 8 MiB). A grid
+ * device (the current device of the calling thread). The array sits in a device-code module of
+ * its own: a device holds it from the first no-alloc call there until the process exits (or from
+ * context creation when CUDA loads modules eagerly, CUDA_MODULE_LOADING=EAGER); processes that
+ * never make the call do not pay for it under CUDA's default lazy loading. Every call rewrites
+ * the tables on `stream` (twiddles written by kernels that carry them in their parameters,
+ * transfer functions built by a kernel), so nothing in the scratch needs to start at zero.
+ * Fields are processed in chunks that fit: a chunk of n fields needs n * Px * ny * 8 bytes of
+ * workspace and one table of (Px/2 + 1)(Py/2 + 2) * 8 bytes per distinct (lambda, z) among them
+ * (at most 24), and the chunk is the largest n that fits (1024^2 fields at 2x padding: 16 MiB of
+ * workspace and 8.4 MiB of table each, so three fields of one (lambda, z), or two of two). A grid
  * whose single field and table do not fit is rejected with TOP_ERR_UNSUPPORTED before
  * anything is launched.
  * The first call on a device looks up the scratch address (cudaGetSymbolAddress, which loads
- * the library's device code): make it before any stream capture. Calls share the scratch, so
- * two calls in flight at once on one device (other streams, other threads) race; order them on
- * one stream or synchronise between them.
+ * that module): make it before any stream capture. Calls share the scratch, so two calls in
+ * flight at once on one device (other streams, other threads) race; order them on one stream or
+ * synchronise between them.
  * in, out: complex64 [batch][ny][nx] device, 16-byte aligned (in == out allowed); lambda, z:
  * host arrays of n_lz values (1 or batch). Results equal top_propagate's bit for bit. */
 top_status top_propagate_noalloc(const top_grid* g, const void* in, void* out, const double* lambda,
@@ -368,7 +400,10 @@ top_status top_coherence_intensity_backward(top_handle h, const top_grid* g, con
 top_status top_profile_enable(top_handle h, int enable);
 /* Drain the recorded events (synchronising on them) and return per-kind totals.
  * kinds (up to `cap` entries) get static names, ms the summed milliseconds and count the
- * launches since the last call; *n receives the number of kinds written. */
+ * launches since the last call; *n receives the number of kinds written. The kinds are
+ * "rows_fwd" (forward row passes), "cols" (column passes), "rows_inv" (inverse row passes),
+ * "aux" (losses, reductions, modulations and the other auxiliary kernels) and "rows_chain"
+ * (the fused inverse-and-forward row passes between the stages of a system chain). */
 top_status top_profile_read(top_handle h, int cap, const char** kinds, double* ms, int64_t* count, int* n);
 
 #ifdef __cplusplus

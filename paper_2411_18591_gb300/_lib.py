@@ -70,6 +70,8 @@ SIGNATURES = {
     "top_propagate_ragged": (C.c_int, [_P, C.c_int, _GRID, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), _D, _D,
                                        C.c_int, _P]),
     "top_fused_chain": (C.c_int, [_P, _GRID, _P, _P, _P, _I64, _D, _I64, C.POINTER(TopStage), C.c_int, _P]),
+    "top_fused_chain_backward": (C.c_int, [_P, _GRID, _P, _P, _I64, _D, _I64, C.POINTER(TopStage), C.c_int, _GRADS,
+                                           _P, _P]),
     "top_propagate_backward": (C.c_int, [_P, _GRID, _P, _P, _D, _D, _I64, _MOD, _MOD, _GRADS, _P]),
     "top_propagate_intensity": (C.c_int, [_P, _GRID, _P, _P, _P, _I64, _P, _D, _D, _I64, _MOD, _MOD, _P]),
     "top_propagate_intensity_backward": (C.c_int, [_P, _GRID, _P, _P, _P, _I64, _P, _D, _D, _I64, _MOD, _MOD,

@@ -385,6 +385,41 @@ def top_fused_chain(field: torch.Tensor, dy: float, dx: float, lam, stages: Sequ
     return out, inten
 
 
+def top_fused_chain_backward(field: torch.Tensor, grad_intensity: torch.Tensor, dy: float, dx: float, lam,
+                             stages: Sequence[Stage], pad: float = 2.0, method="as", intensity_group: int = 1,
+                             saved_in: Optional[torch.Tensor] = None, want_grad_in: bool = True,
+                             grad_phase: Optional[torch.Tensor] = None, grad_amplitude: Optional[torch.Tensor] = None,
+                             grad_mask: Optional[torch.Tensor] = None) -> Optional[torch.Tensor]:
+    """Backward of top_fused_chain's grouped intensity: ``field`` is the chain's last field x_K,
+    ``grad_intensity`` dL/dI; ``stages`` in forward order. Returns dL/dx_0 (None if not
+    ``want_grad_in``) and fills the gradients of stages[0].pre given ``saved_in`` = x_0."""
+    _field(field, "field")
+    _real(grad_intensity, "grad_intensity")
+    b, ny, nx = _shape3(field)
+    grad_in = torch.empty_like(field) if want_grad_in else None
+    lams = [lam] if isinstance(lam, (int, float)) else list(lam)
+    mods = []
+    arr = (TopStage * len(stages))()
+    for i, st in enumerate(stages):
+        arr[i].z = float(st.z)
+        if st.pre is not None:
+            m = st.pre.to_c()
+            mods.append(m)
+            arr[i].pre = C.pointer(m)
+    grads = None
+    if grad_phase is not None or grad_amplitude is not None or grad_mask is not None:
+        if saved_in is None:
+            raise ValueError("modulation gradients need saved_in (the chain's input)")
+        _field(saved_in, "saved_in")
+        grads = C.byref(TopModGrads(saved_in.data_ptr(), _ptr(_real(grad_phase, "grad_phase")),
+                                    _ptr(_real(grad_amplitude, "grad_amplitude")), _ptr(grad_mask)))
+    g = make_grid(b, ny, nx, dy, dx, pad, method)
+    check(_lib.load().top_fused_chain_backward(handle(field.device), C.byref(g), field.data_ptr(),
+                                               grad_intensity.data_ptr(), int(intensity_group), doubles(lams),
+                                               len(lams), arr, len(stages), grads, _ptr(grad_in), _stream(field)))
+    return grad_in
+
+
 def top_propagate_noalloc(field: torch.Tensor, dy: float, dx: float, lam, z, pad: float = 2.0, method="as", *,
                           out: torch.Tensor) -> torch.Tensor:
     """out = P_z(field) through the library's static device scratch: no handle, no device allocation.

@@ -577,6 +577,12 @@ struct Request {
   int64_t target_stride;
   double* ov_out;              // EPI_OVERLAP: [2 batch] overlaps, [batch] powers (may be null)
   double* pw_out;
+  // upstream adjoint stages of a fused backward chain, run before this propagation: stage j
+  // propagates by up[j].z with conj(H) (up[0] starts from this request's source), then its field
+  // is multiplied by conj(up[j].pre) and enters stage j + 1, the last one this propagation (whose
+  // own source modulation is then null); each boundary is one fused row pass
+  const top_stage* up;
+  int n_up;
 };
 
 // A scratch buffer owned by the handle, grown on demand (the previous contents are not kept).
@@ -1033,6 +1039,55 @@ top_status run_bluestein(top_handle h, const Request& q, const Geometry& geo, cu
   });
 }
 
+top_status run_propagation(top_handle h, const Request& q, cudaStream_t st);
+
+// Whether every boundary of a request's upstream stages runs as one fused row pass: the next
+// stage's source operands fit the fused kernel's shared memory (as in run_chain).
+bool upstream_fuses(const Geometry& geo, const Request& q) {
+  EngineInfo ex;
+  if (!find_engine(geo.Px / 2, &ex)) return false;
+  for (int j = 0; j < q.n_up; ++j) {
+    PassParams probe{};
+    probe.nx = geo.nx;
+    probe.src_kind = SRC_FIELD;
+    probe.msrc = mod_dev(q.up[j].pre, 1, nullptr);
+    const size_t planes = src_plane_floats(probe, ex.rows);
+    const size_t rows_end = sizeof(float2) * (size_t(2) * ex.rows * ex.M + size_t(ex.rows) * geo.nx);
+    const size_t bytes = std::max(rows_end, ex.row_smem) + sizeof(float) * planes;
+    if (!((planes == 0 || geo.nx % 4 == 0) && bytes <= kChainSmemMax)) return false;
+  }
+  return true;
+}
+
+// The upstream stages of a request one propagation at a time through a field-sized scratch (sizes
+// without a plan of their own, or boundaries that do not fuse), then the request itself; the same
+// results as the fused passes.
+top_status run_upstream_unfused(top_handle h, const Request& q, cudaStream_t st) {
+  const int64_t B = q.g->batch;
+  const size_t plane = size_t(q.g->ny) * size_t(q.g->nx);
+  TOP_TRY(grow_scratch(&h->chain, &h->chain_bytes, sizeof(float2) * size_t(B) * plane, "cudaMalloc(chain scratch)"));
+  void* tmp = h->chain;
+  for (int j = 0; j < q.n_up; ++j) {
+    const std::vector<double> zj(size_t(q.n_lz), q.up[j].z);
+    Request r{};
+    r.g = q.g; r.lam = q.lam; r.z = zj.data(); r.n_lz = q.n_lz; r.adjoint = 1;
+    if (j == 0) {
+      r.src_kind = q.src_kind; r.in = q.in; r.psi_src = q.psi_src; r.gI = q.gI; r.group = q.group;
+      r.weights = q.weights;
+    } else {
+      r.src_kind = SRC_FIELD; r.in = tmp; r.group = 1;
+      r.msrc = q.up[j - 1].pre; r.msrc_conj = 1;
+    }
+    r.epi_kind = EPI_FIELD; r.out = tmp;
+    TOP_TRY(run_propagation(h, r, st));
+  }
+  Request m = q;
+  m.up = nullptr; m.n_up = 0;
+  m.src_kind = SRC_FIELD; m.in = tmp; m.psi_src = nullptr; m.gI = nullptr; m.weights = nullptr; m.group = 1;
+  m.msrc = q.up[q.n_up - 1].pre; m.msrc_conj = 1;
+  return run_propagation(h, m, st);
+}
+
 top_status run_propagation(top_handle h, const Request& q, cudaStream_t st) {
   const top_grid* g = q.g;
   Geometry geo;
@@ -1081,6 +1136,14 @@ top_status run_propagation(top_handle h, const Request& q, cudaStream_t st) {
         if (p && !aligned16(p)) return fail(TOP_ERR_INVALID_ARG, "gradient output not 16-byte aligned");
     }
   }
+  if (q.n_up > 0) {
+    if (!q.adjoint || q.msrc) return fail(TOP_ERR_INTERNAL, "upstream stages need an adjoint request without a source modulation");
+    for (int j = 0; j < q.n_up; ++j) {
+      if (!std::isfinite(q.up[j].z)) return fail(TOP_ERR_INVALID_ARG, "stage %d: z must be finite", j);
+      TOP_TRY(check_mod(q.up[j].pre, "stage modulation"));
+    }
+    if (!planned || !upstream_fuses(geo, q)) return run_upstream_unfused(h, q, st);
+  }
   if (!planned) return run_bluestein(h, q, geo, st);
   TOP_TRY(bind(h));
 
@@ -1095,7 +1158,9 @@ top_status run_propagation(top_handle h, const Request& q, cudaStream_t st) {
   if (q.msrc && (q.msrc->flags & TOP_MOD_CIRC)) TOP_TRY(circ_table(h, geo.ny, geo.nx, g->dy, g->dx, q.msrc->radius, &circ_src));
   if (q.mepi && (q.mepi->flags & TOP_MOD_CIRC)) TOP_TRY(circ_table(h, geo.ny, geo.nx, g->dy, g->dx, q.mepi->radius, &circ_epi));
 
-  // per-field parameter sets
+  // per-field parameter sets (the source-side lens tables of this propagation belong to its
+  // source modulation, or with upstream stages to the last boundary's)
+  const top_mod* src_mod = q.n_up > 0 ? q.up[q.n_up - 1].pre : q.msrc;
   std::vector<FieldSet> field_sets(B);
   for (int64_t b = 0; b < B; ++b) {
     const int64_t i = q.n_lz == 1 ? 0 : b;
@@ -1103,9 +1168,9 @@ top_status run_propagation(top_handle h, const Request& q, cudaStream_t st) {
     TOP_TRY(field_transfer(h, g, geo.ny, geo.nx, geo.Py, geo.Px, q.lam[i], q.z[i], st, &te));
     FieldSet fs{};
     fs.hq = te.hq;
-    if (q.msrc && (q.msrc->flags & TOP_MOD_LENS)) {
-      TOP_TRY(lens_table(h, geo.nx, g->dx, q.lam[i], q.msrc->focal_length, &fs.src_lx));
-      TOP_TRY(lens_table(h, geo.ny, g->dy, q.lam[i], q.msrc->focal_length, &fs.src_ly));
+    if (src_mod && (src_mod->flags & TOP_MOD_LENS)) {
+      TOP_TRY(lens_table(h, geo.nx, g->dx, q.lam[i], src_mod->focal_length, &fs.src_lx));
+      TOP_TRY(lens_table(h, geo.ny, g->dy, q.lam[i], src_mod->focal_length, &fs.src_ly));
     }
     if (q.mepi && (q.mepi->flags & TOP_MOD_LENS)) {
       TOP_TRY(lens_table(h, geo.nx, g->dx, q.lam[i], q.mepi->focal_length, &fs.epi_lx));
@@ -1113,7 +1178,37 @@ top_status run_propagation(top_handle h, const Request& q, cudaStream_t st) {
     }
     field_sets[b] = fs;
   }
-  auto same = [](const FieldSet& a, const FieldSet& b) { return std::memcmp(&a, &b, sizeof(FieldSet)) == 0; };
+  // upstream stages: stage j's transfer table and the lens tables of the boundary modulation its
+  // forward row pass applies (none for the first, which starts from the request's source)
+  std::vector<std::vector<FieldSet>> up_sets(size_t(q.n_up), std::vector<FieldSet>(B));
+  std::vector<const int2*> up_circ(size_t(q.n_up), nullptr);
+  for (int j = 0; j < q.n_up; ++j) {
+    const top_mod* bm = j > 0 ? q.up[j - 1].pre : nullptr;
+    if (q.up[j].pre && (q.up[j].pre->flags & TOP_MOD_CIRC))
+      TOP_TRY(circ_table(h, geo.ny, geo.nx, g->dy, g->dx, q.up[j].pre->radius, &up_circ[j]));
+    for (int64_t b = 0; b < B; ++b) {
+      const int64_t i = q.n_lz == 1 ? 0 : b;
+      TransferEntry te;
+      TOP_TRY(field_transfer(h, g, geo.ny, geo.nx, geo.Py, geo.Px, q.lam[i], q.up[j].z, st, &te));
+      FieldSet fs{};
+      fs.hq = te.hq;
+      if (bm && (bm->flags & TOP_MOD_LENS)) {
+        TOP_TRY(lens_table(h, geo.nx, g->dx, q.lam[i], bm->focal_length, &fs.src_lx));
+        TOP_TRY(lens_table(h, geo.ny, g->dy, q.lam[i], bm->focal_length, &fs.src_ly));
+      }
+      up_sets[j][b] = fs;
+    }
+  }
+  if (q.n_up > 0 && q.msrc == nullptr && src_mod && (src_mod->flags & TOP_MOD_CIRC))
+    TOP_TRY(circ_table(h, geo.ny, geo.nx, g->dy, g->dx, src_mod->radius, &circ_src));
+  auto same_one = [](const FieldSet& a, const FieldSet& b) { return std::memcmp(&a, &b, sizeof(FieldSet)) == 0; };
+  // fields share a parameter-set slot when every stage's set agrees
+  auto same_field = [&](int64_t a, int64_t b) {
+    if (!same_one(field_sets[a], field_sets[b])) return false;
+    for (int j = 0; j < q.n_up; ++j)
+      if (!same_one(up_sets[j][a], up_sets[j][b])) return false;
+    return true;
+  };
 
   // epilogue grouping and workspace
   const long long plane = (long long)geo.ny * geo.nx;
@@ -1198,7 +1293,7 @@ top_status run_propagation(top_handle h, const Request& q, cudaStream_t st) {
   p.twy = twy;
   p.wpx = wpx;
   p.wpy = wpy;
-  const ModDev msrc_base = mod_dev(q.msrc, q.msrc_conj, circ_src);
+  const ModDev msrc_base = q.n_up > 0 ? mod_dev(src_mod, 1, circ_src) : mod_dev(q.msrc, q.msrc_conj, circ_src);
   const ModDev mepi_base = mod_dev(q.mepi, q.mepi_conj, circ_epi);
   p.ws = ws;
   p.ws_stride = (long long)geo.Px * geo.ny;
@@ -1210,37 +1305,36 @@ top_status run_propagation(top_handle h, const Request& q, cudaStream_t st) {
   p.outf_stride = plane;
   p.part_stride = plane;
 
+  std::vector<PassParams> pu(size_t(q.n_up));
   int64_t pos = 0;
   while (pos < B) {
-    // grow the chunk field by field while the distinct parameter sets fit
+    // grow the chunk field by field while the distinct parameter sets fit (one representative
+    // field per set)
     int64_t n = 0;
     p.nsets = 0;
+    std::vector<int64_t> rep;
     while (pos + n < B && n < chunk) {
       // a whole aligned group of fields at a time
       int64_t gend = std::min<int64_t>(B, pos + n + align);
-      int added_sets = 0;
-      FieldSet tmp[kMaxSets];
-      int tmpn = p.nsets;
-      std::memcpy(tmp, p.sets, sizeof(FieldSet) * p.nsets);
+      std::vector<int64_t> rep2 = rep;
       unsigned char idx_tmp[kMaxFields];
       bool ok = true;
       for (int64_t b = pos + n; b < gend; ++b) {
-        int k = 0;
-        while (k < tmpn && !same(tmp[k], field_sets[b])) ++k;
-        if (k == tmpn) {
-          if (tmpn == kMaxSets) { ok = false; break; }
-          tmp[tmpn++] = field_sets[b];
-          ++added_sets;
+        size_t k = 0;
+        while (k < rep2.size() && !same_field(rep2[k], b)) ++k;
+        if (k == rep2.size()) {
+          if ((int)rep2.size() == kMaxSets) { ok = false; break; }
+          rep2.push_back(b);
         }
         idx_tmp[b - pos - n] = (unsigned char)k;
       }
       if (!ok) break;
-      std::memcpy(p.sets, tmp, sizeof(FieldSet) * tmpn);
-      p.nsets = tmpn;
+      rep = rep2;
       std::memcpy(p.set_of + n, idx_tmp, size_t(gend - pos - n));
       n = gend - pos;
-      (void)added_sets;
     }
+    p.nsets = int(rep.size());
+    for (size_t k = 0; k < rep.size(); ++k) p.sets[k] = field_sets[rep[k]];
     if (n == 0) return fail(TOP_ERR_UNSUPPORTED, "a group of fields uses more than %d (lambda, z) sets", kMaxSets);
     p.nfields = int(n);
     p.group = int(group);
@@ -1276,7 +1370,39 @@ top_status run_propagation(top_handle h, const Request& q, cudaStream_t st) {
       // per-field gradients use groups of one field
       p.group = partials ? int(group) : 1;
     }
-    if (share) {
+    if (q.n_up > 0) {
+      // upstream adjoint stages: the first from this request's source, each boundary (inverse rows
+      // of one stage, conj(pre) of its element, forward rows of the next) one fused pass
+      for (int j = 0; j < q.n_up; ++j) {
+        PassParams& u = pu[j];
+        u = p;
+        for (size_t k = 0; k < rep.size(); ++k) u.sets[k] = up_sets[j][rep[k]];
+        u.epi_kind = EPI_FIELD;
+        u.out = nullptr;
+        u.outf = nullptr;
+        u.mepi = ModDev{};
+        u.group = 1;
+        u.part_phase = nullptr;
+        u.part_amp = nullptr;
+        u.part_mask = nullptr;
+        u.xs = nullptr;
+        if (j > 0) {
+          u.src_kind = SRC_FIELD;
+          u.msrc = offset_mod(mod_dev(q.up[j - 1].pre, 1, up_circ[j - 1]), pos);
+        } else {
+          u.msrc = ModDev{};
+        }
+      }
+      TOP_TRY(timed(h, KK_ROWS_FWD, st, "rows forward pass", [&] { return launch_pass(PASS_ROWS_FWD, p.Mx, pu[0], st); }));
+      TOP_TRY(timed(h, KK_COLS, st, "column pass", [&] { return launch_pass(PASS_COLS, p.My, pu[0], st); }));
+      for (int j = 0; j < q.n_up; ++j) {
+        PassParams nxt = j + 1 < q.n_up ? pu[j + 1] : p;
+        nxt.src_kind = SRC_FIELD;
+        TOP_TRY(timed(h, KK_ROWS_CHAIN, st, "fused row pass",
+                      [&] { return launch_pass(PASS_ROWS_CHAIN, p.Mx, pu[j], st, &nxt); }));
+        TOP_TRY(timed(h, KK_COLS, st, "column pass", [&] { return launch_pass(PASS_COLS, p.My, nxt, st); }));
+      }
+    } else if (share) {
       const PassParams ps = source_params(p, int(in_repeat), spec);
       PassParams pc = p;
       pc.spec_in = spec;
@@ -1589,13 +1715,14 @@ top_status run_ragged(top_handle h, int count, const top_grid* grids, const void
     q.epi_kind = EPI_FIELD; q.out = out[i];
     TOP_TRY(run_bluestein(h, q, geos[i], st));
   }
-  // groups of one geometry and method, in first-appearance order
+  // groups of one geometry (padded sizes and the field's size), in first-appearance order: fields of
+  // any method, wavelength, distance and spacing share a launch (each column reads its own table)
   std::vector<std::vector<int>> groups;
-  std::vector<std::array<int, 5>> keys;
+  std::vector<std::array<int, 4>> keys;
   for (int i = 0; i < count; ++i) {
     const Geometry& q = geos[i];
     if (!has_engines(q)) continue;
-    const std::array<int, 5> key = {q.ny, q.nx, q.Py, q.Px, grids[i].method};
+    const std::array<int, 4> key = {q.ny, q.nx, q.Py, q.Px};
     size_t k = 0;
     while (k < keys.size() && keys[k] != key) ++k;
     if (k == keys.size()) {
@@ -1606,7 +1733,6 @@ top_status run_ragged(top_handle h, int count, const top_grid* grids, const void
   }
   for (const auto& grp : groups) {
     const Geometry geo = geos[grp[0]];
-    const int method = grids[grp[0]].method;
     const long long plane = (long long)geo.ny * geo.nx;
     const float2 *twx, *twy, *wpx, *wpy;
     TOP_TRY(engine_twiddles(h, geo.Px / 2, &twx));
@@ -1614,16 +1740,15 @@ top_status run_ragged(top_handle h, int count, const top_grid* grids, const void
     TOP_TRY(split_twiddles(h, geo.Px, &wpx));
     TOP_TRY(split_twiddles(h, geo.Py, &wpy));
     const int64_t nf = int64_t(grp.size());
-    std::vector<FieldSet> fsets(nf);
+    std::vector<const float2*> tables(nf);
     for (int64_t j = 0; j < nf; ++j) {
       const int i = grp[j];
       TransferEntry te;
       TOP_TRY(field_transfer(h, &grids[i], geo.ny, geo.nx, geo.Py, geo.Px, lam[i], z[i], st, &te));
-      fsets[j] = FieldSet{};
-      fsets[j].hq = te.hq;
+      tables[j] = te.hq;
     }
     const size_t ws_field = size_t(geo.Px) * size_t(geo.ny) * sizeof(float2);
-    const size_t ptr_field = 2 * sizeof(void*);
+    const size_t ptr_field = 3 * sizeof(void*);
     int64_t chunk = std::min<int64_t>(nf, kMaxFields);
     auto need = [&](int64_t c) { return size_t(c) * ws_field + 256 + size_t(c) * ptr_field; };
     while (chunk > 1 && need(chunk) > h->ws_limit) chunk /= 2;
@@ -1634,8 +1759,7 @@ top_status run_ragged(top_handle h, int count, const top_grid* grids, const void
     float2* ws = static_cast<float2*>(h->ws);
     char* tail = reinterpret_cast<char*>(h->ws) + size_t(chunk) * ws_field;
     tail = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(tail) + 255) & ~uintptr_t(255));
-    const float2** d_in = reinterpret_cast<const float2**>(tail);
-    float2** d_out = reinterpret_cast<float2**>(tail + size_t(chunk) * sizeof(void*));
+    void** d_lists = reinterpret_cast<void**>(tail);  // [in][out][table], chunk entries each
 
     PassParams p{};
     p.ny = geo.ny;
@@ -1646,7 +1770,7 @@ top_status run_ragged(top_handle h, int count, const top_grid* grids, const void
     p.Mx = geo.Px / 2;
     p.oy = geo.oy;
     p.ox = geo.ox;
-    p.method = method;
+    p.method = grids[grp[0]].method;
     p.adjoint = backward ? 1 : 0;
     p.src_kind = SRC_FIELD;
     p.epi_kind = EPI_FIELD;
@@ -1661,33 +1785,22 @@ top_status run_ragged(top_handle h, int count, const top_grid* grids, const void
     p.group = 1;
     p.src_group = 1;
     p.in_repeat = 1;
-    p.in_list = d_in;
-    p.out_list = d_out;
-    auto same = [](const FieldSet& a, const FieldSet& b) { return std::memcmp(&a, &b, sizeof(FieldSet)) == 0; };
-    std::vector<const void*> ptrs(2 * size_t(chunk));
+    p.in_list = reinterpret_cast<const float2* const*>(d_lists);
+    p.out_list = reinterpret_cast<float2* const*>(d_lists + chunk);
+    p.hq_list = reinterpret_cast<const float2* const*>(d_lists + 2 * chunk);
+    p.nsets = 1;  // no lens tables; every column pass reads its field's table from hq_list
+    std::vector<const void*> lists(3 * size_t(chunk));
     int64_t pos = 0;
     while (pos < nf) {
-      int64_t n = 0;
-      p.nsets = 0;
-      while (pos + n < nf && n < chunk) {
-        int k = 0;
-        while (k < p.nsets && !same(p.sets[k], fsets[pos + n])) ++k;
-        if (k == p.nsets) {
-          if (p.nsets == kMaxSets) break;
-          p.sets[p.nsets++] = fsets[pos + n];
-        }
-        p.set_of[n] = (unsigned char)k;
-        ++n;
-      }
+      const int64_t n = std::min<int64_t>(chunk, nf - pos);
       for (int64_t j = 0; j < n; ++j) {
-        ptrs[j] = in[grp[pos + j]];
-        ptrs[size_t(chunk) + j] = out[grp[pos + j]];
+        lists[j] = in[grp[pos + j]];
+        lists[size_t(chunk) + j] = out[grp[pos + j]];
+        lists[2 * size_t(chunk) + j] = tables[pos + j];
       }
-      // the pointer arrays are rewritten in stream order after the previous chunk's kernels
-      TOP_CUDA(cudaMemcpyAsync(d_in, ptrs.data(), size_t(n) * sizeof(void*), cudaMemcpyHostToDevice, st),
-               "cudaMemcpyAsync(ragged input pointers)");
-      TOP_CUDA(cudaMemcpyAsync(d_out, ptrs.data() + chunk, size_t(n) * sizeof(void*), cudaMemcpyHostToDevice, st),
-               "cudaMemcpyAsync(ragged output pointers)");
+      // the lists are rewritten in stream order after the previous chunk's kernels, by kernels
+      // that carry them in their parameters
+      TOP_CUDA(launch_put(d_lists, lists.data(), lists.size() * sizeof(void*), st), "ragged field lists");
       p.nfields = int(n);
       TOP_TRY(timed(h, KK_ROWS_FWD, st, "rows forward pass", [&] { return launch_pass(PASS_ROWS_FWD, p.Mx, p, st); }));
       TOP_TRY(timed(h, KK_COLS, st, "column pass", [&] { return launch_pass(PASS_COLS, p.My, p, st); }));
@@ -2019,6 +2132,37 @@ top_status top_propagate_intensity(top_handle h, const top_grid* g, const void* 
   return run_propagation(h, q, static_cast<cudaStream_t>(stream));
 }
 
+top_status top_fused_chain_backward(top_handle h, const top_grid* g, const void* field, const float* grad_intensity,
+                                    int64_t group, const double* lambda, int64_t n_lz, const top_stage* stages,
+                                    int nstages, const top_mod_grads* first_grads, void* grad_in, void* stream) {
+  if (!h) return fail(TOP_ERR_INVALID_ARG, "handle is NULL");
+  if (!g) return fail(TOP_ERR_INVALID_ARG, "grid is NULL");
+  if (!stages || nstages < 1) return fail(TOP_ERR_INVALID_ARG, "a chain needs at least one stage");
+  if (g->input_repeat > 1) return fail(TOP_ERR_INVALID_ARG, "the backward of a chain takes input_repeat 0 or 1");
+  for (int k = 0; k < nstages; ++k) {
+    if (!std::isfinite(stages[k].z)) return fail(TOP_ERR_INVALID_ARG, "stage %d: z must be finite", k);
+    TOP_TRY(check_mod(stages[k].pre, "stage modulation"));
+  }
+  // stage 0's adjoint is the request; stages K-1 .. 1 run upstream of it, in that order
+  std::vector<top_stage> up;
+  for (int k = nstages - 1; k >= 1; --k) up.push_back(stages[k]);
+  std::vector<double> z0(size_t(std::max<int64_t>(1, n_lz)), stages[0].z);
+  Request q{};
+  q.g = g; q.lam = lambda; q.z = z0.data(); q.n_lz = n_lz; q.adjoint = 1;
+  q.src_kind = SRC_INTENSITY; q.psi_src = field; q.gI = grad_intensity; q.group = group;
+  q.up = up.empty() ? nullptr : up.data();
+  q.n_up = int(up.size());
+  const top_mod* pre0 = stages[0].pre;
+  const bool pg = first_grads && (first_grads->grad_phase || first_grads->grad_amplitude || first_grads->grad_mask);
+  if (pg) {
+    q.epi_kind = EPI_MODGRAD; q.out = grad_in; q.mepi = pre0; q.mepi_conj = 0; q.grads = first_grads;
+  } else {
+    if (!grad_in) return fail(TOP_ERR_INVALID_ARG, "grad_in is NULL and no modulation gradient requested");
+    q.epi_kind = EPI_FIELD; q.out = grad_in; q.mepi = pre0; q.mepi_conj = 1;
+  }
+  return run_propagation(h, q, static_cast<cudaStream_t>(stream));
+}
+
 top_status top_propagate_intensity_backward(top_handle h, const top_grid* g, const void* field,
                                             const float* grad_intensity, void* grad_in, int64_t group,
                                             const float* weights, const double* lambda, const double* z,
@@ -2341,30 +2485,15 @@ top_status top_profile_read(top_handle h, int cap, const char** kinds, double* m
 
 // ============================================================================= static-scratch propagation
 
-// Tables and workspace of top_propagate_noalloc: one static array per device, no allocation.
-static __device__ __align__(256) unsigned char g_noalloc_scratch[TOP_NOALLOC_SCRATCH_BYTES];
-
 namespace {
-
-constexpr int kNoallocDevices = 64;
-std::mutex g_noalloc_mutex;
-void* g_noalloc_addr[kNoallocDevices] = {};
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
-// Address of the scratch on the current device, looked up once per device.
+// Address of the static scratch on the current device (looked up once per device).
 top_status noalloc_scratch(void** out) {
-  int dev = -1;
-  TOP_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
-  if (dev < 0 || dev >= kNoallocDevices) return fail(TOP_ERR_UNSUPPORTED, "device %d beyond the %d supported", dev, kNoallocDevices);
-  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-  if (!g_noalloc_addr[dev]) {
-    void* p = nullptr;
-    TOP_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch), "cudaGetSymbolAddress(static scratch)");
-    if (!p) return fail(TOP_ERR_CUDA, "static scratch has no device address");
-    g_noalloc_addr[dev] = p;
-  }
-  *out = g_noalloc_addr[dev];
+  const cudaError_t e = noalloc_scratch_address(out);
+  if (e == cudaErrorInvalidDevice) return fail(TOP_ERR_UNSUPPORTED, "device beyond the ones the static scratch supports");
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(static scratch)");
   return TOP_OK;
 }
 
@@ -2430,16 +2559,23 @@ top_status propagate_noalloc(const top_grid* g, const void* in, void* out, const
     std::sort(all.begin(), all.end());
     distinct = std::unique(all.begin(), all.end()) - all.begin();
   }
-  const int slots = int(std::min<int64_t>({int64_t(kMaxSets), distinct, int64_t((cap - tw_bytes - ws_field) / set_bytes)}));
+  // the chunk first: the most fields n whose workspace and min(n, distinct, kMaxSets) tables fit
+  auto fits = [&](int64_t n) {
+    const int64_t sets = std::min<int64_t>({n, distinct, int64_t(kMaxSets)});
+    return tw_bytes + size_t(sets) * set_bytes + size_t(n) * ws_field <= cap;
+  };
+  int64_t chunk = std::min<int64_t>(B, kMaxFields);
+  while (chunk > 1 && !fits(chunk)) --chunk;
+  const int slots = int(std::min<int64_t>({chunk, distinct, int64_t(kMaxSets)}));
   const size_t table_bytes = tw_bytes + size_t(slots) * set_bytes;
-  const int64_t chunk = std::min<int64_t>({B, int64_t(kMaxFields), int64_t((cap - table_bytes) / ws_field)});
 
   void* scratch = nullptr;
   TOP_TRY(noalloc_scratch(&scratch));
   unsigned char* base = static_cast<unsigned char*>(scratch);
   float2* ws = reinterpret_cast<float2*>(base + table_bytes);
 
-  // twiddles: host image, one copy ordered on the stream
+  // twiddles: written in stream order by kernels that carry them in their parameters (no copy from
+  // pageable host memory)
   std::vector<float2> twx, twy, wpx(geo.Px / 2), wpy(geo.Py / 2);
   noalloc_engine_twiddles(geo.Px / 2, twx);
   noalloc_engine_twiddles(geo.Py / 2, twy);
@@ -2448,7 +2584,8 @@ top_status propagate_noalloc(const top_grid* g, const void* in, void* out, const
   std::vector<unsigned char> img;
   const size_t o_twx = put(img, twx), o_twy = put(img, twy), o_wpx = put(img, wpx), o_wpy = put(img, wpy);
   if (img.size() > tw_bytes) return fail(TOP_ERR_INTERNAL, "static twiddle image above its reserved size");
-  TOP_CUDA(cudaMemcpyAsync(base, img.data(), img.size(), cudaMemcpyHostToDevice, st), "cudaMemcpyAsync(static twiddles)");
+  img.resize((img.size() + 7) & ~size_t(7));
+  TOP_CUDA(launch_put(base, img.data(), img.size(), st), "static twiddles");
 
   PassParams p{};
   p.ny = geo.ny;

@@ -75,6 +75,9 @@ struct PassParams {
   // in + f * in_stride and out + f * out_stride when non-null
   const float2* const* in_list;
   float2* const* out_list;
+  // per-field transfer-function tables (device array of nfields entries) that replace
+  // sets[set_of[f]].hq in the column pass when non-null (ragged batches: no limit on the sets)
+  const float2* const* hq_list;
   float2* ws;         long long ws_stride;   // pass workspace [field][Px][ny]
   float2* out;        long long out_stride;
   float* outf;        long long outf_stride; // intensity output per group / partial sums per group

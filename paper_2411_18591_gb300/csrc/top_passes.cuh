@@ -522,6 +522,7 @@ __global__ void __launch_bounds__(ColShape<EY>::THREADS, ColShape<EY>::MINB) k_c
   const int ncols = min(COLS, p.Px - kpos0);  // a multiple of CB
   const int f = blockIdx.y;
   const FieldSet& fs = p.sets[p.set_of[f]];
+  const float2* hq = p.hq_list ? p.hq_list[f] : fs.hq;
   float2* line = smem + cl * LS;                            // [COLS][LS]
   float2* obuf = smem + COLS * LS + cl * EY::BUF;           // the odd half's exchange buffer and output
   float2* xbuf = r ? obuf : line;
@@ -566,7 +567,7 @@ __global__ void __launch_bounds__(ColShape<EY>::THREADS, ColShape<EY>::MINB) k_c
     // waited for only where it is applied: the copy overlaps the forward transform
     if (!p.spec_out && !p.hq_out) {
       const int ct = threadIdx.x - cl * 2 * G;  // thread of the column's 2G
-      const float2* hsrc = fs.hq + (long long)abs_kx(cl) * SH::HS;
+      const float2* hsrc = hq + (long long)abs_kx(cl) * SH::HS;
       float2* hdst = hrows + cl * SH::HSS;
       if constexpr (EY::BIN_PAD) {
         for (int q = ct; q < SH::HS; q += 2 * G) top_cp_async8(hdst + EY::bin_slot(q), hsrc + q);
@@ -636,13 +637,13 @@ __global__ void __launch_bounds__(ColShape<EY>::THREADS, ColShape<EY>::MINB) k_c
   } else if constexpr (EY::BIN_PAD) {
     // lanes hold bins 16 apart: the half's part of the row goes, read in order, into the half's
     // own exchange buffer (free between the transforms) and is applied from there
-    const float2* part = fs.hq + (long long)abs_kx(cl) * SH::HS + r * (M / 2 + 1);
+    const float2* part = hq + (long long)abs_kx(cl) * SH::HS + r * (M / 2 + 1);
     EY::sync_group();  // every lane is past its last read of the forward transform's exchanges
     for (int i = t; i < M / 2 + 1; i += G) xbuf[EY::bin_slot(i)] = ldg2(part + i);
     EY::sync_group();
     apply_transfer<EY, true, true>(v, xbuf, r, p.adjoint, t);
   } else {
-    apply_transfer<EY, false>(v, fs.hq + (long long)abs_kx(cl) * SH::HS, r, p.adjoint, t);
+    apply_transfer<EY, false>(v, hq + (long long)abs_kx(cl) * SH::HS, r, p.adjoint, t);
   }
   EY::inv(v, xbuf, t, p.twy);
   if constexpr (X2 && CB == 4 && COLS == 4 && (4 * M) % NT == 0 && EY::NS == 2 && EY::E == EY::RL &&

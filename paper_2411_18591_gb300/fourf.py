@@ -10,6 +10,8 @@ A sequence of library calls, no arithmetic of its own:
   L   = mean((I - T)^2), dL/dI
   B4  g3 = P_f^H(2 dL/dI psi4)               (intensity backward)
   B3  dL/dphi = sum_b Im(g_y conj(pupil psi2)),  g_y = P_f^H(conj(lens2) g3)
+      (B4-B3 run as one fused backward chain: the row passes between the two adjoint
+      propagations are one kernel)
 
 Fields are ordered (object, component, wavelength), so each object's fields are
 consecutive (one intensity group) and each (object, component) input feeds its
@@ -62,9 +64,7 @@ class FourF:
     def pupil(self, phase: torch.Tensor) -> B.Modulation:
         return B.Modulation(phase=phase, radius=self.pupil_radius)
 
-    def step(self, obj: torch.Tensor, phase: torch.Tensor, target: torch.Tensor, grad_phase: torch.Tensor,
-             buffers: dict | None = None):
-        """One forward + backward pass; returns (loss device scalar, intensity). grad_phase is overwritten."""
+    def _forward(self, obj, phase, target, buffers):
         lam = self.field_lambdas()
         d, f, pad, m = self.d, self.f, self.pad, self.method
         bufs = buffers if buffers is not None else {}
@@ -73,16 +73,32 @@ class FourF:
             bufs["a"] = torch.empty(shape, dtype=torch.complex64, device=obj.device)
             bufs["b"] = torch.empty(shape, dtype=torch.complex64, device=obj.device)
         a, b = bufs["a"], bufs["b"]
-        lens = self.lens()
-        pupil = self.pupil(phase)
+        lens, pupil = self.lens(), self.pupil(phase)
         # F1-F4 as one fused chain: psi2 kept in a, psi4 and the grouped intensity out of the last stage
         stages = [B.Stage(f), B.Stage(f, pre=lens, keep=a), B.Stage(f, pre=pupil), B.Stage(f, pre=lens)]
         _, inten = B.top_fused_chain(obj, d, d, lam, stages, pad, m, out=b, intensity_group=self.group,
                                      input_repeat=self.repeat)
         loss, g_i = B.top_mse_loss(inten, target)
+        return lam, a, b, inten, loss, g_i, lens, pupil
+
+    def step(self, obj: torch.Tensor, phase: torch.Tensor, target: torch.Tensor, grad_phase: torch.Tensor,
+             buffers: dict | None = None):
+        """One forward + backward pass; returns (loss device scalar, intensity). grad_phase is overwritten."""
+        lam, a, b, inten, loss, g_i, lens, pupil = self._forward(obj, phase, target, buffers)
+        # B4-B3: the backward of the last two stages, from psi4 (in b) to the pupil's phase gradient
+        B.top_fused_chain_backward(b, g_i, self.d, self.d, lam, [B.Stage(self.f, pre=pupil), B.Stage(self.f, pre=lens)],
+                                   self.pad, self.method, intensity_group=self.group, saved_in=a,
+                                   want_grad_in=False, grad_phase=grad_phase)
+        return loss, inten
+
+    def step_unfused_backward(self, obj: torch.Tensor, phase: torch.Tensor, target: torch.Tensor,
+                              grad_phase: torch.Tensor, buffers: dict | None = None):
+        """``step`` with the backward as two separate calls (intensity backward, then propagation
+        backward through the pupil): the same results, for comparison."""
+        lam, a, b, inten, loss, g_i, lens, pupil = self._forward(obj, phase, target, buffers)
         _intensity_backward_into(b, g_i, b, self, lam)                                                # B4 (g3 in b)
-        B.top_propagate_backward(b, d, d, lam, f, pad, m, pre=pupil, post=lens, saved_in=a,
-                                 want_grad_in=False, grad_phase=grad_phase)                           # B3
+        B.top_propagate_backward(b, self.d, self.d, lam, self.f, self.pad, self.method, pre=pupil, post=lens,
+                                 saved_in=a, want_grad_in=False, grad_phase=grad_phase)               # B3
         return loss, inten
 
 
