@@ -315,6 +315,11 @@ def run_ours(args, rank, world):
             D.average_gradient(gphase)  # the one exchange of a step: mean pupil-phase gradient
         return loss
 
+    # with --autotune, the pass variants measured on this geometry by the library's autotuner
+    # (the defaults otherwise), then the warm-up
+    tune_rows = tune_cols = None
+    if args.autotune:
+        tune_rows, tune_cols = Bd.top_autotune(16, c["n"], c["n"], c["d"], c["d"], c["pad"], device=dev)
     for _ in range(max(3, args.warmup)):
         step(obj)
     torch.cuda.synchronize()
@@ -442,7 +447,9 @@ def run_ours(args, rank, world):
             "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "c64/f32 (FP64 phase tables)", "data": "synthetic",
             "config": workload_config(objects=objects), "roofline": roofline, "clocks": clocks, "e2e": e2e,
-            "gpu_launches": launches}
+            "gpu_launches": launches,
+            "autotune": None if tune_rows is None else {"rows_flags": tune_rows, "cols_flags": tune_cols,
+                                                        "line_length": c["n"]}}
     if rank == 0 and world == 1 and not args.no_context:
         line["context"] = context_paths(dev, c)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -460,6 +467,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-context", action="store_true", help="skip the unbatched and torch.fft context timings")
+    ap.add_argument("--autotune", action="store_true",
+                    help="run the library's autotuner on the workload's geometry before the warm-up")
     ap.add_argument("--objects", type=int, default=S.CFG4["objects"],
                     help="objects per GPU (a smaller batch for profiler captures; the workload has 16)")
     args = ap.parse_args()

@@ -394,6 +394,41 @@ top_status top_coherence_intensity(top_handle h, const top_grid* g, const void* 
 top_status top_coherence_intensity_backward(top_handle h, const top_grid* g, const float* grad_intensity,
                                             void* grad_gamma, void* stream);
 
+/* ---------------------------------------------------------------- autotuning */
+
+/* Pass variants the autotuner chooses between, per line length M = P/2 (flags 0: the defaults).
+ * Row passes of M (the x axis) read the row bits, the column pass of M (the y axis) the column
+ * bit. TOP_TUNE_CLASSIC_*: the block-cooperative row kernels instead of the pair-local ones (plans
+ * of one warp a half line at padding 2); TOP_TUNE_NO_L2_*: no L2 prefetch of the next wave's
+ * inputs; bits 8-10 (TOP_TUNE_SPAN): fields per block of the inverse row pass with a field
+ * epilogue, c -> 2^(c - 1) (0: 4). */
+#define TOP_TUNE_CLASSIC_FWD 0x1u
+#define TOP_TUNE_CLASSIC_INV 0x2u
+#define TOP_TUNE_CLASSIC_CHAIN 0x4u
+#define TOP_TUNE_NO_L2_COLS 0x8u
+#define TOP_TUNE_NO_L2_FWD 0x10u
+#define TOP_TUNE_SPAN(c) ((uint32_t)(c) << 8)
+
+/* Measure the pass variants on g's geometry (padded sizes with a plan of their own; g->batch
+ * fields of scratch, allocated and freed by the call -- 16 or more fields at 1024^2 give passes
+ * long enough to time) with CUDA events, keep for every pass kind the fastest, and record the
+ * choices in the process-wide table for Px/2 (row bits) and Py/2 (column bit). Synchronises the
+ * device. rows_flags / cols_flags (may be NULL) receive the entries written. */
+top_status top_autotune(top_handle h, const top_grid* g, uint32_t* rows_flags, uint32_t* cols_flags);
+/* The process-wide table, host-only: set, get (0 when absent), clear. Invalid flags:
+ * TOP_ERR_INVALID_ARG. */
+top_status top_autotune_set(int line_length, uint32_t flags);
+top_status top_autotune_get(int line_length, uint32_t* flags);
+top_status top_autotune_clear(void);
+/* Write the table to a text file (a header line, one "M flags" line per entry, and a line with
+ * the FNV-1a checksum of everything before it), or replace the table by a file's contents. A
+ * missing, truncated, altered or malformed file is refused with TOP_ERR_INVALID_ARG and leaves
+ * the table unchanged. The first top_create of a process loads the file named by the environment
+ * variable TOP_AUTOTUNE_CACHE, if set (a refused file leaves the defaults, and the handle is
+ * created all the same). */
+top_status top_autotune_save(const char* path);
+top_status top_autotune_load(const char* path);
+
 /* ---------------------------------------------------------------- instrumentation */
 
 /* Enable (1) or disable (0) CUDA-event timing of every kernel launched by the handle. */

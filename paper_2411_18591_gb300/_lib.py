@@ -92,6 +92,12 @@ SIGNATURES = {
     "top_propagate_coherence_backward": (C.c_int, [_P, _GRID, _P, _P, _D, _D, _MOD, _GRADS, _P]),
     "top_coherence_intensity": (C.c_int, [_P, _GRID, _P, _P, _P]),
     "top_coherence_intensity_backward": (C.c_int, [_P, _GRID, _P, _P, _P]),
+    "top_autotune": (C.c_int, [_P, _GRID, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]),
+    "top_autotune_set": (C.c_int, [C.c_int, C.c_uint32]),
+    "top_autotune_get": (C.c_int, [C.c_int, C.POINTER(C.c_uint32)]),
+    "top_autotune_clear": (C.c_int, []),
+    "top_autotune_save": (C.c_int, [C.c_char_p]),
+    "top_autotune_load": (C.c_int, [C.c_char_p]),
     "top_profile_enable": (C.c_int, [_P, C.c_int]),
     "top_profile_read": (C.c_int, [_P, C.c_int, C.POINTER(C.c_char_p), C.POINTER(C.c_double),
                                    C.POINTER(C.c_int64), C.POINTER(C.c_int)]),

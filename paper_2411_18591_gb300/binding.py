@@ -634,3 +634,37 @@ def profile_read(device=None) -> dict:
     n = C.c_int()
     check(_lib.load().top_profile_read(handle(device), cap, kinds, ms, cnt, C.byref(n)))
     return {kinds[i].decode(): (ms[i], cnt[i]) for i in range(n.value)}
+
+
+# ----------------------------------------------------------------------------- autotuning
+
+def top_autotune(batch: int, ny: int, nx: int, dy: float, dx: float, pad: float = 2.0, method="as",
+                 device=None):
+    """Measure the pass variants on this geometry (``batch`` scratch fields) and record the fastest
+    in the process-wide table; returns (row flags of Px/2, column flags of Py/2)."""
+    g = make_grid(batch, ny, nx, dy, dx, pad, method)
+    rf, cf = C.c_uint32(), C.c_uint32()
+    check(_lib.load().top_autotune(handle(device), C.byref(g), C.byref(rf), C.byref(cf)))
+    return rf.value, cf.value
+
+
+def autotune_set(line_length: int, flags: int) -> None:
+    check(_lib.load().top_autotune_set(int(line_length), int(flags)))
+
+
+def autotune_get(line_length: int) -> int:
+    v = C.c_uint32()
+    check(_lib.load().top_autotune_get(int(line_length), C.byref(v)))
+    return v.value
+
+
+def autotune_clear() -> None:
+    check(_lib.load().top_autotune_clear())
+
+
+def autotune_save(path: str) -> None:
+    check(_lib.load().top_autotune_save(str(path).encode()))
+
+
+def autotune_load(path: str) -> None:
+    check(_lib.load().top_autotune_load(str(path).encode()))

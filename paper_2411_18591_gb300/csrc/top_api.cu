@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <complex>
 #include <cstring>
 #include <map>
@@ -1285,6 +1286,8 @@ top_status run_propagation(top_handle h, const Request& q, cudaStream_t st) {
   p.Mx = geo.Px / 2;
   p.oy = geo.oy;
   p.ox = geo.ox;
+  p.tune_rows = tune_flags(geo.Px / 2);
+  p.tune_cols = tune_flags(geo.Py / 2);
   p.method = g->method;
   p.adjoint = q.adjoint;
   p.src_kind = q.src_kind;
@@ -1583,6 +1586,8 @@ top_status run_chain(top_handle h, const top_grid* g, const void* in, void* out,
   base.Mx = geo.Px / 2;
   base.oy = geo.oy;
   base.ox = geo.ox;
+  base.tune_rows = tune_flags(geo.Px / 2);
+  base.tune_cols = tune_flags(geo.Py / 2);
   base.method = g->method;
   base.src_kind = SRC_FIELD;
   base.epi_kind = EPI_FIELD;
@@ -1770,6 +1775,8 @@ top_status run_ragged(top_handle h, int count, const top_grid* grids, const void
     p.Mx = geo.Px / 2;
     p.oy = geo.oy;
     p.ox = geo.ox;
+    p.tune_rows = tune_flags(geo.Px / 2);
+    p.tune_cols = tune_flags(geo.Py / 2);
     p.method = grids[grp[0]].method;
     p.adjoint = backward ? 1 : 0;
     p.src_kind = SRC_FIELD;
@@ -1844,9 +1851,158 @@ top_status top_create(top_handle* out, int device) {
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
   if (device < 0 || device >= count) return fail(TOP_ERR_INVALID_ARG, "device %d out of range (%d devices)", device, count);
   TOP_CUDA(cudaSetDevice(device), "cudaSetDevice");
+  static std::once_flag tune_once;
+  std::call_once(tune_once, [] {
+    const char* path = std::getenv("TOP_AUTOTUNE_CACHE");
+    std::string err;
+    if (path && *path) tune_load(path, &err);  // a refused file leaves the defaults
+  });
   top_ctx* h = new top_ctx();
   h->device = device;
   *out = h;
+  return TOP_OK;
+}
+
+top_status top_autotune(top_handle h, const top_grid* g, uint32_t* rows_flags, uint32_t* cols_flags) {
+  if (!h) return fail(TOP_ERR_INVALID_ARG, "handle is NULL");
+  Geometry geo;
+  TOP_TRY(check_grid(g, &geo));
+  TOP_TRY(check_engines(geo));
+  if (!has_engines(geo)) return fail(TOP_ERR_UNSUPPORTED, "autotune needs padded sizes with a plan of their own");
+  TOP_TRY(bind(h));
+  const int64_t B = g->batch;
+  const size_t bytes = sizeof(float2) * size_t(B) * size_t(geo.ny) * size_t(geo.nx);
+  void *x = nullptr, *y = nullptr, *gi = nullptr;
+  TOP_CUDA(cudaMalloc(&x, bytes), "cudaMalloc(autotune fields)");
+  if (cudaMalloc(&y, bytes) != cudaSuccess || cudaMalloc(&gi, bytes / 2) != cudaSuccess) {
+    cudaFree(x);
+    cudaFree(y);
+    return fail(TOP_ERR_OOM, "cudaMalloc(autotune fields) failed");
+  }
+  cudaMemset(x, 0x3c, bytes);  // every float 0.0115
+  cudaMemset(gi, 0x3c, bytes / 2);
+  const int Mx = geo.Px / 2, My = geo.Py / 2;
+  const uint32_t row_bits = TOP_TUNE_CLASSIC_FWD | TOP_TUNE_CLASSIC_INV | TOP_TUNE_CLASSIC_CHAIN | TOP_TUNE_NO_L2_FWD |
+                            TOP_TUNE_SPAN(7);
+  const uint32_t col_bits = TOP_TUNE_NO_L2_COLS;
+  const uint32_t keep_x = tune_flags(Mx), keep_y = tune_flags(My);
+  const bool keep_prof = h->prof;
+  // launches the caller profiled before this call keep their totals
+  for (auto& pe : h->pending) {
+    float ms = 0.f;
+    cudaEventSynchronize(pe.second.second);
+    if (cudaEventElapsedTime(&ms, pe.second.first, pe.second.second) == cudaSuccess) {
+      h->prof_ms[pe.first] += ms;
+      h->prof_cnt[pe.first] += 1;
+    }
+    h->pool.push_back(pe.second.first);
+    h->pool.push_back(pe.second.second);
+  }
+  h->pending.clear();
+  auto apply = [&](uint32_t rows, uint32_t cols) {
+    tune_set(Mx, (tune_flags(Mx) & ~row_bits) | rows);
+    tune_set(My, (tune_flags(My) & ~col_bits) | cols);
+  };
+  top_mod lens{};
+  lens.flags = TOP_MOD_LENS;
+  lens.focal_length = 0.1;
+  const double lam = 532e-9, z = 0.01;
+  const top_stage stages[2] = {{z, nullptr, nullptr}, {z, &lens, nullptr}};
+  top_grid gg = *g;
+  gg.input_repeat = 0;
+  // one candidate: a propagation and a two-stage chain, the mean milliseconds per kind over 3 runs
+  auto measure = [&](uint32_t rows, uint32_t cols, double (&t)[KK_COUNT]) -> top_status {
+    apply(rows, cols);
+    for (int rep = 0; rep < 4; ++rep) {
+      h->prof = rep > 0;
+      Request q{};
+      q.g = &gg; q.lam = &lam; q.z = &z; q.n_lz = 1; q.src_kind = SRC_FIELD; q.in = x; q.group = 1;
+      q.epi_kind = EPI_FIELD; q.out = y;
+      TOP_TRY(run_propagation(h, q, nullptr));
+      // the backward from an intensity (the other source the forward rows see)
+      Request b{};
+      b.g = &gg; b.lam = &lam; b.z = &z; b.n_lz = 1; b.adjoint = 1; b.src_kind = SRC_INTENSITY; b.psi_src = x;
+      b.gI = static_cast<const float*>(gi); b.group = 1; b.epi_kind = EPI_FIELD; b.out = y;
+      TOP_TRY(run_propagation(h, b, nullptr));
+      TOP_TRY(run_chain(h, &gg, x, y, nullptr, 1, &lam, 1, stages, 2, nullptr));
+    }
+    h->prof = false;
+    TOP_CUDA(cudaDeviceSynchronize(), "cudaDeviceSynchronize(autotune)");
+    for (int k = 0; k < KK_COUNT; ++k) t[k] = 0.0;
+    for (auto& pe : h->pending) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, pe.second.first, pe.second.second) == cudaSuccess) t[pe.first] += ms / 3.0;
+      h->pool.push_back(pe.second.first);
+      h->pool.push_back(pe.second.second);
+    }
+    h->pending.clear();
+    return TOP_OK;
+  };
+  double A[KK_COUNT], Bc[KK_COUNT], C[KK_COUNT], D[KK_COUNT], E[KK_COUNT];
+  top_status st = measure(0, 0, A);
+  if (st == TOP_OK) st = measure(TOP_TUNE_CLASSIC_FWD | TOP_TUNE_CLASSIC_INV | TOP_TUNE_CLASSIC_CHAIN, 0, Bc);
+  if (st == TOP_OK) st = measure(TOP_TUNE_NO_L2_FWD | TOP_TUNE_SPAN(1), TOP_TUNE_NO_L2_COLS, C);
+  if (st == TOP_OK) st = measure(TOP_TUNE_SPAN(2), 0, D);
+  if (st == TOP_OK) st = measure(TOP_TUNE_SPAN(4), 0, E);
+  h->prof = keep_prof;
+  cudaFree(x);
+  cudaFree(y);
+  cudaFree(gi);
+  if (st != TOP_OK) {
+    tune_set(Mx, keep_x);
+    tune_set(My, keep_y);
+    return st;
+  }
+  // a variant replaces the default only when it is more than 2 % faster
+  auto better = [](double cand, double base) { return cand < 0.98 * base; };
+  uint32_t rows = 0, cols = 0;
+  double fwd = A[KK_ROWS_FWD];
+  if (better(Bc[KK_ROWS_FWD], fwd)) { rows |= TOP_TUNE_CLASSIC_FWD; fwd = Bc[KK_ROWS_FWD]; }
+  if (better(C[KK_ROWS_FWD], fwd)) { rows = (rows & ~TOP_TUNE_CLASSIC_FWD) | TOP_TUNE_NO_L2_FWD; }
+  double inv = A[KK_ROWS_INV];
+  uint32_t inv_bits = 0;
+  const std::pair<double, uint32_t> inv_cands[] = {{Bc[KK_ROWS_INV], TOP_TUNE_CLASSIC_INV}, {C[KK_ROWS_INV], TOP_TUNE_SPAN(1)},
+                                                   {D[KK_ROWS_INV], TOP_TUNE_SPAN(2)}, {E[KK_ROWS_INV], TOP_TUNE_SPAN(4)}};
+  for (const auto& c : inv_cands)
+    if (better(c.first, inv)) { inv = c.first; inv_bits = c.second; }
+  rows |= inv_bits;
+  if (better(Bc[KK_ROWS_CHAIN], A[KK_ROWS_CHAIN])) rows |= TOP_TUNE_CLASSIC_CHAIN;
+  if (better(C[KK_COLS], A[KK_COLS])) cols |= TOP_TUNE_NO_L2_COLS;
+  apply(rows, cols);
+  if (rows_flags) *rows_flags = tune_flags(Mx);
+  if (cols_flags) *cols_flags = tune_flags(My);
+  return TOP_OK;
+}
+
+top_status top_autotune_set(int line_length, uint32_t flags) {
+  if (line_length < 1 || line_length > (1 << 20)) return fail(TOP_ERR_INVALID_ARG, "line length %d out of range", line_length);
+  if (!tune_flags_valid(flags)) return fail(TOP_ERR_INVALID_ARG, "unknown autotune flags 0x%x", flags);
+  tune_set(line_length, flags);
+  return TOP_OK;
+}
+
+top_status top_autotune_get(int line_length, uint32_t* flags) {
+  if (!flags) return fail(TOP_ERR_INVALID_ARG, "flags is NULL");
+  *flags = tune_flags(line_length);
+  return TOP_OK;
+}
+
+top_status top_autotune_clear(void) {
+  tune_clear();
+  return TOP_OK;
+}
+
+top_status top_autotune_save(const char* path) {
+  if (!path) return fail(TOP_ERR_INVALID_ARG, "path is NULL");
+  std::string err;
+  if (!tune_save(path, &err)) return fail(TOP_ERR_INVALID_ARG, "autotune cache %s: %s", path, err.c_str());
+  return TOP_OK;
+}
+
+top_status top_autotune_load(const char* path) {
+  if (!path) return fail(TOP_ERR_INVALID_ARG, "path is NULL");
+  std::string err;
+  if (!tune_load(path, &err)) return fail(TOP_ERR_INVALID_ARG, "autotune cache %s: %s", path, err.c_str());
   return TOP_OK;
 }
 
@@ -2596,6 +2752,8 @@ top_status propagate_noalloc(const top_grid* g, const void* in, void* out, const
   p.Mx = geo.Px / 2;
   p.oy = geo.oy;
   p.ox = geo.ox;
+  p.tune_rows = tune_flags(geo.Px / 2);
+  p.tune_cols = tune_flags(geo.Py / 2);
   p.method = g->method;
   p.adjoint = 0;
   p.src_kind = SRC_FIELD;

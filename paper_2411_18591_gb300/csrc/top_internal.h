@@ -8,6 +8,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "../../include/top.h"
 
 namespace top {
@@ -68,6 +70,8 @@ struct PassParams {
   int epi_kind;
   int fp64_r;      // reserved
   int l2_ahead;    // blocks ahead whose input a block prefetches into L2 (0: none)
+  uint32_t tune_rows;  // TOP_TUNE_* choices for the row passes (of Mx) and the column pass (of My)
+  uint32_t tune_cols;
 
   // buffers (element strides per field)
   const float2* in;   long long in_stride;
@@ -165,6 +169,19 @@ struct CztParams {
   const float2* wsplit;  // L = 8192: exp(-2 pi i p / L), p < L/2
   const float2* const* h;  // CZT_FILTER: per field, rows [line][P] of H / (Py Px) in natural order
 };
+
+// The autotune table (top_tune.cu): TOP_TUNE_* flags per line length M (0: the defaults).
+uint32_t tune_flags(int M);
+bool tune_flags_valid(uint32_t flags);
+void tune_set(int M, uint32_t flags);
+void tune_clear();
+bool tune_save(const char* path, std::string* err);
+bool tune_load(const char* path, std::string* err);
+// Fields per block of the pair-local inverse pass with a field epilogue under tuning flags.
+inline int tune_span(uint32_t flags) {
+  const uint32_t c = (flags >> 8) & 7u;
+  return c == 0 ? 4 : 1 << (c - 1);
+}
 
 // Largest dynamic shared memory of a fused chain block (R2 of one propagation + R1 of the next).
 constexpr size_t kChainSmemMax = 227 * 1024;

@@ -1366,7 +1366,7 @@ cudaError_t launch_rows_fwd_pair_k(const PassParams& p, cudaStream_t s) {
   if (attr != cudaSuccess) return attr;
   static const int resident = resident_blocks(k_rows_fwd_pair<EX, MF>, PR::THREADS, PR::SMEM);
   PassParams q = p;
-  q.l2_ahead = TOP_L2_AHEAD ? resident : 0;
+  q.l2_ahead = TOP_L2_AHEAD && !(p.tune_rows & TOP_TUNE_NO_L2_FWD) ? resident : 0;
   dim3 grid((p.ny + PR::ROWS - 1) / PR::ROWS, p.nfields);
   TOP_LAUNCH((k_rows_fwd_pair<EX, MF>), grid, PR::THREADS, PR::SMEM, s, q);
   return cudaGetLastError();
@@ -1386,7 +1386,7 @@ cudaError_t launch_rows_inv_pair_k(const PassParams& p, cudaStream_t s) {
   if (attr != cudaSuccess) return attr;
   PassParams q = p;
   // a field epilogue has no group: a block runs its rows of a few consecutive fields
-  if (KIND == EPI_FIELD) q.group = p.nfields < 4 ? p.nfields : 4;
+  if (KIND == EPI_FIELD) q.group = p.nfields < tune_span(p.tune_rows) ? p.nfields : tune_span(p.tune_rows);
   const size_t bytes = PR::SMEM + sizeof(float) * 2 * size_t((pair_epi_floats<KIND>(q) + 3) & ~3);
   dim3 grid((q.ny + PR::ROWS - 1) / PR::ROWS, (q.nfields + q.group - 1) / q.group);
   TOP_LAUNCH((k_rows_inv_pair<EX, KIND, MF>), grid, PR::THREADS, bytes, s, q);
@@ -1452,7 +1452,7 @@ cudaError_t launch_cols_t(const PassParams& p, cudaStream_t s) {
   const size_t bytes = SH::template smem<X2>(p.ny);
   static const int resident = resident_blocks(k_cols<EY, X2>, SH::THREADS, bytes);
   PassParams q = p;
-  q.l2_ahead = TOP_L2_AHEAD ? resident : 0;
+  q.l2_ahead = TOP_L2_AHEAD && !(p.tune_cols & TOP_TUNE_NO_L2_COLS) ? resident : 0;
   dim3 grid((p.Px + SH::COLS - 1) / SH::COLS, p.nfields);
   TOP_LAUNCH((k_cols<EY, X2>), grid, SH::THREADS, bytes, s, q);
   return cudaGetLastError();
@@ -1488,7 +1488,8 @@ inline bool exact2(int n, int M, int o) { return n == M && o == M / 2; }
 template <class EX>
 cudaError_t launch_rows_fwd(const PassParams& p, cudaStream_t s) {
   if constexpr (pair_rows<EX>()) {
-    if (exact2(p.nx, p.Mx, p.ox) && pair_fwd_fits<EX>(p)) return launch_rows_fwd_pair<EX>(p, s);
+    if (exact2(p.nx, p.Mx, p.ox) && pair_fwd_fits<EX>(p) && !(p.tune_rows & TOP_TUNE_CLASSIC_FWD))
+      return launch_rows_fwd_pair<EX>(p, s);
   }
   return exact2(p.nx, p.Mx, p.ox) ? launch_rows_fwd_t<EX, true>(p, s) : launch_rows_fwd_t<EX, false>(p, s);
 }
@@ -1501,7 +1502,8 @@ cudaError_t launch_cols(const PassParams& p, cudaStream_t s) {
 template <class EX>
 cudaError_t launch_rows_chain(const PassParams& pa, const PassParams& pb, cudaStream_t s) {
   if constexpr (pair_rows<EX>()) {
-    if (exact2(pa.nx, pa.Mx, pa.ox) && pa.nx % 4 == 0) return launch_rows_chain_pair<EX>(pa, pb, s);
+    if (exact2(pa.nx, pa.Mx, pa.ox) && pa.nx % 4 == 0 && !(pa.tune_rows & TOP_TUNE_CLASSIC_CHAIN))
+      return launch_rows_chain_pair<EX>(pa, pb, s);
   }
   return exact2(pa.nx, pa.Mx, pa.ox) ? launch_rows_chain_t<EX, true>(pa, pb, s) : launch_rows_chain_t<EX, false>(pa, pb, s);
 }
@@ -1509,7 +1511,8 @@ cudaError_t launch_rows_chain(const PassParams& pa, const PassParams& pb, cudaSt
 template <class EX>
 cudaError_t launch_rows_inv(const PassParams& p, cudaStream_t s) {
   if constexpr (pair_rows<EX>()) {
-    if (exact2(p.nx, p.Mx, p.ox) && pair_epilogue(p)) return launch_rows_inv_pair<EX>(p, s);
+    if (exact2(p.nx, p.Mx, p.ox) && pair_epilogue(p) && !(p.tune_rows & TOP_TUNE_CLASSIC_INV))
+      return launch_rows_inv_pair<EX>(p, s);
   }
   return exact2(p.nx, p.Mx, p.ox) ? launch_rows_inv_t<EX, true>(p, s) : launch_rows_inv_t<EX, false>(p, s);
 }

@@ -153,3 +153,41 @@ def test_jones_constructors_reject_bad_arguments(lib):
     assert _jones(lib, "top_jones_circular_polarizer", 0)[0] == 1
     assert _jones(lib, "top_jones_linear_polarizer", C.c_double(float("nan")))[0] == 1
     assert cdll.top_jones_waveplate(C.c_double(1.0), C.c_double(0.0), None) == 1
+
+
+def test_autotune_table_round_trip_and_corruption(lib, tmp_path):
+    """The autotune cache file: what is saved loads back; an altered, truncated or malformed file
+    is refused with TOP_ERR_INVALID_ARG and leaves the table as it was (host-only calls)."""
+    cdll = lib.load()
+    assert cdll.top_autotune_clear() == 0
+    entries = {1024: 0x1 | 0x8, 512: 0x2 | (3 << 8), 250: 0}
+    for m, f in entries.items():
+        assert cdll.top_autotune_set(m, f) == 0
+    assert cdll.top_autotune_set(1024, 0x8000) == 1  # unknown flag bit
+    assert cdll.top_autotune_set(0, 0) == 1
+    path = tmp_path / "tune.txt"
+    assert cdll.top_autotune_save(str(path).encode()) == 0
+    assert cdll.top_autotune_clear() == 0
+
+    def get(m):
+        v = C.c_uint32()
+        assert cdll.top_autotune_get(m, C.byref(v)) == 0
+        return v.value
+
+    assert get(1024) == 0
+    assert cdll.top_autotune_load(str(path).encode()) == 0
+    assert {m: get(m) for m in entries} == entries
+    text = path.read_text()
+    assert text.startswith("top-autotune 1\n") and "checksum" in text
+    # an altered entry, a truncated file, a bad header and a missing file are all refused
+    cdll.top_autotune_set(2048, 0x4)
+    bad = {"altered": text.replace("1024 9", "1024 1"), "truncated": text[: len(text) // 2],
+           "header": text.replace("top-autotune 1", "top-autotune 9"), "empty": ""}
+    for name, body in bad.items():
+        p = tmp_path / f"{name}.txt"
+        p.write_text(body)
+        assert cdll.top_autotune_load(str(p).encode()) == 1, name
+        assert b"autotune cache" in cdll.top_last_error()
+        assert get(2048) == 0x4 and get(1024) == entries[1024]  # unchanged
+    assert cdll.top_autotune_load(str(tmp_path / "missing.txt").encode()) == 1
+    assert cdll.top_autotune_clear() == 0
