@@ -143,35 +143,59 @@ def oracle_sample_step(obj_field, lam, fourf_cfg, phase, target):
     return time.perf_counter() - t0, loss, g_phi
 
 
+def _oracle_field(i: int):
+    """The oracle's 4f step on field i of the workload's sample (object i, Ex, 450 nm); returns
+    (seconds, loss, pupil-phase gradient). Runs in a worker process."""
+    c = S.CFG4
+    obj = S.cfg4_objects(1, 1, c["n"], first=i)[0, 0].astype(np.complex128)
+    phase = S.cfg4_pupil_phase(c["n"])
+    target = S.cfg4_target(1, c["n"], first=i)[0]
+    lam = float(S.cfg4_wavelengths(c["wavelengths"])[0])
+    cfg = dict(d=c["d"], f=c["f"], lens_radius=c["lens_radius"], pupil_radius=c["pupil_radius"], pad=c["pad"])
+    return oracle_sample_step(obj, lam, cfg, phase, target)
+
+
 def cpu_baseline(steps: int, warmup: int, budget_s: float = 25.0, want_sample: bool = False):
-    """The oracle timed on one field of the workload. With want_sample, also returns that field's
-    inputs and the oracle's results on it (the 4f loss and pupil-phase gradient, and one AS
-    propagation and its adjoint of the object field), for the parity of the GPU line."""
+    """The oracle timed on the host cores: one worker process per core (spawned, so no GPU state is
+    inherited), each running the full 4f chain of one field of the workload; rounds of one field a
+    worker until the budget is spent. With want_sample, also returns the first field's inputs and
+    the oracle's results on it (the 4f loss and pupil-phase gradient, and one AS propagation and
+    its adjoint of the object field), for the parity of the GPU line."""
+    import multiprocessing as mp
     n = S.CFG4["n"]
     c = S.CFG4
+    workers = max(1, min(16, os.cpu_count() or 1))
+    rounds, fields, t_total = 0, 0, 0.0
+    loss = g_phi = None
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(workers) as pool:
+        t_start = time.perf_counter()
+        while True:
+            t0 = time.perf_counter()
+            res = pool.map(_oracle_field, range(rounds * workers, (rounds + 1) * workers))
+            dt = time.perf_counter() - t0
+            if rounds == 0:
+                _, loss, g_phi = res[0]
+            rounds += 1
+            if rounds > warmup:
+                fields += workers
+                t_total += dt
+            if rounds >= warmup + max(1, steps) or time.perf_counter() - t_start > budget_s:
+                if fields == 0:  # the budget ran out inside the warm-up: time the last round
+                    fields, t_total = workers, dt
+                break
+    units = (4 + 2) / 2.0
+    cb = {"value": units * fields / t_total, "unit": UNIT, "cores": workers, "kind": "oracle",
+          "sample": f"{fields} of the workload's fields (object i, Ex, 450 nm), one per worker process at a time: "
+                    "the full 4f chain in float64 numpy (4 forward + 2 backward propagations, 2048^2 FFTs) and "
+                    f"the loss on that field's intensity; {t_total:.2f} s wall for them on {workers} cores"}
+    if not want_sample:
+        return cb
+    import oracle as O
     obj = S.cfg4_objects(1, 1, n)[0, 0].astype(np.complex128)
     phase = S.cfg4_pupil_phase(n)
     target = S.cfg4_target(1, n)[0]
     lam = float(S.cfg4_wavelengths(c["wavelengths"])[0])
-    cfg = dict(d=c["d"], f=c["f"], lens_radius=c["lens_radius"], pupil_radius=c["pupil_radius"], pad=c["pad"])
-    times = []
-    t_start = time.perf_counter()
-    loss = g_phi = None
-    for i in range(warmup + steps):
-        dt, loss, g_phi = oracle_sample_step(obj, lam, cfg, phase, target)
-        if i >= warmup:
-            times.append(dt)
-        if time.perf_counter() - t_start > budget_s and len(times) >= 1:
-            break
-    per = statistics.median(times)
-    units = (4 + 2) / 2.0
-    cb = {"value": units / per, "unit": UNIT, "cores": 1, "kind": "oracle",
-          "sample": "1 of 384 fields (object 0, Ex, 450 nm): the full 4f chain in float64 numpy "
-                    "(4 forward + 2 backward propagations, 2048^2 FFTs), loss on that field's intensity; "
-                    f"{len(times)} timed of {warmup + len(times)} runs, median {per:.2f} s per field"}
-    if not want_sample:
-        return cb
-    import oracle as O
     fwd = O.propagate(obj[None], c["d"], c["d"], lam, c["f"], c["pad"])[0]
     bwd = O.propagate_adjoint(obj[None], c["d"], c["d"], lam, c["f"], c["pad"])[0]
     sample = dict(obj=obj, lam=lam, phase=phase, target=target, loss=float(loss), g_phi=g_phi, fwd=fwd, bwd=bwd)
@@ -208,7 +232,7 @@ def gpu_parity(dev, sample):
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    cb = cpu_baseline(args.steps, args.warmup, budget_s=150.0)
+    cb = cpu_baseline(args.steps, args.warmup, budget_s=150.0)  # rounds of one field per core
     line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * 3.0 / cb["value"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -278,6 +302,110 @@ def context_paths(dev, c):
             "fwd_ms_per_field_torch_fft": ref, "unbatched_over_batched": unbatched / batched,
             "torch_fft_over_batched": ref / batched,
             "note": "one 1024^2 AS forward propagation at 2x padding, 16 fields, event-timed; context only"}
+
+
+def _event_ms(fn, reps, warm=2):
+    """Mean milliseconds of fn() over reps runs on the current stream (CUDA events, after warm-up)."""
+    import torch
+    stream = torch.cuda.current_stream()
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def context_workloads(dev, peak_gbs, reps=5):
+    """The other workloads' steps on their own, event-timed after warm-up, with the HBM fraction of
+    their model bytes (context for the headline, not part of it):
+    * large fields: one AS propagation forward + backward of a 2048^2 and of a 4096^2 field at 2x
+      padding (the 4096^2 one is the large-field workload, 8192^2 transforms); model 160 n^2 B;
+    * coherence: the 64^4 Gaussian Schell-model workload, P (M M* Gamma) P^H through the trainable
+      mask, the intensity, its backward and the mask-phase gradient; compulsory bytes 4 x 134 MB
+      (Gamma read and written once per direction);
+    * Bluestein sizes: one AS forward propagation of 1021^2 fields at 2x padding (2042-point lines,
+      4096-point chirp transforms), 4 fields a call; model 80 n^2 B per field;
+    * the diffractive network: 64 fields of 512^2 through 5 phase masks, MSE and every mask's gradient
+      (5 fwd + 5 bwd propagations a field); model 160 n^2 B per fwd+bwd pair;
+    * the ragged batch: 200 fields of six sizes (250-1000^2) forward and backward in one call each;
+      model 160 n^2 B per field."""
+    import torch
+    from paper_2411_18591_gb300 import binding as Bd
+    out = {}
+    g = torch.Generator(device="cpu").manual_seed(11)
+    for n in (2048, 4096):
+        x = torch.complex(torch.randn(1, n, n, generator=g), torch.randn(1, n, n, generator=g)).to(dev)
+        ms = _event_ms(lambda: (Bd.top_propagate(x, 5e-6, 5e-6, 633e-9, 0.2, 2.0),
+                                Bd.top_propagate_backward(x, 5e-6, 5e-6, 633e-9, 0.2, 2.0)), reps)
+        gbs = 160.0 * n * n / (ms * 1e-3) / 1e9
+        out[f"fwd_bwd_{n}"] = {"ms": ms, "model_bytes": 160 * n * n, "achieved_gbs": gbs, "frac": gbs / peak_gbs}
+        del x
+    c = S.cfg5a_coherence()
+    gam = torch.from_numpy(c["gamma"]).to(dev)
+    ph = torch.from_numpy(c["phase"]).to(dev)
+    tgt = torch.from_numpy(c["target"]).to(dev)
+    mask = Bd.Modulation(phase=ph)
+    gp = torch.zeros_like(ph)
+
+    def coherence_step():
+        gz = Bd.top_propagate_coherence(gam, c["d"], c["d"], c["lam"], c["z"], c["pad"], mask=mask)
+        inten = Bd.top_coherence_intensity(gz)
+        _, gi = Bd.top_mse_loss(inten[None], tgt[None])
+        G = Bd.top_coherence_intensity_backward(gi[0], gz)
+        Bd.top_propagate_coherence_backward(G, c["d"], c["d"], c["lam"], c["z"], c["pad"], mask=mask, saved_in=gam,
+                                            want_grad_in=False, grad_phase=gp)
+
+    ms = _event_ms(coherence_step, reps)
+    comp = 4 * gam.numel() * 8
+    out["coherence_64_4"] = {"ms": ms, "compulsory_bytes": comp, "achieved_gbs": comp / (ms * 1e-3) / 1e9,
+                             "frac": comp / (ms * 1e-3) / 1e9 / peak_gbs}
+    n = 1021
+    x = torch.complex(torch.randn(4, n, n, generator=g), torch.randn(4, n, n, generator=g)).to(dev)
+    ms = _event_ms(lambda: Bd.top_propagate(x, 5e-6, 5e-6, 633e-9, 0.05, 2.0), reps) / 4
+    gbs = 80.0 * n * n / (ms * 1e-3) / 1e9
+    out["bluestein_1021_fwd_per_field"] = {"ms": ms, "model_bytes": 80 * n * n, "achieved_gbs": gbs,
+                                           "frac": gbs / peak_gbs}
+    del x
+    # the diffractive network: 64 binary 512^2 inputs through 5 phase masks, MSE, every mask's gradient
+    from paper_2411_18591_gb300.stack import MaskStack
+    c2 = S.cfg2_diffractive()
+    x2 = torch.from_numpy(c2["field"]).to(dev)
+    ph2 = torch.from_numpy(c2["phases"]).to(dev)
+    t2 = torch.from_numpy(c2["target"]).to(dev)
+    K = ph2.shape[0]
+    stack = MaskStack(c2["d"], c2["lam"], [c2["gap"]] * (K - 1) + [c2["detector"]], c2["pad"])
+
+    def diffractive_step():
+        inten, st = stack.forward(x2, ph2)
+        _, gi = Bd.top_mse_loss(inten, t2)
+        stack.backward(st, ph2, gi)
+
+    ms = _event_ms(diffractive_step, reps)
+    units = x2.shape[0] * K  # fwd+bwd propagation pairs per step
+    n = x2.shape[-1]
+    gbs = units * 160.0 * n * n / (ms * 1e-3) / 1e9
+    out["diffractive_5x512"] = {"ms": ms, "fwd_bwd_per_s": units / (ms * 1e-3), "model_bytes": units * 160 * n * n,
+                                "achieved_gbs": gbs, "frac": gbs / peak_gbs}
+    del x2, t2
+    # the ragged batch: 200 fields of six sizes with their own spacings, wavelengths and distances,
+    # forward and backward in one call each (random fields of those shapes)
+    descs = S.cfg3_ragged()
+    xs = [torch.complex(torch.randn(f["n"], f["n"], generator=g), torch.randn(f["n"], f["n"], generator=g)).to(dev)
+          for f in descs]
+    outs = [torch.empty_like(v) for v in xs]
+    sp, lm, zz = [f["d"] for f in descs], [f["lam"] for f in descs], [f["z"] for f in descs]
+    ms = _event_ms(lambda: (Bd.top_propagate_ragged(xs, sp, lm, zz, 2.0, out=outs),
+                            Bd.top_propagate_ragged(outs, sp, lm, zz, 2.0, backward=True, out=xs)), reps)
+    model = sum(160 * f["n"] * f["n"] for f in descs)
+    out["ragged_200"] = {"ms": ms, "fwd_bwd_per_s": len(descs) / (ms * 1e-3), "model_bytes": model,
+                         "achieved_gbs": model / (ms * 1e-3) / 1e9, "frac": model / (ms * 1e-3) / 1e9 / peak_gbs}
+    out["note"] = "event-timed after warm-up on the launching stream; fractions of the measured HBM copy bandwidth"
+    return out
 
 
 def run_ours(args, rank, world):
@@ -452,8 +580,9 @@ def run_ours(args, rank, world):
                                                         "line_length": c["n"]}}
     if rank == 0 and world == 1 and not args.no_context:
         line["context"] = context_paths(dev, c)
+        line["context"]["workloads"] = context_workloads(dev, peaks["hbm_gbs"])
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"], sample = cpu_baseline(2, 0, want_sample=True)
+        line["cpu_baseline"], sample = cpu_baseline(2, 1, want_sample=True)
         line["parity"] = gpu_parity(dev, sample)
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -467,6 +596,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-context", action="store_true", help="skip the unbatched and torch.fft context timings")
+    ap.add_argument("--context-only", action="store_true",
+                    help="time only the other workloads (large fields, coherence, Bluestein sizes), --steps runs each")
     ap.add_argument("--autotune", action="store_true",
                     help="run the library's autotuner on the workload's geometry before the warm-up")
     ap.add_argument("--objects", type=int, default=S.CFG4["objects"],
@@ -476,6 +607,14 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)  # host-only; ranks other than 0 exit without work
+        return
+    if args.context_only:
+        # the context workloads alone (for profiler captures of their kernels)
+        import torch
+        import __graft_entry__ as ge
+        ge.build()
+        peaks, _ = measured_peaks()
+        print(json.dumps(context_workloads(torch.device("cuda", 0), peaks["hbm_gbs"], reps=args.steps)), flush=True)
         return
     if world > 1:
         import torch

@@ -89,6 +89,8 @@ struct top_ctx {
   size_t coh_bytes = 0;
   void* chain = nullptr;  // the intermediate fields of a chain at a padded size without a plan
   size_t chain_bytes = 0;
+  void* cohg = nullptr;  // the coherence backward's G' when the caller wants no grad_in
+  size_t cohg_bytes = 0;
   std::vector<void*> allocs;  // cached tables, freed with the handle
   std::map<int, float2*> eng_tw;
   std::map<int, float2*> split_tw;
@@ -2013,6 +2015,7 @@ top_status top_destroy(top_handle h) {
   for (void* p : h->allocs) cudaFree(p);
   if (h->ws) cudaFree(h->ws);
   if (h->coh) cudaFree(h->coh);
+  if (h->cohg) cudaFree(h->cohg);
   if (h->chain) cudaFree(h->chain);
   for (auto& pe : h->pending) {
     cudaEventDestroy(pe.second.first);
@@ -2541,19 +2544,19 @@ top_status top_propagate_coherence_backward(top_handle h, const top_grid* g, con
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int n = g->ny * g->nx;
   const size_t tensor = sizeof(float2) * size_t(g->batch) * n * n;
-  // G' = P^H G P lands in grad_in, or in a second scratch tensor placed in the workspace tail
+  // G' = P^H G P lands in grad_in, or (when the caller wants no grad_in) in a scratch tensor the
+  // handle keeps: the two-sided propagation uses the workspace and the transpose scratch already
   void* dst = grad_in;
-  // the two-sided propagation uses the workspace and the transpose scratch, so an internal G' needs its own block
-  void* own = nullptr;
   if (!dst) {
-    TOP_CUDA(cudaMalloc(&own, tensor), "cudaMalloc(coherence gradient)");
-    dst = own;
+    TOP_TRY(grow_scratch(&h->cohg, &h->cohg_bytes, tensor, "cudaMalloc(coherence gradient)"));
+    dst = h->cohg;
   }
   top_status s = coh_two_sided(h, g, grad_out, dst, lambda, z, 0, st);
   if (s == TOP_OK && pg) {
     PassParams mp;
     s = coh_mask_params(h, g, mask, lambda[0], &mp);
-    if (s == TOP_OK && h->ws_bytes < size_t(n) * sizeof(float2) + 256) s = ensure_workspace(h, size_t(n) * sizeof(float2) + 256);
+    const size_t work = coh_mask_grads_work(int(n)) + 256;
+    if (s == TOP_OK && h->ws_bytes < work) s = ensure_workspace(h, work);
     if (s == TOP_OK)
       s = timed(h, KK_AUX, st, "coherence mask gradients", [&] {
         return launch_coh_mask_grads(static_cast<const float2*>(dst), static_cast<const float2*>(grads->saved_in), mp,
@@ -2568,10 +2571,6 @@ top_status top_propagate_coherence_backward(top_handle h, const top_grid* g, con
       s = timed(h, KK_AUX, st, "coherence modulation backward", [&] {
         return launch_coh_modulate(static_cast<const float2*>(dst), static_cast<float2*>(dst), mp, g->batch, 1, st);
       });
-  }
-  if (own) {
-    cudaStreamSynchronize(st);
-    cudaFree(own);
   }
   return s;
 }

@@ -731,16 +731,21 @@ __global__ void __launch_bounds__(256) k_coh_diag_backward(const float* gI, floa
   if (r < n) grad[(b * n + r) * n + r] = make_float2(gI[b * n + r], 0.f);
 }
 
+// M(s) for every s of the grid (the mask of Eq. 12, evaluated once for the gradient sums)
+__global__ void __launch_bounds__(256) k_coh_mask_values(const __grid_constant__ PassParams p, int n, float2* mv) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < n) mv[s] = coh_mask(p, s);
+}
+
 // row term: one block per r, fixed tree order over s; batch summed in order
-__global__ void __launch_bounds__(256) k_coh_grad_rows(const float2* G, const float2* Gm, const __grid_constant__ PassParams p,
-                                                       int n, long long batch, float2* gm) {
+__global__ void __launch_bounds__(256) k_coh_grad_rows(const float2* G, const float2* Gm, const float2* mv, int n,
+                                                       long long batch, float2* gm) {
   __shared__ float2 red[256];
   const int r = blockIdx.x;
   float2 acc = make_float2(0.f, 0.f);
   for (long long b = 0; b < batch; ++b) {
     const long long row = (b * n + r) * n;
-    for (int s = threadIdx.x; s < n; s += blockDim.x)
-      acc = c_add(acc, c_mul(c_mulc(G[row + s], Gm[row + s]), coh_mask(p, s)));
+    for (int s = threadIdx.x; s < n; s += blockDim.x) acc = c_add(acc, c_mul(c_mulc(G[row + s], Gm[row + s]), mv[s]));
   }
   red[threadIdx.x] = acc;
   __syncthreads();
@@ -751,24 +756,49 @@ __global__ void __launch_bounds__(256) k_coh_grad_rows(const float2* G, const fl
   if (threadIdx.x == 0) gm[r] = red[0];
 }
 
-// column term: one thread per r, loop over s in order; then the parameter gradients
-__global__ void __launch_bounds__(256) k_coh_grad_cols(const float2* G, const float2* Gm, const __grid_constant__ PassParams p,
-                                                       int n, long long batch, const float2* gm_rows, float* gphase,
-                                                       float* gamp, float2* gmask) {
+// column term, partial sums: block (32 r, kCohWarps warps) of slice `split` of the s range; warp w
+// sums its part of the slice in order (over the batch, then s), and the warps' sums are added in
+// warp order: part[split][r]
+constexpr int kCohSplit = 16;
+constexpr int kCohWarps = 8;
+__global__ void __launch_bounds__(32 * kCohWarps) k_coh_grad_cols_part(const float2* G, const float2* Gm, const float2* mv,
+                                                                       int n, long long batch, float2* part) {
+  __shared__ float2 red[kCohWarps][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int r = blockIdx.x * 32 + lane;
+  const int per = (n + kCohSplit * kCohWarps - 1) / (kCohSplit * kCohWarps);
+  const int s0 = (blockIdx.y * kCohWarps + w) * per, s1 = min(n, s0 + per);
+  float2 acc = make_float2(0.f, 0.f);
+  if (r < n) {
+    for (long long b = 0; b < batch; ++b)
+      for (int s = s0; s < s1; ++s) {
+        const long long i = (b * n + s) * n + r;
+        acc = c_add(acc, c_mul(c_mulc(Gm[i], G[i]), mv[s]));
+      }
+  }
+  red[w][lane] = acc;
+  __syncthreads();
+  if (w == 0 && r < n) {
+    float2 t = red[0][lane];
+    for (int k = 1; k < kCohWarps; ++k) t = c_add(t, red[k][lane]);
+    part[(long long)blockIdx.y * n + r] = t;
+  }
+}
+
+// g_M(r) = row term + the column slices in order; then the parameter gradients
+__global__ void __launch_bounds__(256) k_coh_grad_finish(const __grid_constant__ PassParams p, int n,
+                                                         const float2* gm_rows, const float2* part, float* gphase,
+                                                         float* gamp, float2* gmask) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n) return;
   float2 acc = gm_rows[r];
-  for (long long b = 0; b < batch; ++b)
-    for (int s = 0; s < n; ++s) {
-      const long long i = (b * n + s) * n + r;
-      acc = c_add(acc, c_mul(c_mulc(Gm[i], G[i]), coh_mask(p, s)));
-    }
+  for (int k = 0; k < kCohSplit; ++k) acc = c_add(acc, part[(long long)k * n + r]);
   // acc = g_M(r) for the complex mask value M(r)
   const int y = r / p.nx, x = r - (r / p.nx) * p.nx;
   const FieldSet& fs = p.sets[0];
   const ModDev& m = p.msrc;
-  const float2 mv = mod_value(m, m.flags, 0, fs.src_lx, fs.src_ly, 0, y, x, p.nx);
-  if (gphase) gphase[r] = fmaf(mv.x, acc.y, -mv.y * acc.x);  // Im(conj(M) g_M)
+  const float2 mval = mod_value(m, m.flags, 0, fs.src_lx, fs.src_ly, 0, y, x, p.nx);
+  if (gphase) gphase[r] = fmaf(mval.x, acc.y, -mval.y * acc.x);  // Im(conj(M) g_M)
   if (gamp) {
     const float2 ra = mod_value(m, m.flags & ~TOP_MOD_AMPLITUDE, 0, fs.src_lx, fs.src_ly, 0, y, x, p.nx);
     gamp[r] = fmaf(acc.x, ra.x, acc.y * ra.y);  // Re(conj(g_M) R_A)
@@ -778,6 +808,8 @@ __global__ void __launch_bounds__(256) k_coh_grad_cols(const float2* G, const fl
     gmask[r] = c_mulc(acc, rc);  // g_M conj(R_C)
   }
 }
+
+size_t coh_mask_grads_work(int n) { return sizeof(float2) * size_t(n) * (2 + kCohSplit); }
 
 cudaError_t launch_coh_modulate(const float2* in, float2* out, const PassParams& p, long long batch, int conj_mask,
                                 cudaStream_t s) {
@@ -811,10 +843,19 @@ cudaError_t launch_coh_mask_grads(const float2* G, const float2* gamma_in, const
                                   float2* gm_work, float* grad_phase, float* grad_amp, float2* grad_mask,
                                   cudaStream_t s) {
   const int n = p.ny * p.nx;
-  TOP_LAUNCH(k_coh_grad_rows, n, 256, 0, s, G, gamma_in, p, n, batch, gm_work);
+  float2* rows = gm_work;
+  float2* mv = gm_work + n;
+  float2* part = gm_work + 2 * size_t(n);
+  TOP_LAUNCH(k_coh_mask_values, (n + 255) / 256, 256, 0, s, p, n, mv);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  TOP_LAUNCH(k_coh_grad_cols, (n + 255) / 256, 256, 0, s, G, gamma_in, p, n, batch, gm_work, grad_phase, grad_amp, grad_mask);
+  TOP_LAUNCH(k_coh_grad_rows, n, 256, 0, s, G, gamma_in, mv, n, batch, rows);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  TOP_LAUNCH(k_coh_grad_cols_part, dim3((n + 31) / 32, kCohSplit), 32 * kCohWarps, 0, s, G, gamma_in, mv, n, batch, part);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  TOP_LAUNCH(k_coh_grad_finish, (n + 255) / 256, 256, 0, s, p, n, rows, part, grad_phase, grad_amp, grad_mask);
   return cudaGetLastError();
 }
 

@@ -90,7 +90,10 @@ cudaError_t launch_transpose(const float2* in, float2* out, long long batch, int
 cudaError_t launch_coh_diag(const float2* gamma, float* inten, long long batch, int n, cudaStream_t s);
 cudaError_t launch_coh_diag_backward(const float* gI, float2* grad, long long batch, int n, cudaStream_t s);
 // g_M(r) = sum_s G(r,s) conj(Gm(r,s)) M(s) + sum_s conj(G(s,r)) Gm(s,r) M(s), summed over the batch,
-// then turned into phase / amplitude / complex-mask gradients.
+// then turned into phase / amplitude / complex-mask gradients; gm_work holds
+// coh_mask_grads_work(ny nx) bytes (the row terms, the mask values and the column slices; the
+// column sum runs in slices over the grid, each slice in a fixed order, the slices in order).
+size_t coh_mask_grads_work(int n);
 cudaError_t launch_coh_mask_grads(const float2* G, const float2* gamma_in, const PassParams& p, long long batch,
                                   float2* gm_work, float* grad_phase, float* grad_amp, float2* grad_mask,
                                   cudaStream_t s);

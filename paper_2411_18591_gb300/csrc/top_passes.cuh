@@ -1326,6 +1326,10 @@ inline int resident_blocks(K kernel, int threads, size_t smem) {
 #ifndef TOP_L2_AHEAD
 #define TOP_L2_AHEAD 1
 #endif
+// How far ahead the column pass prefetches, in hundredths of a wave of resident blocks.
+#ifndef TOP_L2_WAVES
+#define TOP_L2_WAVES 100
+#endif
 
 // Whether the pair-local row passes take the rows of plan EX at padding exactly 2.
 #ifndef TOP_PAIR_ROWS
@@ -1452,7 +1456,7 @@ cudaError_t launch_cols_t(const PassParams& p, cudaStream_t s) {
   const size_t bytes = SH::template smem<X2>(p.ny);
   static const int resident = resident_blocks(k_cols<EY, X2>, SH::THREADS, bytes);
   PassParams q = p;
-  q.l2_ahead = TOP_L2_AHEAD && !(p.tune_cols & TOP_TUNE_NO_L2_COLS) ? resident : 0;
+  q.l2_ahead = TOP_L2_AHEAD && !(p.tune_cols & TOP_TUNE_NO_L2_COLS) ? resident * TOP_L2_WAVES / 100 : 0;
   dim3 grid((p.Px + SH::COLS - 1) / SH::COLS, p.nfields);
   TOP_LAUNCH((k_cols<EY, X2>), grid, SH::THREADS, bytes, s, q);
   return cudaGetLastError();

@@ -188,6 +188,27 @@ def test_config4_full_batch_intensity_sampled(T):
     assert np.isfinite(float(loss)) and np.isfinite(host(gp)).all()
 
 
+def test_config4_full_batch_gradient_is_the_mean_over_objects(T):
+    """The pupil gradient of the full 384-field step (the bench's launch) against the mean of the 16
+    single-object steps' gradients (the MSE averages over objects, so the batch gradient is their
+    mean: a property that holds at any size), and the loss against the mean of their losses.
+    Object 0's step itself is the oracle-checked case above at two wavelengths; here the full eight."""
+    sysm, obj, phase, target, lams = fourf_setup(T, 16, 3, 8)
+    gp = torch.empty((1024, 1024), dtype=torch.float32, device="cuda")
+    loss, _ = sysm.step(dev(obj), dev(phase), dev(target), gp)
+    one, _, _, _, _ = fourf_setup(T, 1, 3, 8)
+    acc = torch.zeros((1024, 1024), dtype=torch.float64, device="cuda")
+    losses = []
+    g1 = torch.empty_like(gp)
+    for o in range(16):
+        l1, _ = one.step(dev(obj[3 * o:3 * o + 3]), dev(phase), dev(target[o:o + 1]), g1)
+        acc += g1.double()
+        losses.append(float(l1))
+    mean = acc / 16
+    assert rel_l2(host(gp).astype(np.float64), host(mean)) < TOL
+    assert abs(float(loss) - np.mean(losses)) / np.mean(losses) < 1e-6
+
+
 # ----------------------------------------------------------------------------- config 5
 
 def test_config5a_coherence_full_size(T):
