@@ -398,6 +398,59 @@ struct Engine : Radices<R0, R1, R2, R3> {
       for (int j = 0; j < RB; ++j) v[q * RB + j] = buf[padi(pos<B>(t, q, j))];
   }
 
+  // fwd_compact / inv_compact: two-stage plans with equal radices run their two stages as one loop
+  // over a single copy of the in-register DFT (half the code of the unrolled form), for kernels
+  // whose code otherwise spills out of the instruction cache (the fused row passes hold a forward
+  // and an inverse transform); elsewhere the unrolled form measured faster.
+  static constexpr bool LOOP2 = NS == 2 && Rd::radix(0) == Rd::radix(1);
+
+  template <int DIR>
+  __device__ __forceinline__ static void dfts(float2 (&v)[E]) {
+    constexpr int R = radix(0), Q = M / (R * G);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) dft<R, 1, DIR>(v + q * R);
+  }
+  // the twiddles of stage 0 (span span(0)), conjugated for the inverse
+  template <int DIR>
+  __device__ __forceinline__ static void stage0_twiddles(float2 (&v)[E], int t, const float2* __restrict__ tw) {
+    constexpr int R = radix(0), SP = span(0), Q = M / (R * G);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      float2* w = v + q * R;
+      const int i = (t + G * q) % SP;
+      const float2* tp = tw + tw_off(0) + i;
+#pragma unroll
+      for (int j = 1; j < R; ++j) w[j] = DIR < 0 ? c_mul(w[j], __ldg(tp + (j - 1) * SP)) : c_mulc(w[j], __ldg(tp + (j - 1) * SP));
+    }
+  }
+
+  __device__ __forceinline__ static void fwd_compact(float2 (&v)[E], float2* buf, int t, const float2* __restrict__ tw) {
+    if constexpr (LOOP2) {
+#pragma unroll 1
+      for (int s = 0; s < 2; ++s) {
+        if (s == 1) exchange<0, 1>(v, buf, t);
+        dfts<-1>(v);
+        if (s == 0) stage0_twiddles<-1>(v, t, tw);
+      }
+    } else {
+      fwd(v, buf, t, tw);
+    }
+  }
+  __device__ __forceinline__ static void inv_compact(float2 (&v)[E], float2* buf, int t, const float2* __restrict__ tw) {
+    if constexpr (LOOP2) {
+#pragma unroll 1
+      for (int s = 0; s < 2; ++s) {
+        if (s == 1) {
+          exchange<1, 0>(v, buf, t);
+          stage0_twiddles<+1>(v, t, tw);
+        }
+        dfts<+1>(v);
+      }
+    } else {
+      inv(v, buf, t, tw);
+    }
+  }
+
   // forward DFT: natural-order input (in_pos layout) -> digit-reversed bins (bin layout)
   __device__ __forceinline__ static void fwd(float2 (&v)[E], float2* buf, int t, const float2* __restrict__ tw) {
     stage<0, -1>(v, t, tw);

@@ -22,6 +22,10 @@ namespace top {
 #ifndef TOP_PAIR_INV_MINB
 #define TOP_PAIR_INV_MINB 3
 #endif
+// Whether the fused row pass runs its forward transform in the compact (looped) form too.
+#ifndef TOP_CHAIN_FWD_COMPACT
+#define TOP_CHAIN_FWD_COMPACT 1
+#endif
 // Whether the inverse pass loads the next field's bins before this field's epilogue.
 #ifndef TOP_PAIR_PREFETCH
 #define TOP_PAIR_PREFETCH 1
@@ -142,9 +146,13 @@ __device__ __forceinline__ void pair_spread(float2 (&v)[EX::E], const float2 (&o
 }
 
 // Inverse transform of the bins in v, then the odd half's unfold twiddle (v = E or O').
-template <class EX>
+template <class EX, bool COMPACT = false>
 __device__ __forceinline__ void pair_inverse(const PassParams& p, float2 (&v)[EX::E], float2* mine, int r, int t) {
-  EX::inv(v, mine, t, p.twx);
+  if constexpr (COMPACT) {
+    EX::inv_compact(v, mine, t, p.twx);
+  } else {
+    EX::inv(v, mine, t, p.twx);
+  }
   if (r) {
     const float2 wt = ldg2(p.wpx + t);
     for_slots(
@@ -374,7 +382,7 @@ __global__ void __launch_bounds__(PairRows<EX>::THREADS, TOP_PAIR_INV_MINB) k_ro
         xs = reinterpret_cast<const float2*>(xdst);
       }
     }
-    pair_inverse<EX>(p, v, mine, r, t);
+    pair_inverse<EX, true>(p, v, mine, r, t);
     float2 o[H];
     pair_combine<EX>(v, o, mine, theirs, r, t, row);
 #if TOP_PAIR_PREFETCH
@@ -459,7 +467,7 @@ __global__ void __launch_bounds__(PairRows<EX>::THREADS, 4)
 #pragma unroll
     for (int e = 0; e < EX::E; ++e) v[e] = make_float2(0.f, 0.f);
   }
-  pair_inverse<EX>(pa, v, mine, r, t);
+  pair_inverse<EX, true>(pa, v, mine, r, t);
   float2 o[PR::H];
   pair_combine<EX>(v, o, mine, theirs, r, t, row);
   if (sf) {
@@ -478,7 +486,11 @@ __global__ void __launch_bounds__(PairRows<EX>::THREADS, 4)
     o[k] = val;
   }
   pair_spread<EX>(v, o, mine, theirs, r, t, row, pb.wpx);
+#if TOP_CHAIN_FWD_COMPACT
+  EX::fwd_compact(v, mine, t, pb.twx);
+#else
   EX::fwd(v, mine, t, pb.twx);
+#endif
   if (live) pair_store_bins<EX>(pb, f, y, r, t, v);
 }
 
