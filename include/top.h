@@ -401,13 +401,16 @@ top_status top_coherence_intensity_backward(top_handle h, const top_grid* g, con
  * bit. TOP_TUNE_CLASSIC_*: the block-cooperative row kernels instead of the pair-local ones (plans
  * of one warp a half line at padding 2); TOP_TUNE_NO_L2_*: no L2 prefetch of the next wave's
  * inputs; bits 8-10 (TOP_TUNE_SPAN): fields per block of the inverse row pass with a field
- * epilogue, c -> 2^(c - 1) (0: 4). */
+ * epilogue, c -> 2^(c - 1) (0: 4); TOP_TUNE_THREE_PASS (read for M = 64): fields of 64 x 64 at
+ * padding 2 go through the three passes and the workspace instead of the one-kernel on-chip
+ * propagation (plain propagations: no modulation, a field epilogue). */
 #define TOP_TUNE_CLASSIC_FWD 0x1u
 #define TOP_TUNE_CLASSIC_INV 0x2u
 #define TOP_TUNE_CLASSIC_CHAIN 0x4u
 #define TOP_TUNE_NO_L2_COLS 0x8u
 #define TOP_TUNE_NO_L2_FWD 0x10u
 #define TOP_TUNE_SPAN(c) ((uint32_t)(c) << 8)
+#define TOP_TUNE_THREE_PASS 0x800u
 
 /* Measure the pass variants on g's geometry (padded sizes with a plan of their own; g->batch
  * fields of scratch, allocated and freed by the call -- 16 or more fields at 1024^2 give passes

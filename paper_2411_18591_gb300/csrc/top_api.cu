@@ -1225,7 +1225,11 @@ top_status run_propagation(top_handle h, const Request& q, cudaStream_t st) {
     const int64_t want_groups = std::max<int64_t>(1, (4 * 152 + tiles - 1) / tiles);
     group = std::max<int64_t>(1, (B + want_groups - 1) / want_groups);
   }
-  const size_t ws_field = size_t(geo.Px) * size_t(geo.ny) * sizeof(float2);
+  // plain propagations of 64 x 64 fields at padding 2 run as one on-chip kernel (no workspace)
+  const bool onchip = geo.Py == 128 && geo.Px == 128 && geo.ny == 64 && geo.nx == 64 && q.n_up == 0 &&
+                      q.src_kind == SRC_FIELD && !(q.msrc && q.msrc->flags) && q.epi_kind == EPI_FIELD &&
+                      !(q.mepi && q.mepi->flags) && !(tune_flags(geo.Px / 2) & TOP_TUNE_THREE_PASS);
+  const size_t ws_field = onchip ? 0 : size_t(geo.Px) * size_t(geo.ny) * sizeof(float2);
   EngineInfo ex_info;
   find_engine(geo.Px / 2, &ex_info);
   const int ntiles = (geo.ny + ex_info.rows - 1) / ex_info.rows;  // R2 row tiles (overlap partial sums)
@@ -1246,7 +1250,7 @@ top_status run_propagation(top_handle h, const Request& q, cudaStream_t st) {
   int64_t chunk = std::min<int64_t>(B, kMaxFields);
   chunk = std::max<int64_t>(align, chunk - chunk % align);
   // broadcast sources: one forward spectrum per source (Px x Py samples) after the partials
-  const bool share = q.src_kind == SRC_FIELD && in_repeat > 1 && shared_source(q.msrc);
+  const bool share = q.src_kind == SRC_FIELD && in_repeat > 1 && shared_source(q.msrc) && !onchip;
   const size_t spec_src = share ? size_t(geo.Px) * size_t(geo.Py) * sizeof(float2) : 0;
   auto need = [&](int64_t c) {
     const int64_t ng = (c + group - 1) / group;
@@ -1407,6 +1411,11 @@ top_status run_propagation(top_handle h, const Request& q, cudaStream_t st) {
                       [&] { return launch_pass(PASS_ROWS_CHAIN, p.Mx, pu[j], st, &nxt); }));
         TOP_TRY(timed(h, KK_COLS, st, "column pass", [&] { return launch_pass(PASS_COLS, p.My, nxt, st); }));
       }
+    } else if (onchip) {
+      if (!onchip_supported(p)) return fail(TOP_ERR_INTERNAL, "on-chip propagation chosen for a request it does not take");
+      TOP_TRY(timed(h, KK_ONCHIP, st, "on-chip propagation", [&] { return launch_onchip(p, st); }));
+      pos += n;
+      continue;
     } else if (share) {
       const PassParams ps = source_params(p, int(in_repeat), spec);
       PassParams pc = p;
@@ -1811,6 +1820,12 @@ top_status run_ragged(top_handle h, int count, const top_grid* grids, const void
       // that carry them in their parameters
       TOP_CUDA(launch_put(d_lists, lists.data(), lists.size() * sizeof(void*), st), "ragged field lists");
       p.nfields = int(n);
+      if (onchip_supported(p) && !(tune_flags(geo.Px / 2) & TOP_TUNE_THREE_PASS)) {
+        // 64 x 64 fields at padding 2: the same on-chip kernel as a single call's
+        TOP_TRY(timed(h, KK_ONCHIP, st, "on-chip propagation", [&] { return launch_onchip(p, st); }));
+        pos += n;
+        continue;
+      }
       TOP_TRY(timed(h, KK_ROWS_FWD, st, "rows forward pass", [&] { return launch_pass(PASS_ROWS_FWD, p.Mx, p, st); }));
       TOP_TRY(timed(h, KK_COLS, st, "column pass", [&] { return launch_pass(PASS_COLS, p.My, p, st); }));
       TOP_TRY(timed(h, KK_ROWS_INV, st, "rows inverse pass", [&] { return launch_pass(PASS_ROWS_INV, p.Mx, p, st); }));
@@ -2623,7 +2638,7 @@ top_status top_profile_read(top_handle h, int cap, const char** kinds, double* m
     h->pool.push_back(pe.second.second);
   }
   h->pending.clear();
-  static const char* names[KK_COUNT] = {"rows_fwd", "cols", "rows_inv", "aux", "rows_chain"};
+  static const char* names[KK_COUNT] = {"rows_fwd", "cols", "rows_inv", "aux", "rows_chain", "onchip"};
   int w = 0;
   for (int k = 0; k < KK_COUNT && w < cap; ++k, ++w) {
     if (kinds) kinds[w] = names[k];

@@ -76,6 +76,10 @@ cudaError_t launch_intensity_sum(const float2* psi, const float* weights, int gr
 // part[(b ntiles + tile) 3 + c], for launch_overlap_finish; target_stride 0 shares phi.
 cudaError_t launch_overlap_partials(const float2* psi, const float2* target, long long target_stride, long long batch,
                                     long long plane, int ntiles, double* part, cudaStream_t s);
+// Whole propagations of 64 x 64 fields at padding 2 in one kernel (top_onchip.cu), for plain
+// requests: a field source without modulation and a field epilogue without modulation.
+bool onchip_supported(const PassParams& p);
+cudaError_t launch_onchip(const PassParams& p, cudaStream_t s);
 // out[b][c][r] = in[b][r][c] for a batch of [rows][cols] planes.
 cudaError_t launch_transpose_rect(const float2* in, float2* out, long long batch, int rows, int cols, cudaStream_t s);
 

@@ -186,6 +186,6 @@ inline int tune_span(uint32_t flags) {
 // Largest dynamic shared memory of a fused chain block (R2 of one propagation + R1 of the next).
 constexpr size_t kChainSmemMax = 227 * 1024;
 
-enum KernelKind : int { KK_ROWS_FWD = 0, KK_COLS, KK_ROWS_INV, KK_AUX, KK_ROWS_CHAIN, KK_COUNT };
+enum KernelKind : int { KK_ROWS_FWD = 0, KK_COLS, KK_ROWS_INV, KK_AUX, KK_ROWS_CHAIN, KK_ONCHIP, KK_COUNT };
 
 }  // namespace top

@@ -19,7 +19,7 @@ std::mutex g_tune_mutex;
 std::map<int, uint32_t> g_tune;
 
 constexpr const char* kTuneHeader = "top-autotune 1";
-constexpr uint32_t kTuneMask = 0x7ffu;  // every defined flag bit
+constexpr uint32_t kTuneMask = 0xfffu;  // every defined flag bit
 
 // FNV-1a, 64 bits
 uint64_t fnv1a(const char* p, size_t n) {
