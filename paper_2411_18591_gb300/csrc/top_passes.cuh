@@ -55,6 +55,21 @@ __device__ __forceinline__ long long direct_base(int r, int t, int y, int ny) {
   return ws_index(r * EN::M + EN::kbase(t), y, ny);
 }
 
+// Registers a thread of the blocks whose line groups do not tile a warp (the mixed-radix plans of
+// 25 and 50 threads a line) are held to, per pass kind: left to itself the compiler took 160-210
+// and one to three blocks per SM for twenty samples a thread (measured on the 1000-point plan:
+// column pass 52.0 -> 38.5 us per field at 96, inverse rows 25.8 -> 17.7 at 128).
+#ifndef TOP_GROUP_REGS_COLS
+#define TOP_GROUP_REGS_COLS 96
+#endif
+#ifndef TOP_GROUP_REGS_ROWS
+#define TOP_GROUP_REGS_ROWS 128
+#endif
+// Blocks per SM that hold a block of `threads` to at most `regs` registers a thread.
+__host__ __device__ constexpr int blocks_for_regs(int threads, int regs) {
+  return 65536 / (((threads + 31) / 32) * 32 * regs) > 0 ? 65536 / (((threads + 31) / 32) * 32 * regs) : 1;
+}
+
 // Rows per block of the row passes; two thread groups (the two halves) per row. Two-stage plans
 // move their bins directly between registers and the workspace (DIRECT); deeper plans stage them
 // through a shared tile [2M][LD].
@@ -75,7 +90,7 @@ struct RowShape {
   static constexpr size_t SMEM = sizeof(float2) * (MAX2 > ROWBUF ? MAX2 : ROWBUF);
   // the inverse pass keeps 128 registers a thread (four 128-thread blocks per SM, two of 256);
   // the forward pass of 256-thread blocks too (smaller blocks stay below 128 unbounded)
-  static constexpr int MINB_INV = THREADS % 128 == 0 ? 512 / THREADS : 1;
+  static constexpr int MINB_INV = THREADS % 128 == 0 ? 512 / THREADS : blocks_for_regs(THREADS, TOP_GROUP_REGS_ROWS);
   static constexpr bool FWD_B2 = THREADS == 256;
   // R1 stages the planes its source needs besides the field rows after SMEM (at most five floats
   // per sample: intensity gradient, phase, amplitude, complex mask)
@@ -112,7 +127,8 @@ struct ColShape {
   // two-stage power-of-two plans fit five blocks per SM (96 registers) without real spills; other
   // blocks of whole 128-thread multiples keep 128 registers a thread (at least two blocks of 256)
   static constexpr int MINB = (EN::NS == 2 && (EN::G & (EN::G - 1)) == 0 && THREADS <= 128) ? 5
-                              : (THREADS % 128 == 0 && THREADS <= 256) ? 512 / THREADS : 1;
+                              : (THREADS % 128 == 0 && THREADS <= 256) ? 512 / THREADS
+                              : THREADS % 32 != 0 ? blocks_for_regs(THREADS, TOP_GROUP_REGS_COLS) : 1;
   // line stride: room for the column and an exchange buffer, and LS = 16 / CB (mod 16) so that the
   // CB lines of a copy instruction fall on distinct banks
   __host__ __device__ static constexpr int line_stride(int ny) {
