@@ -135,6 +135,10 @@ struct ColShape {
     const int l = ny > EN::BUF ? ny : EN::BUF;
     return l + ((16 / CB - l) % 16 + 16) % 16;
   }
+  // Two-stage plans without bin padding read their H entries straight from the table (L1/L2; a
+  // warp's loads for one slot are consecutive): measured faster than staging the rows (1024-point
+  // plan 15.9 -> 15.1 us per field); the deeper plans stage them (2048-point 108 against 130 us).
+  static constexpr bool TWO_STAGE_GLOBAL_H = EN::NS == 2 && !EN::BIN_PAD;
   // With padding exactly 2 (ny = M) the transfer-function rows of the block's columns (HS entries
   // each) are staged in shared memory too, where that keeps two blocks per SM (or where the
   // registers hold one block per SM anyway); otherwise the rows are read from global memory.
@@ -144,7 +148,7 @@ struct ColShape {
   static constexpr size_t H_BUDGET = 65536 / (THREADS * 128) >= 2 ? 110 * 1024 : 220 * 1024;
   template <bool X2>
   static constexpr bool stage_h() {
-    return X2 && sizeof(float2) * COLS * (line_stride(EN::M) + EN::BUF + HSS) <= H_BUDGET;
+    return X2 && !TWO_STAGE_GLOBAL_H && sizeof(float2) * COLS * (line_stride(EN::M) + EN::BUF + HSS) <= H_BUDGET;
   }
   template <bool X2>
   static size_t smem(int ny) {
