@@ -2816,6 +2816,12 @@ top_status propagate_noalloc(const top_grid* g, const void* in, void* out, const
     p.nfields = int(n);
     p.in = static_cast<const float2*>(in) + pos * plane;
     p.out = static_cast<float2*>(out) + pos * plane;
+    if (onchip_supported(p) && !(tune_flags(p.Mx) & TOP_TUNE_THREE_PASS)) {
+      // 64 x 64 fields at padding 2: the on-chip kernel, as top_propagate runs them
+      TOP_CUDA(launch_onchip(p, st), "on-chip propagation");
+      pos += n;
+      continue;
+    }
     TOP_CUDA(launch_pass(PASS_ROWS_FWD, p.Mx, p, st), "rows forward pass");
     TOP_CUDA(launch_pass(PASS_COLS, p.My, p, st), "column pass");
     TOP_CUDA(launch_pass(PASS_ROWS_INV, p.Mx, p, st), "rows inverse pass");

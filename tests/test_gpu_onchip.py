@@ -113,3 +113,15 @@ def test_modulated_requests_keep_the_three_passes(T, rel):
     assert n_on == 0 and n_cols >= 1
     ref = O.propagate(x0 * np.exp(1j * phi.astype(np.float64)), d, d, 633e-9, 0.02, 2.0)
     assert rel(y.cpu().numpy(), ref) < TOL
+
+
+def test_noalloc_call_takes_the_same_kernel(T):
+    # the handle-free call gives top_propagate's results bit for bit at this size too
+    d = 10e-6
+    x = torch.from_numpy(fields(307, 5)).cuda()
+    lams = [450e-9, 532e-9, 633e-9, 700e-9, 532e-9]
+    ref = T.top_propagate(x, d, d, lams, 0.02, 2.0)
+    out = torch.empty_like(x)
+    T.top_propagate_noalloc(x, d, d, lams, 0.02, 2.0, out=out)
+    torch.cuda.synchronize()
+    assert torch.equal(out, ref)
