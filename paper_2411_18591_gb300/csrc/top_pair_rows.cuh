@@ -22,6 +22,10 @@ namespace top {
 #ifndef TOP_PAIR_INV_MINB
 #define TOP_PAIR_INV_MINB 3
 #endif
+// Blocks per SM the pair-local fused row pass is compiled for.
+#ifndef TOP_PAIR_CHAIN_MINB
+#define TOP_PAIR_CHAIN_MINB 4
+#endif
 // Whether the fused row pass runs its forward transform in the compact (looped) form too.
 #ifndef TOP_CHAIN_FWD_COMPACT
 #define TOP_CHAIN_FWD_COMPACT 1
@@ -440,7 +444,7 @@ __global__ void __launch_bounds__(PairRows<EX>::THREADS, TOP_PAIR_INV_MINB) k_ro
 // forward rows (pb) of a system chain, as k_rows_chain does, pair-local. The next source's
 // operands are staged after the exchange buffers while the rows are transformed.
 template <class EX, uint32_t MF>
-__global__ void __launch_bounds__(PairRows<EX>::THREADS, 4)
+__global__ void __launch_bounds__(PairRows<EX>::THREADS, TOP_PAIR_CHAIN_MINB)
     k_rows_chain_pair(const __grid_constant__ PassParams pa, const __grid_constant__ PassParams pb) {
   using PR = PairRows<EX>;
   TOP_DYN_SMEM(float2, smem);

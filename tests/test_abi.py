@@ -160,10 +160,11 @@ def test_autotune_table_round_trip_and_corruption(lib, tmp_path):
     is refused with TOP_ERR_INVALID_ARG and leaves the table as it was (host-only calls)."""
     cdll = lib.load()
     assert cdll.top_autotune_clear() == 0
-    entries = {1024: 0x1 | 0x8, 512: 0x2 | (3 << 8), 250: 0}
+    entries = {1024: 0x1 | 0x8, 512: 0x2 | (3 << 8), 250: 0, 64: 0x800}  # 0x800: TOP_TUNE_THREE_PASS
     for m, f in entries.items():
         assert cdll.top_autotune_set(m, f) == 0
     assert cdll.top_autotune_set(1024, 0x8000) == 1  # unknown flag bit
+    assert cdll.top_autotune_set(1024, 0x1000) == 1
     assert cdll.top_autotune_set(0, 0) == 1
     path = tmp_path / "tune.txt"
     assert cdll.top_autotune_save(str(path).encode()) == 0
