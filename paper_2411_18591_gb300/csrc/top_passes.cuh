@@ -55,6 +55,11 @@ __device__ __forceinline__ long long direct_base(int r, int t, int y, int ny) {
   return ws_index(r * EN::M + EN::kbase(t), y, ny);
 }
 
+// Blocks per SM of the column pass of two-stage plans with blocks of 128 threads or fewer.
+#ifndef TOP_COL_MINB_SMALL
+#define TOP_COL_MINB_SMALL 5
+#endif
+
 // Registers a thread of the blocks whose line groups do not tile a warp (the mixed-radix plans of
 // 25 and 50 threads a line) are held to, per pass kind: left to itself the compiler took 160-210
 // and one to three blocks per SM for twenty samples a thread (measured on the 1000-point plan:
@@ -126,7 +131,7 @@ struct ColShape {
   static constexpr int THREADS = GROUPS * EN::G;
   // two-stage power-of-two plans fit five blocks per SM (96 registers) without real spills; other
   // blocks of whole 128-thread multiples keep 128 registers a thread (at least two blocks of 256)
-  static constexpr int MINB = (EN::NS == 2 && (EN::G & (EN::G - 1)) == 0 && THREADS <= 128) ? 5
+  static constexpr int MINB = (EN::NS == 2 && (EN::G & (EN::G - 1)) == 0 && THREADS <= 128) ? TOP_COL_MINB_SMALL
                               : (THREADS % 128 == 0 && THREADS <= 256) ? 512 / THREADS
                               : THREADS % 32 != 0 ? blocks_for_regs(THREADS, TOP_GROUP_REGS_COLS) : 1;
   // line stride: room for the column and an exchange buffer, and LS = 16 / CB (mod 16) so that the
