@@ -282,6 +282,20 @@ top_status top_propagate_intensity_backward(top_handle h, const top_grid* g, con
                                             int64_t n_lz, const top_mod* pre, const top_mod* post,
                                             const top_mod_grads* pre_grads, void* stream);
 
+/* Detector intensity of fields already at the detector (Eq. 14, without a propagation):
+ * I[b / group] = sum over each consecutive group of `group` fields of w_b |field_b|^2, summed in
+ * field order. field: complex64 [batch][ny][nx] device; intensity: float32 [batch/group][ny][nx]
+ * device; weights: device float32 [batch] or NULL (all 1); group >= 1 divides batch. The grid's
+ * spacing, padding and method are not used. Errors: TOP_ERR_INVALID_ARG before any launch. */
+top_status top_intensity(top_handle h, const top_grid* g, const void* field, float* intensity, int64_t group,
+                         const float* weights, void* stream);
+
+/* Backward of top_intensity: grad_field_b = 2 w_b grad_I[b / group] field_b (the gradient of a
+ * real loss in the g = dL/dRe + i dL/dIm convention). grad_intensity: float32 [batch/group][ny][nx];
+ * grad_field: complex64 [batch][ny][nx] (grad_field == field allowed). */
+top_status top_intensity_backward(top_handle h, const top_grid* g, const void* field, const float* grad_intensity,
+                                  void* grad_field, int64_t group, const float* weights, void* stream);
+
 /* ---------------------------------------------------------------- modulation (Eq. 1) */
 
 /* out = M * in, point-wise (in == out allowed). lambda (host, n_lz values) is used by lenses only. */

@@ -90,6 +90,8 @@ SIGNATURES = {
     "top_overlap_loss": (C.c_int, [_P, _GRID, _P, _P, _I64, _P, _P, _P]),
     "top_propagate_coherence": (C.c_int, [_P, _GRID, _P, _P, _D, _D, _MOD, _P]),
     "top_propagate_coherence_backward": (C.c_int, [_P, _GRID, _P, _P, _D, _D, _MOD, _GRADS, _P]),
+    "top_intensity": (C.c_int, [_P, _GRID, _P, _P, _I64, _P, _P]),
+    "top_intensity_backward": (C.c_int, [_P, _GRID, _P, _P, _P, _I64, _P, _P]),
     "top_coherence_intensity": (C.c_int, [_P, _GRID, _P, _P, _P]),
     "top_coherence_intensity_backward": (C.c_int, [_P, _GRID, _P, _P, _P]),
     "top_autotune": (C.c_int, [_P, _GRID, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]),

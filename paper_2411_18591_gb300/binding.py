@@ -480,6 +480,34 @@ def top_propagate_intensity(field: torch.Tensor, dy: float, dx: float, lam, z, p
     return inten, fout
 
 
+def top_intensity(field: torch.Tensor, group: int = 1, weights: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """I[b/group] = sum over each group of `group` fields of w_b |field_b|^2 (Eq. 14, no propagation)."""
+    _field(field, "field")
+    b, ny, nx = _shape3(field)
+    inten = torch.empty((b // max(1, group), ny, nx), dtype=torch.float32, device=field.device)
+    g = make_grid(b, ny, nx, 1.0, 1.0, 1.0, "as")
+    check(_lib.load().top_intensity(handle(field.device), C.byref(g), field.data_ptr(), inten.data_ptr(), group,
+                                    _ptr(_real(weights, "weights")), _stream(field)))
+    return inten
+
+
+def top_intensity_backward(field: torch.Tensor, grad_intensity: torch.Tensor, group: int = 1,
+                           weights: Optional[torch.Tensor] = None, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """Backward of top_intensity: grad_field_b = 2 w_b grad_I[b/group] field_b."""
+    _field(field, "field")
+    _real(grad_intensity, "grad_intensity")
+    b, ny, nx = _shape3(field)
+    if out is None:
+        out = torch.empty_like(field)
+    else:
+        _field(out, "out")
+    g = make_grid(b, ny, nx, 1.0, 1.0, 1.0, "as")
+    check(_lib.load().top_intensity_backward(handle(field.device), C.byref(g), field.data_ptr(),
+                                             grad_intensity.data_ptr(), out.data_ptr(), group,
+                                             _ptr(_real(weights, "weights")), _stream(field)))
+    return out
+
+
 def top_propagate_intensity_backward(field: torch.Tensor, grad_intensity: torch.Tensor, dy: float, dx: float, lam,
                                      z, pad: float = 2.0, method="as", group: int = 1,
                                      weights: Optional[torch.Tensor] = None, pre: Optional[Modulation] = None,

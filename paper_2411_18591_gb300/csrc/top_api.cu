@@ -2590,6 +2590,47 @@ top_status top_propagate_coherence_backward(top_handle h, const top_grid* g, con
   return s;
 }
 
+static top_status intensity_check(top_handle h, const top_grid* g, const void* field, const void* other, int64_t group,
+                                  const float* weights, long long* plane) {
+  if (!h) return fail(TOP_ERR_INVALID_ARG, "handle is NULL");
+  Geometry geo;
+  TOP_TRY(check_grid(g, &geo));
+  TOP_TRY(check_ptr(field, "field"));
+  TOP_TRY(check_ptr(other, "intensity or gradient"));
+  if (group < 1 || g->batch % group != 0)
+    return fail(TOP_ERR_INVALID_ARG, "group (%lld) must be >= 1 and divide batch (%lld)", (long long)group,
+                (long long)g->batch);
+  if (group > 65535) return fail(TOP_ERR_UNSUPPORTED, "group larger than 65535 fields");
+  if (weights && !aligned16(weights)) return fail(TOP_ERR_INVALID_ARG, "weights not 16-byte aligned");
+  *plane = (long long)g->ny * g->nx;
+  return TOP_OK;
+}
+
+top_status top_intensity(top_handle h, const top_grid* g, const void* field, float* intensity, int64_t group,
+                         const float* weights, void* stream) {
+  long long plane = 0;
+  TOP_TRY(intensity_check(h, g, field, intensity, group, weights, &plane));
+  TOP_TRY(bind(h));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  return timed(h, KK_AUX, st, "intensity", [&] {
+    return launch_intensity_sum(static_cast<const float2*>(field), weights, int(group), g->batch / group, plane,
+                                intensity, st);
+  });
+}
+
+top_status top_intensity_backward(top_handle h, const top_grid* g, const void* field, const float* grad_intensity,
+                                  void* grad_field, int64_t group, const float* weights, void* stream) {
+  long long plane = 0;
+  TOP_TRY(intensity_check(h, g, field, grad_field, group, weights, &plane));
+  TOP_TRY(check_ptr(grad_intensity, "grad_intensity"));
+  TOP_TRY(bind(h));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  return timed(h, KK_AUX, st, "intensity backward", [&] {
+    return launch_intensity_source(static_cast<const float2*>(field), grad_intensity, weights, int(group), g->batch,
+                                   plane, static_cast<float2*>(grad_field), st);
+  });
+}
+
 top_status top_coherence_intensity(top_handle h, const top_grid* g, const void* gamma, float* intensity, void* stream) {
   if (!h) return fail(TOP_ERR_INVALID_ARG, "handle is NULL");
   Geometry geo;

@@ -1,7 +1,7 @@
-"""Degenerate cases of the propagation through the C ABI: z = 0 is the identity, a propagation by
--z is the adjoint at z when no sample is evanescent, zero fields stay zero, and empty requests
-are refused (a batch of fields) or do nothing (a ragged list) -- on the on-chip path (64^2 at
-padding 2) and on the three passes alike."""
+"""Degenerate cases of the propagation through the C ABI -- z = 0 is the identity, a propagation
+by -z is the adjoint at z when no sample is evanescent, zero fields stay zero, empty requests are
+refused (a batch of fields) or do nothing (a ragged list), on the on-chip path (64^2 at padding 2)
+and on the three passes alike -- and the standalone detector intensity (Eq. 14) with its backward."""
 import numpy as np
 import pytest
 import torch
@@ -70,3 +70,23 @@ def test_empty_requests(T):
     st = _lib.load().top_propagate_ragged(handle(), 0, None, None, None, None, None, 0, None)
     assert st == 0
     assert _lib.load().top_propagate_ragged(handle(), -1, None, None, None, None, None, 0, None) == 1
+
+
+@pytest.mark.parametrize("group,weighted", [(1, False), (3, True), (6, False)])
+def test_standalone_intensity_and_backward(T, rel, group, weighted):
+    # Eq. 14 on fields already at the detector, and its backward, against the oracle
+    b, n = 6, 96
+    x0 = fields(403, b, n)
+    w = np.linspace(0.5, 1.5, b).astype(np.float32) if weighted else None
+    x = torch.from_numpy(x0).cuda()
+    wt = torch.from_numpy(w).cuda() if weighted else None
+    inten = T.top_intensity(x, group, wt)
+    ref = O.intensity_sum(x0, group, None if w is None else w.astype(np.float64))
+    assert rel(inten.cpu().numpy(), ref) < 1e-6
+    gi0 = S.normal(404, (b // group, n, n)).astype(np.float32)
+    g = T.top_intensity_backward(x, torch.from_numpy(gi0).cuda(), group, wt)
+    wb = np.ones(b) if w is None else w.astype(np.float64)
+    gref = np.stack([wb[i] * O.grad_intensity(x0[i], gi0[i // group].astype(np.float64)) for i in range(b)])
+    assert rel(g.cpu().numpy(), gref) < 1e-6
+    with pytest.raises(T.TopError, match="INVALID_ARG"):
+        T.top_intensity(x, 4)  # 4 does not divide 6
