@@ -160,15 +160,13 @@ bool onchip_supported(const PassParams& p) {
 }
 
 cudaError_t launch_onchip(const PassParams& p, cudaStream_t s) {
-  static int sms = 0;
-  if (sms == 0) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return e;
-  }
-  cudaError_t e = cudaFuncSetAttribute(k_onchip64, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSmem));
+  // SM count of the current device (the grid is two blocks per SM)
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_onchip64, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSmem));
   if (e != cudaSuccess) return e;
   const int grid = p.nfields < 2 * sms ? p.nfields : 2 * sms;
   if (grid <= 0) return cudaSuccess;
